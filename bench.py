@@ -1,0 +1,335 @@
+"""Benchmark of the warping fast path: extrapolated Mpixel/s on one or more GB300s.
+
+Default workload (one "step"): the 1920x1080 FP32 sequence of 60 source frames with 32 moving rectangles (5% of
+them 1-3 px slivers); every step extrapolates P_1..P_3 at t + k/4 for all 60 frames with hole fill = 180 output
+frames = 373,248,000 output pixels, through one exw_extrapolate call.  Inputs (3.0 GB) and outputs (4.9 GB) are
+far larger than the 129 MB L2, so no flush is needed between steps.
+
+Reported (one JSON line on rank 0):
+  value       whole-job output Mpixel/s with inputs resident in HBM (device-timed with CUDA events)
+  e2e         the same through the C ABI with host buffers: pinned host -> device copies of the step's inputs,
+              the extrapolation, device -> host copies of its outputs, all inside the timed region
+  roofline    the dominant kernel's algorithmic bytes per launch / its mean event-timed duration, against the
+              measured HBM copy bandwidth
+  cpu_baseline the CPU oracle (FP64, single thread) on a bounded sample of the same workload
+  clocks      nvidia-smi SM clocks and throttle reasons sampled during the timed region
+--impl reference times the CPU oracle on the host cores instead (the reference arm of this build).
+Multi-GPU: one process per GPU (torchrun), each extrapolating its own sequence (replicas, weak scaling, no data
+collective); the step time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+W1080, H1080, NFRAMES, NFRAC = 1920, 1080, 60, 3
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["exw", "reference"], default="exw")
+    ap.add_argument("--frames", type=int, default=NFRAMES)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def render_sequence(nframes, seed_scene=None):
+    from paper_2307_12607_gb300 import scenes
+    s = scenes.sequence_1080p_scene(seed_scene)
+    col = np.empty((nframes, 3, s.H, s.W), np.float32)
+    dep = np.empty((nframes, s.H, s.W), np.float32)
+    mv = np.empty((nframes, 2, s.H, s.W), np.float32)
+    for f in range(nframes):
+        scenes.render(s, float(f), out=(col[f], dep[f], mv[f]))
+    return s, col, dep, mv
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle-reason samples while the timed region runs."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm = []
+        smax = None
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                smax = float(r[1])
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(seconds: float, seq):
+    """The CPU oracle as it stands (FP64 C, single thread) on whole frames of the benchmark's own 1080p sequence:
+    one frame is timed first, then as many frames as fit in ~``seconds`` are timed together."""
+    import oracle
+    oracle.build()
+    s, col, dep, mv = seq
+    t0 = time.perf_counter()
+    oracle.extrapolate(col[0].astype(np.float64), dep[0], mv[0], NFRAC)
+    one = time.perf_counter() - t0
+    n = int(max(1, min(len(col), seconds // max(one, 1e-3))))
+    inputs = [(col[f].astype(np.float64), dep[f], mv[f]) for f in range(n)]
+    t0 = time.perf_counter()
+    for cd, d, m in inputs:
+        oracle.extrapolate(cd, d, m, NFRAC)
+    dt = time.perf_counter() - t0
+    mpx = n * NFRAC * s.W * s.H / dt / 1e6
+    return {"value": mpx, "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} of the 60 source frames of the 1920x1080 FP32 sequence, {NFRAC} fractions each with "
+                      f"hole fill, FP64 C oracle single-threaded, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2307_12607_gb300 import scenes
+    oracle.build()
+    s = scenes.sequence_1080p_scene()
+    frames = [scenes.render(s, float(f)) for f in range(2)]
+    frames = [(c.astype(np.float64), d, m) for c, d, m in frames]
+    # each step extrapolates one source frame (a bounded sample of the 60-frame step)
+    for i in range(args.warmup):
+        oracle.extrapolate(*frames[i % 2], NFRAC)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        oracle.extrapolate(*frames[i % 2], NFRAC)
+    dt = (time.perf_counter() - t0) / max(1, args.steps)
+    mpx = NFRAC * s.W * s.H / dt / 1e6
+    line = {"impl": "reference", "metric": "extrapolated Mpixel/s (fwd) at 1080p", "value": mpx, "unit": "Mpixel/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "1920x1080 FP32 sequence (60 source frames, 32 rectangles, 5% slivers), P_1..P_3 "
+                                   "with hole fill; each reference step = 1 source frame (bounded sample)",
+                       "parallelism": "replicas"},
+            "cpu_baseline": {"value": mpx, "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
+                             "sample": "1 source frame of the 1080p sequence per step, 3 fractions with fill, FP64 C "
+                                       "oracle single-threaded"},
+            "e2e": {"value": mpx, "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_exw(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2307_12607_gb300 import binding as b, build
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    devc = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=devc)
+    build.build()
+
+    F = args.frames
+    seq = render_sequence(F)
+    s, col, dep, mv = seq
+    W, H = s.W, s.H
+    c = torch.from_numpy(col).to(devc)
+    d = torch.from_numpy(dep).to(devc)
+    m = torch.from_numpy(mv).to(devc)
+    out = torch.empty((F, NFRAC, 3, H, W), dtype=torch.float32, device=devc)
+    mask = torch.empty((F, NFRAC, H, W), dtype=torch.uint8, device=devc)
+    ws = b.workspace(b.exw_workspace_bytes(b.OP_EXTRAPOLATE, W, H, b.F32, F, NFRAC), devc)
+    stream = torch.cuda.current_stream(devc)
+
+    def step():
+        b.exw_extrapolate(c, d, m, nfrac=NFRAC, fill=True, out=out, mask=mask, ws=ws)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local] if \
+        os.environ.get("CUDA_VISIBLE_DEVICES") else str(local)
+    launches0 = b.exw_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_index) as clocks:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    launches = b.exw_launch_count() - launches0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=devc)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    out_px = F * NFRAC * W * H
+    value = world * out_px / (ms / 1e3) / 1e6
+
+    # per-kernel event timing over a second timed region (same steps), on the launching stream
+    b.exw_timing_enable(True)
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    kern = {}
+    for name in b.exw_timing_names():
+        tot, n = b.exw_timing_query(name)
+        kern[name] = (tot, n)
+    b.exw_timing_enable(False)
+    dom = max(kern, key=lambda k: kern[k][0])
+    tot, n = kern[dom]
+    avg_ms = tot / n
+    c_bytes = 12
+    per_src_px = {"exw_fused": (c_bytes + 4 + 8) + NFRAC * (c_bytes + 1),   # compulsory: source once, 3 outputs
+                  "exw_bounds": 8 + 16.0 / 64,                               # motion read + tile bounds written
+                  "exw_fixup": 0.0}
+    alg_bytes = per_src_px.get(dom, 0.0) * W * H
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (avg_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": alg_bytes, "mean_launch_ms": avg_ms,
+                "kernel_share": {k: v[0] / sum(x[0] for x in kern.values()) for k, v in kern.items()}}
+
+    # end to end through the C ABI with host buffers
+    hc = torch.from_numpy(col).pin_memory()
+    hd = torch.from_numpy(dep).pin_memory()
+    hm = torch.from_numpy(mv).pin_memory()
+    ho = torch.empty(out.shape, dtype=out.dtype).pin_memory()
+    hmask = torch.empty(mask.shape, dtype=mask.dtype).pin_memory()
+
+    def e2e_step():
+        c.copy_(hc, non_blocking=True)
+        d.copy_(hd, non_blocking=True)
+        m.copy_(hm, non_blocking=True)
+        step()
+        ho.copy_(out, non_blocking=True)
+        hmask.copy_(mask, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device=devc)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+        barrier()
+    h2d = (hc.numel() * 4 + hd.numel() * 4 + hm.numel() * 4)
+    d2h = ho.numel() * 4 + hmask.numel()
+
+    if rank == 0:
+        cpu = None if args.no_cpu_baseline else cpu_baseline(args.cpu_seconds, seq)
+        line = {"metric": "extrapolated Mpixel/s (fwd) at 1080p", "value": value, "unit": "Mpixel/s",
+                "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": "1920x1080 FP32 sequence: 60 source frames, 32 moving rectangles (5% 1-3 px "
+                                       "slivers), |mv| <= 16 px; P_1..P_3 at t+k/4 with pull-push hole fill = 180 "
+                                       "output frames per step per GPU",
+                           "frames_per_step": F, "fractions": NFRAC, "output_pixels_per_step_per_gpu": out_px,
+                           "l2_flush": "none needed: 3.0 GB inputs and 4.9 GB outputs per step exceed L2",
+                           "parallelism": f"replicas x{world}"},
+                "gpu_launches": launches, "launches_per_step": launches / args.steps,
+                "clocks": clocks.summary(),
+                "roofline": roofline,
+                "cpu_baseline": cpu,
+                "e2e": {"value": world * out_px / e2e_s / 1e6, "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_exw(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,250 @@
+"""Python binding of libexw: the C entry points under the same names, marshalling torch CUDA tensors to pointers.
+
+Every function checks devices, dtypes, shapes and contiguity, allocates outputs the caller did not pass (torch is
+the device-memory allocator; the library itself never allocates), passes the current torch CUDA stream and raises
+``ExwError`` on a non-zero status.  All arithmetic runs in the CUDA kernels of libexw.so; nothing here computes.
+
+Layouts (see include/exw.h): colour [3][H][W] float32/float16, depth [H][W] float32, motion [2][H][W] float32
+(plane 0 = x), keys [H][W] (uint64 bit patterns held in an int64 tensor), mask [H][W] uint8.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+
+F32, F16 = 0, 1
+OP_MOTION_BOUNDS, OP_FILL_HOLES, OP_EXTRAPOLATE, OP_WARP_BACKWARD = 0, 1, 2, 3
+FLAG_NO_FILL = 1
+MASK_EMPTY, MASK_CRACK = 1, 2
+KEY_EMPTY = -1  # all-ones uint64 as int64
+MAX_FRAC = 3
+
+
+class ExwError(RuntimeError):
+    def __init__(self, status: int, text: str):
+        super().__init__(f"libexw status {status}: {text}")
+        self.status = status
+
+
+def lib():
+    return _lib.load()
+
+
+def _check(status: int):
+    if status != 0:
+        raise ExwError(status, lib().exw_status_string(status).decode())
+
+
+def _cdt(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.float16:
+        return F16
+    raise TypeError(f"colour must be float32 or float16, got {t.dtype}")
+
+
+def _dev(t: torch.Tensor, name: str, dtype=None, shape=None) -> int:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (libexw runs on the GPU only)")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream, device) -> int:
+    if stream is None:
+        return torch.cuda.current_stream(device).cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _hw(depth: torch.Tensor):
+    if depth.dim() != 2:
+        raise ValueError("depth must be [H][W]")
+    return int(depth.shape[1]), int(depth.shape[0])
+
+
+def exw_status_string(status: int) -> str:
+    return lib().exw_status_string(int(status)).decode()
+
+
+def exw_version() -> int:
+    return int(lib().exw_version())
+
+
+def exw_workspace_bytes(op: int, W: int, H: int, cdt: int = F32, nframes: int = 1, nfrac: int = 1) -> int:
+    return int(lib().exw_workspace_bytes(op, W, H, cdt, nframes, nfrac))
+
+
+def workspace(nbytes: int, device) -> torch.Tensor:
+    """Device workspace of at least ``nbytes`` (torch allocates it; contents need no initialisation)."""
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def exw_motion_bounds(depth, mv, tile_bounds=None, frame_bounds=None, ws=None, stream=None):
+    """Stage (a0).  Returns (tile_bounds [ceil(H/8)][ceil(W/8)][4], frame_bounds [4]) float32."""
+    W, H = _hw(depth)
+    dev = depth.device
+    if tile_bounds is None:
+        tile_bounds = torch.empty(((H + 7) // 8, (W + 7) // 8, 4), dtype=torch.float32, device=dev)
+    if frame_bounds is None:
+        frame_bounds = torch.empty(4, dtype=torch.float32, device=dev)
+    need = exw_workspace_bytes(OP_MOTION_BOUNDS, W, H)
+    if ws is None:
+        ws = workspace(need, dev)
+    _check(lib().exw_motion_bounds(_dev(depth, "depth", torch.float32), _dev(mv, "mv", torch.float32, (2, H, W)),
+                                   W, H, _dev(tile_bounds, "tile_bounds", torch.float32),
+                                   _dev(frame_bounds, "frame_bounds", torch.float32), ws.data_ptr(), ws.numel(),
+                                   _stream(stream, dev)))
+    return tile_bounds, frame_bounds
+
+
+def exw_splat_motion(depth, mv, k: int, denom: int = 4, keys=None, stream=None):
+    """Stage (a).  Returns keys [H][W] (int64 tensor holding the uint64 keys)."""
+    W, H = _hw(depth)
+    if keys is None:
+        keys = torch.empty((H, W), dtype=torch.int64, device=depth.device)
+    _check(lib().exw_splat_motion(_dev(depth, "depth", torch.float32), _dev(mv, "mv", torch.float32, (2, H, W)), W,
+                                  H, int(k), int(denom), _dev(keys, "keys", torch.int64, (H, W)),
+                                  _stream(stream, depth.device)))
+    return keys
+
+
+def exw_warp(color, depth, mv, keys, k: int, denom: int = 4, out=None, mask=None, stream=None):
+    """Stage (b).  Returns (out colour [3][H][W] in the colour dtype, mask [H][W] uint8)."""
+    W, H = _hw(depth)
+    if out is None:
+        out = torch.empty((3, H, W), dtype=color.dtype, device=color.device)
+    if mask is None:
+        mask = torch.empty((H, W), dtype=torch.uint8, device=color.device)
+    _check(lib().exw_warp(_dev(color, "color", None, (3, H, W)), _cdt(color), _dev(depth, "depth", torch.float32),
+                          _dev(mv, "mv", torch.float32, (2, H, W)), _dev(keys, "keys", torch.int64, (H, W)), W, H,
+                          int(k), int(denom), _dev(out, "out", color.dtype, (3, H, W)),
+                          _dev(mask, "mask", torch.uint8, (H, W)), _stream(stream, color.device)))
+    return out, mask
+
+
+def exw_fill_holes(color, mask, ws=None, stream=None):
+    """Stage (c), in place on ``color``.  Returns ``color``."""
+    H, W = int(mask.shape[0]), int(mask.shape[1])
+    need = exw_workspace_bytes(OP_FILL_HOLES, W, H, _cdt(color))
+    if ws is None:
+        ws = workspace(need, color.device)
+    _check(lib().exw_fill_holes(_dev(color, "color", None, (3, H, W)), _cdt(color),
+                                _dev(mask, "mask", torch.uint8, (H, W)), W, H, ws.data_ptr(), ws.numel(),
+                                _stream(stream, color.device)))
+    return color
+
+
+def exw_extrapolate(color, depth, mv, nfrac: int = 3, fill: bool = True, out=None, mask=None, ws=None, stream=None):
+    """Stages (a0)+(a)+(b)+(c) for one frame ([3][H][W] colour) or a sequence ([F][3][H][W]).
+
+    Returns (out [F][nfrac][3][H][W], mask [F][nfrac][H][W]) -- without the F axis for a single frame."""
+    single = color.dim() == 3
+    if single:
+        color, depth, mv = color.unsqueeze(0), depth.unsqueeze(0), mv.unsqueeze(0)
+    F, _, H, W = (int(s) for s in color.shape)
+    dev = color.device
+    cdt = _cdt(color)
+    if out is None:
+        out = torch.empty((F, nfrac, 3, H, W), dtype=color.dtype, device=dev)
+    if mask is None:
+        mask = torch.empty((F, nfrac, H, W), dtype=torch.uint8, device=dev)
+    _dev(color, "color", None, (F, 3, H, W))
+    _dev(depth, "depth", torch.float32, (F, H, W))
+    _dev(mv, "mv", torch.float32, (F, 2, H, W))
+    _dev(out, "out", color.dtype, (F, nfrac, 3, H, W))
+    _dev(mask, "mask", torch.uint8, (F, nfrac, H, W))
+    need = exw_workspace_bytes(OP_EXTRAPOLATE, W, H, cdt, F, nfrac)
+    if ws is None:
+        ws = workspace(need, dev)
+    frames = (_lib.ExwFrame * F)()
+    outs = (_lib.ExwFrameOut * (F * nfrac))()
+    for f in range(F):
+        frames[f] = _lib.ExwFrame(color[f].data_ptr(), depth[f].data_ptr(), mv[f].data_ptr(), W, H, cdt)
+        for j in range(nfrac):
+            outs[f * nfrac + j] = _lib.ExwFrameOut(out[f, j].data_ptr(), mask[f, j].data_ptr())
+    _check(lib().exw_extrapolate(ctypes.cast(frames, ctypes.c_void_p), F, int(nfrac),
+                                 0 if fill else FLAG_NO_FILL, ctypes.cast(outs, ctypes.c_void_p), ws.data_ptr(),
+                                 ws.numel(), _stream(stream, dev)))
+    if single:
+        return out[0], mask[0]
+    return out, mask
+
+
+def exw_warp_backward(grad_out, color, depth, mv, keys, k: int, denom: int = 4, grad_color=None, grad_mv=None,
+                      ws=None, stream=None):
+    """Adjoint of stage (b); accumulates into (and returns) grad_color [3][H][W] and grad_mv [2][H][W] float32.
+    ``keys=None`` recomputes the keys into the workspace."""
+    W, H = _hw(depth)
+    dev = color.device
+    if grad_color is None:
+        grad_color = torch.zeros((3, H, W), dtype=torch.float32, device=dev)
+    if grad_mv is None:
+        grad_mv = torch.zeros((2, H, W), dtype=torch.float32, device=dev)
+    kptr = 0 if keys is None else _dev(keys, "keys", torch.int64, (H, W))
+    wsp, wsn = 0, 0
+    if keys is None:
+        if ws is None:
+            ws = workspace(exw_workspace_bytes(OP_WARP_BACKWARD, W, H, _cdt(color)), dev)
+        wsp, wsn = ws.data_ptr(), ws.numel()
+    _check(lib().exw_warp_backward(_dev(grad_out, "grad_out", torch.float32, (3, H, W)),
+                                   _dev(color, "color", None, (3, H, W)), _cdt(color),
+                                   _dev(depth, "depth", torch.float32), _dev(mv, "mv", torch.float32, (2, H, W)),
+                                   kptr, W, H, int(k), int(denom),
+                                   _dev(grad_color, "grad_color", torch.float32, (3, H, W)),
+                                   _dev(grad_mv, "grad_mv", torch.float32, (2, H, W)), wsp, wsn,
+                                   _stream(stream, dev)))
+    return grad_color, grad_mv
+
+
+def exw_l2_loss_grad(out, target, mask, grad_out=None, loss=None, stream=None):
+    """L2 loss over non-hole pixels.  Returns (loss [1] float32, accumulated; grad_out [3][H][W] float32)."""
+    H, W = int(mask.shape[0]), int(mask.shape[1])
+    dev = out.device
+    if grad_out is None:
+        grad_out = torch.empty((3, H, W), dtype=torch.float32, device=dev)
+    if loss is None:
+        loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    _check(lib().exw_l2_loss_grad(_dev(out, "out", None, (3, H, W)), _dev(target, "target", out.dtype, (3, H, W)),
+                                  _cdt(out), _dev(mask, "mask", torch.uint8, (H, W)), W, H,
+                                  _dev(grad_out, "grad_out", torch.float32, (3, H, W)),
+                                  _dev(loss, "loss", torch.float32), _stream(stream, dev)))
+    return loss, grad_out
+
+
+def exw_device_status(ws, stream=None) -> int:
+    return int(lib().exw_device_status(ws.data_ptr(), _stream(stream, ws.device)))
+
+
+def exw_timing_enable(on: bool = True):
+    lib().exw_timing_enable(1 if on else 0)
+
+
+def exw_timing_query(name: str):
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int(0)
+    rc = lib().exw_timing_query(name.encode(), ctypes.byref(ms), ctypes.byref(n))
+    return (float(ms.value), int(n.value)) if rc == 0 else (0.0, 0)
+
+
+def exw_timing_names():
+    need = int(lib().exw_timing_names(None, 0))
+    buf = ctypes.create_string_buffer(need)
+    lib().exw_timing_names(buf, need)
+    s = buf.value.decode()
+    return [x for x in s.split(",") if x]
+
+
+def exw_launch_count() -> int:
+    return int(lib().exw_launch_count())

@@ -1,0 +1,325 @@
+// exw_api.cu -- the extern "C" entry points of libexw: argument checks, workspace carving, launches.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "exw_internal.h"
+
+namespace exw {
+
+// ------------------------------------------------------------------------------------------------------------
+// Kernel timing: CUDA event pairs on the launching stream around every launch, while enabled.
+// ------------------------------------------------------------------------------------------------------------
+struct TimedLaunch {
+    std::string name;
+    cudaEvent_t start, stop;
+};
+static std::mutex g_tmu;
+static bool g_timing = false;
+static std::vector<TimedLaunch> g_timed;
+static std::vector<cudaEvent_t> g_event_pool;
+static std::atomic<uint64_t> g_launches{0};
+
+static cudaEvent_t take_event() {
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+void timing_begin(const char *name, cudaStream_t s) {
+    std::lock_guard<std::mutex> g(g_tmu);
+    if (!g_timing) return;
+    TimedLaunch t{name, take_event(), take_event()};
+    if (t.start == nullptr || t.stop == nullptr) return;
+    cudaEventRecord(t.start, s);
+    g_timed.push_back(t);
+}
+
+void timing_end(const char *name, cudaStream_t s) {
+    std::lock_guard<std::mutex> g(g_tmu);
+    if (!g_timing || g_timed.empty() || g_timed.back().name != name) return;
+    cudaEventRecord(g_timed.back().stop, s);
+}
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// ------------------------------------------------------------------------------------------------------------
+// Argument checks
+// ------------------------------------------------------------------------------------------------------------
+static bool aligned16(const void *p) { return p != nullptr && ((uintptr_t)p & 15u) == 0; }
+static bool size_ok(int W, int H) { return W >= 1 && H >= 1 && W <= 16384 && H <= 16384; }
+static bool dtype_ok(exw_dtype d) { return d == EXW_F32 || d == EXW_F16; }
+static int log2_pow2(int d) {
+    if (d < 1 || d > 64 || (d & (d - 1)) != 0) return -1;
+    int l = 0;
+    while ((1 << l) != d) ++l;
+    return l;
+}
+static exw_status from_cuda(cudaError_t e) { return e == cudaSuccess ? EXW_OK : EXW_ERR_CUDA; }
+static exw_status entry_check() { return cudaGetLastError() == cudaSuccess ? EXW_OK : EXW_ERR_CUDA; }
+
+static TileParams tile_params(const WsLayout &l, void *ws, int W, int H, int nfrac, int L, int k0, int frame) {
+    TileParams p{};
+    char *b = (char *)ws;
+    p.W = W;
+    p.H = H;
+    p.nfrac = nfrac;
+    p.L = L;
+    p.k0 = k0;
+    p.tile_bounds = (const float4 *)(b + l.tile_bounds);
+    p.nbx = l.nbx;
+    p.nby = l.nby;
+    p.fh = (FrameHeader *)(b + l.headers) + frame;
+    p.nodes = (float4 *)(b + l.nodes);
+    p.list = (uint32_t *)(b + l.list);
+    p.fillval = (float4 *)(b + l.fillval);
+    p.coarse = (float4 *)(b + l.coarse);
+    p.n5x = l.n5x;
+    p.n5y = l.n5y;
+    p.ncoarse = l.ncoarse;
+    return p;
+}
+
+}  // namespace exw
+
+using namespace exw;
+
+extern "C" {
+
+const char *exw_status_string(exw_status s) {
+    switch (s) {
+        case EXW_OK: return "EXW_OK";
+        case EXW_ERR_INVALID_ARG: return "EXW_ERR_INVALID_ARG: null, misaligned or out-of-range argument";
+        case EXW_ERR_UNSUPPORTED: return "EXW_ERR_UNSUPPORTED: valid but unimplemented combination";
+        case EXW_ERR_CUDA: return "EXW_ERR_CUDA: a CUDA call or kernel launch failed";
+        case EXW_ERR_TIMEOUT: return "EXW_ERR_TIMEOUT: a bounded device-side wait ran out";
+        case EXW_ERR_WORKSPACE: return "EXW_ERR_WORKSPACE: workspace too small or misaligned";
+    }
+    return "EXW_ERR_UNKNOWN";
+}
+
+int exw_version(void) { return 100; }
+
+size_t exw_workspace_bytes(exw_op op, int W, int H, exw_dtype cdt, int nframes, int nfrac) {
+    if (!size_ok(W, H) || !dtype_ok(cdt)) return 0;
+    switch (op) {
+        case EXW_OP_MOTION_BOUNDS:
+        case EXW_OP_FILL_HOLES: return ws_layout(W, H, 1, 1, false).total;
+        case EXW_OP_EXTRAPOLATE:
+            if (nframes < 1 || nfrac < 1 || nfrac > EXW_MAX_FRAC) return 0;
+            return ws_layout(W, H, nframes, nfrac, false).total;
+        case EXW_OP_WARP_BACKWARD: return ws_layout(W, H, 1, 1, true).total;
+    }
+    return 0;
+}
+
+exw_status exw_motion_bounds(const float *depth, const float *mv, int W, int H, float *tile_bounds,
+                             float *frame_bounds, void *ws, size_t ws_bytes, exw_stream_t stream) {
+    if (!size_ok(W, H) || !aligned16(depth) || !aligned16(mv) || !aligned16(frame_bounds) ||
+        (tile_bounds && !aligned16(tile_bounds)))
+        return EXW_ERR_INVALID_ARG;
+    const WsLayout l = ws_layout(W, H, 1, 1, false);
+    if (!aligned16(ws) || ws_bytes < l.total) return EXW_ERR_WORKSPACE;
+    if (entry_check() != EXW_OK) return EXW_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    char *b = (char *)ws;
+    FrameHeader *fh = (FrameHeader *)(b + l.headers);
+    float4 *tb = tile_bounds ? (float4 *)tile_bounds : (float4 *)(b + l.tile_bounds);
+    cudaError_t e = launch_zero(ws, l.headers + sizeof(FrameHeader), s);
+    if (e == cudaSuccess) e = launch_bounds(depth, mv, W, H, tb, fh, s);
+    if (e == cudaSuccess) e = launch_bounds_finalize(fh, frame_bounds, s);
+    return from_cuda(e);
+}
+
+exw_status exw_splat_motion(const float *depth, const float *mv, int W, int H, int k, int denom, uint64_t *keys,
+                            exw_stream_t stream) {
+    const int L = log2_pow2(denom);
+    if (!size_ok(W, H) || L < 0 || k < 0 || k > denom || !aligned16(depth) || !aligned16(mv) || !aligned16(keys))
+        return EXW_ERR_INVALID_ARG;
+    if (entry_check() != EXW_OK) return EXW_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = launch_clear_keys(keys, (size_t)W * H, s);
+    if (e == cudaSuccess) e = launch_splat_global(depth, mv, W, H, k, L, keys, s);
+    return from_cuda(e);
+}
+
+exw_status exw_warp(const void *color, exw_dtype cdt, const float *depth, const float *mv, const uint64_t *keys,
+                    int W, int H, int k, int denom, void *out_color, uint8_t *mask, exw_stream_t stream) {
+    const int L = log2_pow2(denom);
+    if (!size_ok(W, H) || L < 0 || k < 0 || k > denom || !dtype_ok(cdt) || !aligned16(color) || !aligned16(depth) ||
+        !aligned16(mv) || !aligned16(keys) || !aligned16(out_color) || !aligned16(mask))
+        return EXW_ERR_INVALID_ARG;
+    if (entry_check() != EXW_OK) return EXW_ERR_CUDA;
+    TileParams p{};
+    p.color = color;
+    p.depth = depth;
+    p.mv = mv;
+    p.keys = keys;
+    p.W = W;
+    p.H = H;
+    p.nfrac = 1;
+    p.L = L;
+    p.k0 = k;
+    p.out_color[0] = out_color;
+    p.out_mask[0] = mask;
+    p.n5x = ceil_div(W, 32);
+    p.n5y = ceil_div(H, 32);
+    return from_cuda(launch_warp_tiles(p, cdt, (cudaStream_t)stream));
+}
+
+exw_status exw_fill_holes(void *color, exw_dtype cdt, const uint8_t *mask, int W, int H, void *ws, size_t ws_bytes,
+                          exw_stream_t stream) {
+    if (!size_ok(W, H) || !dtype_ok(cdt) || !aligned16(color) || !aligned16(mask)) return EXW_ERR_INVALID_ARG;
+    const WsLayout l = ws_layout(W, H, 1, 1, false);
+    if (!aligned16(ws) || ws_bytes < l.total) return EXW_ERR_WORKSPACE;
+    if (entry_check() != EXW_OK) return EXW_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    TileParams p = tile_params(l, ws, W, H, 1, 0, 0, 0);
+    p.mask_in = mask;
+    p.out_color[0] = color;
+    cudaError_t e = launch_zero(ws, l.headers + sizeof(FrameHeader), s);
+    if (e == cudaSuccess) e = launch_fill_tiles(p, cdt, s);
+    if (e == cudaSuccess) e = launch_fixup(p, cdt, s);
+    return from_cuda(e);
+}
+
+exw_status exw_extrapolate(const exw_frame *frames, int nframes, int nfrac, unsigned flags, exw_frame_out *out,
+                           void *ws, size_t ws_bytes, exw_stream_t stream) {
+    if (frames == nullptr || out == nullptr || nframes < 1 || nfrac < 1 || nfrac > EXW_MAX_FRAC ||
+        (flags & ~EXW_FLAG_NO_FILL) != 0)
+        return EXW_ERR_INVALID_ARG;
+    const int W = frames[0].W, H = frames[0].H;
+    const exw_dtype cdt = frames[0].cdt;
+    if (!size_ok(W, H) || !dtype_ok(cdt)) return EXW_ERR_INVALID_ARG;
+    for (int f = 0; f < nframes; ++f) {
+        const exw_frame &fr = frames[f];
+        if (fr.W != W || fr.H != H || fr.cdt != cdt || !aligned16(fr.color) || !aligned16(fr.depth) ||
+            !aligned16(fr.mv))
+            return EXW_ERR_INVALID_ARG;
+        for (int j = 0; j < nfrac; ++j) {
+            const exw_frame_out &o = out[(size_t)f * nfrac + j];
+            if (!aligned16(o.color) || !aligned16(o.mask)) return EXW_ERR_INVALID_ARG;
+        }
+    }
+    const WsLayout l = ws_layout(W, H, nframes, nfrac, false);
+    if (!aligned16(ws) || ws_bytes < l.total) return EXW_ERR_WORKSPACE;
+    if (entry_check() != EXW_OK) return EXW_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool fill = (flags & EXW_FLAG_NO_FILL) == 0;
+    cudaError_t e = launch_zero(ws, l.headers + (size_t)nframes * sizeof(FrameHeader), s);
+    for (int f = 0; f < nframes && e == cudaSuccess; ++f) {
+        TileParams p = tile_params(l, ws, W, H, nfrac, 2, 1, f);
+        p.color = frames[f].color;
+        p.depth = frames[f].depth;
+        p.mv = frames[f].mv;
+        for (int j = 0; j < nfrac; ++j) {
+            p.out_color[j] = out[(size_t)f * nfrac + j].color;
+            p.out_mask[j] = out[(size_t)f * nfrac + j].mask;
+        }
+        e = launch_bounds(p.depth, p.mv, W, H, (float4 *)p.tile_bounds, p.fh, s);
+        if (e == cudaSuccess) e = launch_fused(p, cdt, fill, s);
+        if (e == cudaSuccess && fill) e = launch_fixup(p, cdt, s);
+    }
+    return from_cuda(e);
+}
+
+exw_status exw_warp_backward(const float *grad_out, const void *color, exw_dtype cdt, const float *depth,
+                             const float *mv, const uint64_t *keys, int W, int H, int k, int denom, float *grad_color,
+                             float *grad_mv, void *ws, size_t ws_bytes, exw_stream_t stream) {
+    const int L = log2_pow2(denom);
+    if (!size_ok(W, H) || L < 0 || k < 0 || k > denom || !dtype_ok(cdt) || !aligned16(grad_out) ||
+        !aligned16(color) || !aligned16(depth) || !aligned16(mv) || !aligned16(grad_color) || !aligned16(grad_mv) ||
+        (keys != nullptr && !aligned16(keys)))
+        return EXW_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint64_t *kp = keys;
+    if (kp == nullptr) {
+        const WsLayout l = ws_layout(W, H, 1, 1, true);
+        if (!aligned16(ws) || ws_bytes < l.total) return EXW_ERR_WORKSPACE;
+        if (entry_check() != EXW_OK) return EXW_ERR_CUDA;
+        uint64_t *kw = (uint64_t *)((char *)ws + l.keys);
+        cudaError_t e = launch_clear_keys(kw, (size_t)W * H, s);
+        if (e == cudaSuccess) e = launch_splat_global(depth, mv, W, H, k, L, kw, s);
+        if (e != cudaSuccess) return EXW_ERR_CUDA;
+        kp = kw;
+    } else if (entry_check() != EXW_OK) {
+        return EXW_ERR_CUDA;
+    }
+    return from_cuda(launch_backward(grad_out, color, cdt, depth, mv, kp, W, H, k, L, grad_color, grad_mv, s));
+}
+
+exw_status exw_l2_loss_grad(const void *out, const void *target, exw_dtype cdt, const uint8_t *mask, int W, int H,
+                            float *grad_out, float *loss, exw_stream_t stream) {
+    if (!size_ok(W, H) || !dtype_ok(cdt) || !aligned16(out) || !aligned16(target) || !aligned16(mask) ||
+        !aligned16(grad_out) || loss == nullptr || ((uintptr_t)loss & 3u) != 0)
+        return EXW_ERR_INVALID_ARG;
+    if (entry_check() != EXW_OK) return EXW_ERR_CUDA;
+    return from_cuda(launch_l2_loss(out, target, cdt, mask, W, H, grad_out, loss, (cudaStream_t)stream));
+}
+
+exw_status exw_device_status(const void *ws, exw_stream_t stream) {
+    if (!aligned16(ws)) return EXW_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t v = 0;
+    if (cudaMemcpyAsync(&v, ws, sizeof v, cudaMemcpyDeviceToHost, s) != cudaSuccess) return EXW_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return EXW_ERR_CUDA;
+    return (exw_status)v;
+}
+
+// --- timing --------------------------------------------------------------------------------------------------
+void exw_timing_enable(int on) {
+    std::lock_guard<std::mutex> g(g_tmu);
+    for (auto &t : g_timed) {
+        g_event_pool.push_back(t.start);
+        g_event_pool.push_back(t.stop);
+    }
+    g_timed.clear();
+    g_timing = on != 0;
+}
+
+int exw_timing_query(const char *name, double *total_ms, int *launches) {
+    std::lock_guard<std::mutex> g(g_tmu);
+    double sum = 0.0;
+    int n = 0;
+    for (auto &t : g_timed) {
+        if (t.name != name) continue;
+        if (cudaEventSynchronize(t.stop) != cudaSuccess) return -1;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t.start, t.stop) != cudaSuccess) return -1;
+        sum += ms;
+        ++n;
+    }
+    if (total_ms) *total_ms = sum;
+    if (launches) *launches = n;
+    return n > 0 ? 0 : -1;
+}
+
+size_t exw_timing_names(char *buf, size_t len) {
+    std::lock_guard<std::mutex> g(g_tmu);
+    std::vector<std::string> names;
+    for (auto &t : g_timed) {
+        bool seen = false;
+        for (auto &n : names) seen = seen || n == t.name;
+        if (!seen) names.push_back(t.name);
+    }
+    std::string all;
+    for (size_t i = 0; i < names.size(); ++i) all += (i ? "," : "") + names[i];
+    if (buf && len) {
+        const size_t c = all.size() < len - 1 ? all.size() : len - 1;
+        std::memcpy(buf, all.data(), c);
+        buf[c] = '\0';
+    }
+    return all.size() + 1;
+}
+
+uint64_t exw_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

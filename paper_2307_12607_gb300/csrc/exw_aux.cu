@@ -1,0 +1,202 @@
+// exw_aux.cu -- global-memory splat, motion bounds, workspace clearing and the L2 loss.
+#include "exw_device.cuh"
+#include "exw_internal.h"
+
+namespace exw {
+
+__global__ void clear_keys_kernel(unsigned long long *keys, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        keys[i] = kKeyEmpty;
+}
+
+__global__ void zero_kernel(uint32_t *p, size_t nwords) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nwords; i += (size_t)gridDim.x * blockDim.x)
+        p[i] = 0u;
+}
+
+// Stage (a) into a global key buffer: one thread per source pixel, 64-bit atomicMin at the target.
+__global__ void __launch_bounds__(256) splat_global_kernel(const float *__restrict__ depth,
+                                                           const float *__restrict__ mv, int W, int H, int k, int L,
+                                                           unsigned long long *keys) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= W) return;
+    const size_t plane = (size_t)W * H;
+    const size_t i = (size_t)y * W + x;
+    const uint32_t db = __float_as_uint(__ldg(depth + i));
+    const uint32_t ux = __float_as_uint(__ldg(mv + i)), uy = __float_as_uint(__ldg(mv + plane + i));
+    if (!depth_ok(db) || !finite_bits(ux) || !finite_bits(uy)) return;
+    const AxisStep sx = axis_step(ux, k, L), sy = axis_step(uy, k, L);
+    if (!sx.ok || !sy.ok) return;
+    const int gx = x + sx.off, gy = y + sy.off;
+    if (gx < 0 || gx >= W || gy < 0 || gy >= H) return;
+    atomicMin(keys + (size_t)gy * W + gx, (unsigned long long)pack_key_global(db, (uint32_t)i));
+}
+
+// Stage (a0): per 8x8 tile and per frame, min/max of each motion component over pixels that can land, clamped
+// to [-65536, 65536] (for k/4 fractions, |d| >= 16384 beyond that: no landing in any frame) and -0 read as +0.
+// CTA = 32 x 32 source pixels; lane = x (coalesced rows), warp w covers rows 4w .. 4w+3 (one 8-row tile band).
+__global__ void __launch_bounds__(256) bounds_kernel(const float *__restrict__ depth, const float *__restrict__ mv,
+                                                     int W, int H, float4 *tile_bounds, FrameHeader *fh) {
+    __shared__ float4 part[8][4];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int X0 = blockIdx.x * 32, Y0 = blockIdx.y * 32;
+    const size_t plane = (size_t)W * H;
+    float mnx = __int_as_float(0x7F800000), mxx = -mnx, mny = mnx, mxy = -mnx;
+    const int x = X0 + lane;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int y = Y0 + 4 * w + r;
+        if (x < W && y < H) {
+            const size_t i = (size_t)y * W + x;
+            const uint32_t db = __float_as_uint(__ldg(depth + i));
+            const float fx = __ldg(mv + i), fy = __ldg(mv + plane + i);
+            if (depth_ok(db) && finite_bits(__float_as_uint(fx)) && finite_bits(__float_as_uint(fy))) {
+                const float cx = fminf(fmaxf(fx, -65536.0f), 65536.0f) + 0.0f;
+                const float cy = fminf(fmaxf(fy, -65536.0f), 65536.0f) + 0.0f;
+                mnx = fminf(mnx, cx);
+                mxx = fmaxf(mxx, cx);
+                mny = fminf(mny, cy);
+                mxy = fmaxf(mxy, cy);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        mnx = fminf(mnx, __shfl_xor_sync(0xFFFFFFFFu, mnx, o));
+        mxx = fmaxf(mxx, __shfl_xor_sync(0xFFFFFFFFu, mxx, o));
+        mny = fminf(mny, __shfl_xor_sync(0xFFFFFFFFu, mny, o));
+        mxy = fmaxf(mxy, __shfl_xor_sync(0xFFFFFFFFu, mxy, o));
+    }
+    if ((lane & 7) == 0) part[w][lane >> 3] = make_float4(mnx, mxx, mny, mxy);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int t = threadIdx.x;
+        float4 b = make_float4(__int_as_float(0x7F800000), __int_as_float(0xFF800000), __int_as_float(0x7F800000),
+                               __int_as_float(0xFF800000));
+        if (t < 16) {
+            const int bxl = t & 3, byl = t >> 2;
+            const float4 u = part[2 * byl][bxl], v = part[2 * byl + 1][bxl];
+            b = make_float4(fminf(u.x, v.x), fmaxf(u.y, v.y), fminf(u.z, v.z), fmaxf(u.w, v.w));
+            const int gbx = X0 / 8 + bxl, gby = Y0 / 8 + byl;
+            const int nbx = (W + 7) / 8, nby = (H + 7) / 8;
+            if (gbx < nbx && gby < nby) tile_bounds[(size_t)gby * nbx + gbx] = b;
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            b.x = fminf(b.x, __shfl_xor_sync(0xFFFFFFFFu, b.x, o));
+            b.y = fmaxf(b.y, __shfl_xor_sync(0xFFFFFFFFu, b.y, o));
+            b.z = fminf(b.z, __shfl_xor_sync(0xFFFFFFFFu, b.z, o));
+            b.w = fmaxf(b.w, __shfl_xor_sync(0xFFFFFFFFu, b.w, o));
+        }
+        if (t == 0 && b.x <= b.y) {
+            atomicMax(&fh->acc[0], float_order(-b.x));
+            atomicMax(&fh->acc[1], float_order(b.y));
+            atomicMax(&fh->acc[2], float_order(-b.z));
+            atomicMax(&fh->acc[3], float_order(b.w));
+        }
+    }
+}
+
+__global__ void bounds_finalize_kernel(const FrameHeader *fh, float *out) {
+    if (threadIdx.x != 0) return;
+    if (fh->acc[1] == 0u) {
+        out[0] = __int_as_float(0x7F800000);
+        out[1] = __int_as_float(0xFF800000);
+        out[2] = __int_as_float(0x7F800000);
+        out[3] = __int_as_float(0xFF800000);
+        return;
+    }
+    out[0] = -float_unorder(fh->acc[0]);
+    out[1] = float_unorder(fh->acc[1]);
+    out[2] = -float_unorder(fh->acc[2]);
+    out[3] = float_unorder(fh->acc[3]);
+}
+
+template <typename CT>
+__global__ void __launch_bounds__(256) l2_loss_kernel(const CT *__restrict__ out, const CT *__restrict__ target,
+                                                      const uint8_t *__restrict__ mask, size_t n, float *grad,
+                                                      float *loss) {
+    __shared__ float red[8];
+    float acc = 0.0f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const bool valid = __ldg(mask + i) == 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float d = load_c<CT>(out + c * n + i) - load_c<CT>(target + c * n + i);
+            grad[c * n + i] = valid ? 2.0f * d : 0.0f;
+            if (valid) acc += d * d;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        if (threadIdx.x == 0) atomicAdd(loss, v);
+    }
+}
+
+static unsigned grid_for(size_t n, unsigned per_block) {
+    size_t g = (n + per_block - 1) / per_block;
+    if (g > 8192) g = 8192;
+    return (unsigned)(g ? g : 1);
+}
+
+cudaError_t launch_clear_keys(uint64_t *keys, size_t n, cudaStream_t s) {
+    timing_begin("exw_clear_keys", s);
+    clear_keys_kernel<<<grid_for(n, 256 * 4), 256, 0, s>>>((unsigned long long *)keys, n);
+    count_launch();
+    timing_end("exw_clear_keys", s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero(void *p, size_t bytes, cudaStream_t s) {
+    const size_t words = bytes / 4;
+    zero_kernel<<<grid_for(words, 256 * 4), 256, 0, s>>>((uint32_t *)p, words);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_splat_global(const float *depth, const float *mv, int W, int H, int k, int L, uint64_t *keys,
+                                cudaStream_t s) {
+    const dim3 g((unsigned)((W + 255) / 256), (unsigned)H, 1);
+    timing_begin("exw_splat_global", s);
+    splat_global_kernel<<<g, 256, 0, s>>>(depth, mv, W, H, k, L, (unsigned long long *)keys);
+    count_launch();
+    timing_end("exw_splat_global", s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bounds(const float *depth, const float *mv, int W, int H, float4 *tile_bounds, FrameHeader *fh,
+                          cudaStream_t s) {
+    const dim3 g((unsigned)ceil_div(W, 32), (unsigned)ceil_div(H, 32), 1);
+    timing_begin("exw_bounds", s);
+    bounds_kernel<<<g, 256, 0, s>>>(depth, mv, W, H, tile_bounds, fh);
+    count_launch();
+    timing_end("exw_bounds", s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bounds_finalize(const FrameHeader *fh, float *frame_bounds, cudaStream_t s) {
+    bounds_finalize_kernel<<<1, 32, 0, s>>>(fh, frame_bounds);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_l2_loss(const void *out, const void *target, exw_dtype cdt, const uint8_t *mask, int W, int H,
+                           float *grad_out, float *loss, cudaStream_t s) {
+    const size_t n = (size_t)W * H;
+    const unsigned g = grid_for(n, 256 * 4);
+    timing_begin("exw_l2_loss", s);
+    if (cdt == EXW_F32)
+        l2_loss_kernel<float><<<g, 256, 0, s>>>((const float *)out, (const float *)target, mask, n, grad_out, loss);
+    else
+        l2_loss_kernel<__half><<<g, 256, 0, s>>>((const __half *)out, (const __half *)target, mask, n, grad_out,
+                                                 loss);
+    count_launch();
+    timing_end("exw_l2_loss", s);
+    return cudaGetLastError();
+}
+
+}  // namespace exw

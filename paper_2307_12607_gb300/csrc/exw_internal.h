@@ -1,0 +1,114 @@
+// exw_internal.h -- workspace layout and kernel launchers shared by the translation units of libexw.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/exw.h"
+
+namespace exw {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// Per-frame bookkeeping, zeroed at the start of every call that uses it.
+struct FrameHeader {
+    uint32_t acc[4];       // ordered-float maxima of -min mv_x, max mv_x, -min mv_y, max mv_y (0 = none)
+    uint32_t done;         // CTAs that finished the tile pass (the last one runs the coarse pyramid)
+    uint32_t ninvalid[3];  // fill tiles without any valid pixel, per fraction
+    uint32_t status;       // EXW_OK or an error found on the device
+    uint32_t pad[7];
+};
+static_assert(sizeof(FrameHeader) == 64, "FrameHeader is 64 bytes");
+
+// Byte offsets of the workspace sections for nframes frames of W x H with nfrac fractions.
+struct WsLayout {
+    size_t headers, tile_bounds, nodes, list, fillval, coarse, keys, total;
+    int nbx, nby;       // motion-bounds tiles
+    int n5x, n5y;       // fill tiles (level-5 nodes of the pyramid)
+    int ncoarse;        // pyramid nodes above level 5, per fraction
+};
+
+inline int coarse_nodes(int n5x, int n5y) {
+    int total = 0;
+    while (n5x > 1 || n5y > 1) {
+        n5x = (n5x + 1) / 2;
+        n5y = (n5y + 1) / 2;
+        total += n5x * n5y;
+    }
+    return total;
+}
+
+inline WsLayout ws_layout(int W, int H, int nframes, int nfrac, bool with_keys) {
+    WsLayout l{};
+    l.nbx = ceil_div(W, 8);
+    l.nby = ceil_div(H, 8);
+    l.n5x = ceil_div(W, 32);
+    l.n5y = ceil_div(H, 32);
+    l.ncoarse = coarse_nodes(l.n5x, l.n5y);
+    const size_t n5 = (size_t)l.n5x * l.n5y;
+    size_t off = kAlign;  // first 256 bytes: global status word
+    l.headers = off;
+    off += align_up((size_t)nframes * sizeof(FrameHeader));
+    l.tile_bounds = off;
+    off += align_up((size_t)l.nbx * l.nby * 16);
+    l.nodes = off;
+    off += align_up((size_t)nfrac * n5 * 16);
+    l.list = off;
+    off += align_up((size_t)nfrac * n5 * 4);
+    l.fillval = off;
+    off += align_up((size_t)nfrac * n5 * 16);
+    l.coarse = off;
+    off += align_up((size_t)nfrac * (size_t)(l.ncoarse > 0 ? l.ncoarse : 1) * 16);
+    l.keys = off;
+    if (with_keys) off += align_up((size_t)W * H * 8);
+    l.total = off;
+    return l;
+}
+
+// Parameters of the per-tile passes (stage (b)+(c) on 32 x 32 tiles).
+struct TileParams {
+    const void *color;          // source colour (fused/warp) or in-out colour (fill)
+    const float *depth;
+    const float *mv;
+    const uint64_t *keys;       // staged warp: global keys
+    const uint8_t *mask_in;     // staged fill: input mask
+    int W, H, nfrac, L, k0;     // fractions k0 .. k0 + nfrac - 1 of 2^L
+    void *out_color[3];
+    uint8_t *out_mask[3];
+    const float4 *tile_bounds;
+    int nbx, nby;
+    FrameHeader *fh;
+    float4 *nodes;              // [nfrac][n5]
+    uint32_t *list;             // [nfrac][n5]
+    float4 *fillval;            // [nfrac][n5]
+    float4 *coarse;             // [nfrac][ncoarse]
+    int n5x, n5y, ncoarse;
+};
+
+// Launchers (exw_fwd.cu, exw_aux.cu, exw_bwd.cu).  Each returns the launch error.
+cudaError_t launch_clear_keys(uint64_t *keys, size_t n, cudaStream_t s);
+cudaError_t launch_zero(void *p, size_t bytes, cudaStream_t s);
+cudaError_t launch_splat_global(const float *depth, const float *mv, int W, int H, int k, int L, uint64_t *keys,
+                                cudaStream_t s);
+cudaError_t launch_bounds(const float *depth, const float *mv, int W, int H, float4 *tile_bounds, FrameHeader *fh,
+                          cudaStream_t s);
+cudaError_t launch_bounds_finalize(const FrameHeader *fh, float *frame_bounds, cudaStream_t s);
+cudaError_t launch_fused(const TileParams &p, exw_dtype cdt, bool fill, cudaStream_t s);
+cudaError_t launch_warp_tiles(const TileParams &p, exw_dtype cdt, cudaStream_t s);
+cudaError_t launch_fill_tiles(const TileParams &p, exw_dtype cdt, cudaStream_t s);
+cudaError_t launch_fixup(const TileParams &p, exw_dtype cdt, cudaStream_t s);
+cudaError_t launch_l2_loss(const void *out, const void *target, exw_dtype cdt, const uint8_t *mask, int W, int H,
+                           float *grad_out, float *loss, cudaStream_t s);
+cudaError_t launch_backward(const float *grad_out, const void *color, exw_dtype cdt, const float *depth,
+                            const float *mv, const uint64_t *keys, int W, int H, int k, int L, float *grad_color,
+                            float *grad_mv, cudaStream_t s);
+
+// Timing hooks (exw_api.cu): bracket a launch with events when timing is enabled.
+void timing_begin(const char *name, cudaStream_t s);
+void timing_end(const char *name, cudaStream_t s);
+void count_launch();
+
+}  // namespace exw

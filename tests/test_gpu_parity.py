@@ -1,0 +1,358 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle on the same seeded inputs.
+
+Bars: splat keys, hole masks and motion bounds bit-exact; colour within 2e-6 absolute for float32 storage and 1e-3
+for float16 storage (values in [0, 1]); gradients within 1e-5 absolute + 1e-4 relative.  The float32 colour bar
+covers the float32 gather (a few ulp of a value <= 1) and the float32 pull-push pyramid (one rounding per level
+and at most 14 levels), against the oracle's float64.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_2307_12607_gb300 import scenes  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = {torch.float32: 2e-6, torch.float16: 1e-3}
+NPDT = {torch.float32: np.float32, torch.float16: np.float16}
+
+
+@pytest.fixture(scope="module")
+def b():
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA GPU is required for the gpu-marked tests")
+    from paper_2307_12607_gb300 import build, binding
+    build.build()
+    return binding
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def keys_np(t):
+    return t.cpu().numpy().view(np.uint64)
+
+
+def frame_case(name):
+    """Named small inputs: (colour float32 [3][H][W], depth, mv)."""
+    kind, W, H, seed = name
+    if kind == "scene":
+        s = scenes.make_scene(W, H, seed, 6, vmax=6.0, pan_max=2.0, sliver_fraction=0.2)
+        return scenes.render(s, 0.0)
+    if kind == "ties":
+        return scenes.random_frame(W, H, seed, depth_levels=2, mv_scale=3.0, quarter_grid=True, invalid_fraction=0.05)
+    if kind == "invalid":
+        return scenes.random_frame(W, H, seed, depth_levels=0, mv_scale=6.0, invalid_fraction=0.3)
+    return scenes.random_frame(W, H, seed, mv_scale=4.0)
+
+
+CASES = [("rand", 8, 8, 1), ("ties", 37, 29, 2), ("invalid", 64, 64, 3), ("rand", 1, 1, 4), ("rand", 1, 50, 5),
+         ("rand", 50, 1, 6), ("scene", 257, 131, 7), ("ties", 100, 70, 8), ("scene", 640, 360, 9)]
+
+
+def as_storage(color, dtype):
+    return color.astype(NPDT[dtype])
+
+
+# ------------------------------------------------------------------------------------------------------------
+# (a) splat, (a0) bounds
+# ------------------------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", CASES)
+def test_splat_keys_bit_exact(b, case):
+    _, depth, mv = frame_case(case)
+    d, m = dev(depth), dev(mv)
+    for k, denom in [(0, 4), (1, 4), (2, 4), (3, 4), (4, 4), (1, 2), (3, 8), (5, 8), (37, 64), (1, 1)]:
+        got = keys_np(b.exw_splat_motion(d, m, k, denom))
+        want = oracle.splat(depth, mv, k, denom)
+        np.testing.assert_array_equal(got, want, err_msg=f"{case} k={k}/{denom}")
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_motion_bounds_bit_exact(b, case):
+    _, depth, mv = frame_case(case)
+    mv = mv.copy()
+    mv[0].flat[0] = 1e7   # clamped
+    tiles, frame = b.exw_motion_bounds(dev(depth), dev(mv))
+    wt, wf = oracle.motion_bounds(depth, mv, 8)
+    np.testing.assert_array_equal(tiles.cpu().numpy().view(np.uint32), wt.view(np.uint32))
+    np.testing.assert_array_equal(frame.cpu().numpy().view(np.uint32), wf.view(np.uint32))
+
+
+# ------------------------------------------------------------------------------------------------------------
+# (b) staged warp
+# ------------------------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
+@pytest.mark.parametrize("case", CASES)
+def test_warp_matches_oracle(b, case, dtype):
+    color, depth, mv = frame_case(case)
+    cs = as_storage(color, dtype)
+    c, d, m = dev(cs), dev(depth), dev(mv)
+    for k in (1, 2, 3):
+        keys = b.exw_splat_motion(d, m, k, 4)
+        out, mask = b.exw_warp(c, d, m, keys, k, 4)
+        wo, wm = oracle.warp(cs.astype(np.float64), depth, mv, keys_np(keys), k, 4)
+        np.testing.assert_array_equal(mask.cpu().numpy(), wm, err_msg=f"{case} k={k}")
+        got = out.float().cpu().numpy().astype(np.float64)
+        np.testing.assert_allclose(got, wo, rtol=0, atol=TOL[dtype], err_msg=f"{case} k={k}")
+        assert np.all(got[:, wm != 0] == 0.0)
+
+
+# ------------------------------------------------------------------------------------------------------------
+# (c) staged fill
+# ------------------------------------------------------------------------------------------------------------
+
+def fill_inputs(kind, W, H, seed):
+    rng = np.random.default_rng(seed)
+    color = rng.uniform(size=(3, H, W)).astype(np.float32)
+    if kind == "none":
+        mask = np.zeros((H, W), np.uint8)
+    elif kind == "all":
+        mask = np.ones((H, W), np.uint8)
+    elif kind == "single":
+        mask = np.ones((H, W), np.uint8)
+        mask[rng.integers(H), rng.integers(W)] = 0
+    elif kind == "blobs":           # large holes: whole 32x32 tiles without a valid pixel
+        mask = np.zeros((H, W), np.uint8)
+        for _ in range(6):
+            y, x = rng.integers(H), rng.integers(W)
+            mask[y:y + rng.integers(20, 120), x:x + rng.integers(20, 120)] = 2
+    else:
+        mask = (rng.uniform(size=(H, W)) < 0.4).astype(np.uint8)
+    color[:, mask != 0] = 0.0
+    return color, mask
+
+
+FILL_CASES = [("none", 40, 30, 1), ("all", 70, 33, 2), ("single", 100, 90, 3), ("blobs", 300, 200, 4),
+              ("random", 1, 1, 5), ("random", 33, 33, 6), ("blobs", 1000, 37, 7), ("single", 5, 700, 8),
+              ("blobs", 1920, 1080, 9)]
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
+@pytest.mark.parametrize("case", FILL_CASES)
+def test_fill_matches_oracle(b, case, dtype):
+    color, mask = fill_inputs(*case)
+    cs = as_storage(color, dtype)
+    c = dev(cs)
+    b.exw_fill_holes(c, dev(mask))
+    got = c.float().cpu().numpy().astype(np.float64)
+    want = oracle.fill_holes(cs.astype(np.float64), mask)
+    np.testing.assert_allclose(got, want, rtol=0, atol=TOL[dtype], err_msg=str(case))
+    valid = mask == 0
+    np.testing.assert_array_equal(got[:, valid], cs.astype(np.float64)[:, valid])   # valid pixels untouched
+
+
+# ------------------------------------------------------------------------------------------------------------
+# fused (a0)+(a)+(b)+(c)
+# ------------------------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("fill", [True, False])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
+@pytest.mark.parametrize("case", CASES)
+def test_extrapolate_matches_oracle_and_staged(b, case, dtype, fill):
+    color, depth, mv = frame_case(case)
+    cs = as_storage(color, dtype)
+    c, d, m = dev(cs), dev(depth), dev(mv)
+    out, mask = b.exw_extrapolate(c, d, m, nfrac=3, fill=fill)
+    ref = oracle.extrapolate(cs.astype(np.float64), depth, mv, 3, storage=NPDT[dtype], fill=fill)
+    for j, (wo, wm, wk) in enumerate(ref):
+        np.testing.assert_array_equal(mask[j].cpu().numpy(), wm, err_msg=f"{case} k={j + 1}")
+        np.testing.assert_allclose(out[j].float().cpu().numpy().astype(np.float64), wo, rtol=0, atol=TOL[dtype],
+                                   err_msg=f"{case} k={j + 1}")
+        # the fused pass is bit-identical to the staged entry points
+        keys = b.exw_splat_motion(d, m, j + 1, 4)
+        np.testing.assert_array_equal(keys_np(keys), wk)
+        so, sm = b.exw_warp(c, d, m, keys, j + 1, 4)
+        if fill:
+            b.exw_fill_holes(so, sm)
+        assert torch.equal(sm, mask[j])
+        assert torch.equal(so.view(torch.int16 if dtype == torch.float16 else torch.int32),
+                           out[j].view(torch.int16 if dtype == torch.float16 else torch.int32))
+
+
+def test_extrapolate_fewer_fractions_and_sequences(b):
+    frames = [frame_case(("scene", 96, 64, s)) for s in range(4)]
+    c = dev(np.stack([f[0] for f in frames]))
+    d = dev(np.stack([f[1] for f in frames]))
+    m = dev(np.stack([f[2] for f in frames]))
+    for nfrac in (1, 2, 3):
+        out, mask = b.exw_extrapolate(c, d, m, nfrac=nfrac)
+        assert out.shape == (4, nfrac, 3, 64, 96)
+        for f in range(4):
+            single, smask = b.exw_extrapolate(c[f], d[f], m[f], nfrac=nfrac)
+            assert torch.equal(single, out[f]) and torch.equal(smask, mask[f])
+
+
+# ------------------------------------------------------------------------------------------------------------
+# edge cases
+# ------------------------------------------------------------------------------------------------------------
+
+def test_no_valid_source_pixel(b):
+    color, depth, mv = scenes.random_frame(70, 45, 1)
+    depth[...] = np.nan
+    out, mask = b.exw_extrapolate(dev(color), dev(depth), dev(mv))
+    assert torch.all(mask == b.MASK_EMPTY)
+    assert torch.all(out == 0)
+
+
+def test_huge_and_nonfinite_motion_never_lands(b):
+    color, depth, mv = scenes.random_frame(64, 40, 2, mv_scale=2.0)
+    mv[0, :10] = 1e30
+    mv[1, 10:20] = -3e38
+    mv[0, 20:25] = np.nan
+    mv[1, 25:30] = np.inf
+    c, d, m = dev(color), dev(depth), dev(mv)
+    out, mask = b.exw_extrapolate(c, d, m)
+    ref = oracle.extrapolate(color.astype(np.float64), depth, mv, 3)
+    for j, (wo, wm, wk) in enumerate(ref):
+        np.testing.assert_array_equal(mask[j].cpu().numpy(), wm)
+        np.testing.assert_allclose(out[j].cpu().numpy(), wo, rtol=0, atol=2e-6)
+
+
+def test_max_width_row(b):
+    W, H = 16384, 2
+    color, depth, mv = scenes.random_frame(W, H, 3, mv_scale=40.0)
+    out, mask = b.exw_extrapolate(dev(color), dev(depth), dev(mv))
+    ref = oracle.extrapolate(color.astype(np.float64), depth, mv, 3)
+    for j, (wo, wm, _) in enumerate(ref):
+        np.testing.assert_array_equal(mask[j].cpu().numpy(), wm)
+        np.testing.assert_allclose(out[j].cpu().numpy(), wo, rtol=0, atol=2e-6)
+
+
+def test_large_motion_search_window(b):
+    # one fast pixel widens the frame bounds; every tile's candidate scan must still find the right sources
+    color, depth, mv = scenes.random_frame(300, 200, 4, mv_scale=1.0)
+    mv[:, 100, 150] = (250.0, -170.0)
+    out, mask = b.exw_extrapolate(dev(color), dev(depth), dev(mv), fill=False)
+    ref = oracle.extrapolate(color.astype(np.float64), depth, mv, 3, fill=False)
+    for j, (wo, wm, _) in enumerate(ref):
+        np.testing.assert_array_equal(mask[j].cpu().numpy(), wm)
+        np.testing.assert_allclose(out[j].cpu().numpy(), wo, rtol=0, atol=2e-6)
+
+
+def test_invalid_arguments_raise(b):
+    d = torch.ones(8, 8, device="cuda")
+    m = torch.zeros(2, 8, 8, device="cuda")
+    with pytest.raises(b.ExwError) as e:
+        b.exw_splat_motion(d, m, 5, 4)
+    assert e.value.status == 1
+    with pytest.raises(b.ExwError):
+        b.exw_splat_motion(d, m, 1, 3)
+
+
+# ------------------------------------------------------------------------------------------------------------
+# adjoint
+# ------------------------------------------------------------------------------------------------------------
+
+def grad_close(got, want):
+    got = got.astype(np.float64)
+    err = np.abs(got - want)
+    bound = 1e-5 + 1e-4 * np.abs(want)
+    assert np.all(err <= bound), f"max excess {np.max(err - bound)} at {np.unravel_index(np.argmax(err - bound), err.shape)}"
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
+@pytest.mark.parametrize("case", [("ties", 37, 29, 11), ("scene", 257, 131, 12), ("rand", 64, 48, 13),
+                                  ("invalid", 40, 40, 14)])
+def test_backward_matches_oracle(b, case, dtype):
+    color, depth, mv = frame_case(case)
+    cs = as_storage(color, dtype)
+    c, d, m = dev(cs), dev(depth), dev(mv)
+    rng = np.random.default_rng(case[3])
+    H, W = depth.shape
+    for k in (1, 2, 3):
+        g = rng.standard_normal((3, H, W)).astype(np.float32)
+        keys = b.exw_splat_motion(d, m, k, 4)
+        gc, gm = b.exw_warp_backward(dev(g), c, d, m, keys, k, 4)
+        wc, wmv = oracle.warp_backward(g, cs.astype(np.float64), depth, mv, keys_np(keys), k, 4)
+        grad_close(gc.cpu().numpy(), wc)
+        grad_close(gm.cpu().numpy(), wmv)
+        # recomputed keys (checkpointing) give bit-identical gradients; accumulation adds
+        gc2, gm2 = b.exw_warp_backward(dev(g), c, d, m, None, k, 4)
+        assert torch.equal(gc2, gc) and torch.equal(gm2, gm)
+        b.exw_warp_backward(dev(g), c, d, m, keys, k, 4, grad_color=gc2, grad_mv=gm2)
+        assert torch.equal(gc2, 2 * gc) and torch.equal(gm2, 2 * gm)
+
+
+def test_autograd_function_and_loss(b):
+    from paper_2307_12607_gb300 import autograd
+    color, depth, mv = frame_case(("scene", 160, 96, 21))
+    H, W = depth.shape
+    target = np.random.default_rng(0).uniform(size=(3, H, W)).astype(np.float32)
+    k = 3
+    for checkpoint in (True, False):
+        c = dev(color).requires_grad_(True)
+        m = dev(mv).requires_grad_(True)
+        out, mask = autograd.warp(c, dev(depth), m, k, 4, checkpoint=checkpoint)
+        loss = (((out - dev(target)) ** 2) * (mask == 0)).sum()
+        loss.backward()
+        keys = oracle.splat(depth, mv, k)
+        wo, wm = oracle.warp(color.astype(np.float64), depth, mv, keys, k)
+        wl, wg = oracle.l2_loss_grad(wo, target, wm)
+        wc, wmv = oracle.warp_backward(wg, color.astype(np.float64), depth, mv, keys, k)
+        assert abs(loss.item() - wl) <= 1e-4 * max(1.0, abs(wl))
+        grad_close(c.grad.cpu().numpy(), wc)
+        grad_close(m.grad.cpu().numpy(), wmv)
+    # the library's own loss kernel agrees
+    keys = b.exw_splat_motion(dev(depth), dev(mv), k, 4)
+    out, mask = b.exw_warp(dev(color), dev(depth), dev(mv), keys, k, 4)
+    lv, g = b.exw_l2_loss_grad(out, dev(target), mask)
+    assert abs(lv.item() - wl) <= 1e-4 * max(1.0, abs(wl))
+    np.testing.assert_allclose(g.cpu().numpy(), wg, rtol=0, atol=2e-6)
+
+
+# ------------------------------------------------------------------------------------------------------------
+# full-size workloads, in the launch configuration the benchmark times
+# ------------------------------------------------------------------------------------------------------------
+
+def test_full_size_4k_fp16(b):
+    s = scenes.frame_4k_scene()
+    color, depth, mv = scenes.render(s, 0.0, np.float16)
+    c, d, m = dev(color), dev(depth), dev(mv)
+    for fill in (False, True):
+        out, mask = b.exw_extrapolate(c, d, m, nfrac=3, fill=fill)
+        ref = oracle.extrapolate(color.astype(np.float64), depth, mv, 3, storage=np.float16, fill=fill)
+        for j, (wo, wm, _) in enumerate(ref):
+            np.testing.assert_array_equal(mask[j].cpu().numpy(), wm)
+            np.testing.assert_allclose(out[j].float().cpu().numpy().astype(np.float64), wo, rtol=0, atol=1e-3)
+        assert (mask != 0).float().mean().item() > 0.01      # the occluders open real holes
+
+
+def test_full_size_1080p_sequence_sampled(b):
+    s = scenes.sequence_1080p_scene()
+    F = 60
+    H, W = s.H, s.W
+    c = torch.empty((F, 3, H, W), dtype=torch.float32, device="cuda")
+    d = torch.empty((F, H, W), dtype=torch.float32, device="cuda")
+    m = torch.empty((F, 2, H, W), dtype=torch.float32, device="cuda")
+    check = {0: None, 31: None, 59: None}
+    for f in range(F):
+        col, dep, mv = scenes.render(s, float(f))
+        c[f].copy_(torch.from_numpy(col))
+        d[f].copy_(torch.from_numpy(dep))
+        m[f].copy_(torch.from_numpy(mv))
+        if f in check:
+            check[f] = (col, dep, mv)
+    out, mask = b.exw_extrapolate(c, d, m, nfrac=3)
+    for f, (col, dep, mv) in check.items():
+        ref = oracle.extrapolate(col.astype(np.float64), dep, mv, 3)
+        for j, (wo, wm, _) in enumerate(ref):
+            np.testing.assert_array_equal(mask[f, j].cpu().numpy(), wm, err_msg=f"frame {f} k={j + 1}")
+            np.testing.assert_allclose(out[f, j].cpu().numpy(), wo, rtol=0, atol=2e-6)
+
+
+def test_timing_and_launch_count(b):
+    color, depth, mv = frame_case(("scene", 128, 96, 30))
+    n0 = b.exw_launch_count()
+    b.exw_timing_enable(True)
+    b.exw_extrapolate(dev(color), dev(depth), dev(mv))
+    torch.cuda.synchronize()
+    assert "exw_fused" in b.exw_timing_names()
+    ms, n = b.exw_timing_query("exw_fused")
+    assert n == 1 and ms > 0
+    b.exw_timing_enable(False)
+    assert b.exw_launch_count() - n0 == 4   # zero, bounds, fused, fixup
