@@ -26,9 +26,10 @@
  *     (1,1)); holes take the value of their first valid ancestor; valid pixels are unchanged.
  *
  * Conventions for every entry point:
- *   - All image pointers are DEVICE pointers to dense planar arrays with a 16-byte aligned base:
+ *   - All image pointers are DEVICE pointers to dense planar arrays aligned to their element size:
  *       colour [3][H][W] (float32 or float16, exw_dtype), depth [H][W] float32, motion [2][H][W] float32 (plane 0
  *       = x, pixels / frame), keys [H][W] uint64, mask [H][W] uint8.  Pixel (x, y) has index y * W + x.
+ *       Workspaces and tile_bounds must be 16-byte aligned.
  *   - Sizes: 1 <= W, H <= 16384.  Fractions: denom is a power of two in [1, 64] and 0 <= k <= denom.
  *   - A source pixel whose depth is not positive and finite, or whose motion is not finite, never lands.
  *   - Work is enqueued on the caller's CUDA stream (`stream`, a cudaStream_t; NULL = legacy default stream) and

@@ -54,7 +54,9 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 // ------------------------------------------------------------------------------------------------------------
 // Argument checks
 // ------------------------------------------------------------------------------------------------------------
-static bool aligned16(const void *p) { return p != nullptr && ((uintptr_t)p & 15u) == 0; }
+static bool aligned(const void *p, uintptr_t a) { return p != nullptr && ((uintptr_t)p & (a - 1)) == 0; }
+static bool aligned16(const void *p) { return aligned(p, 16); }
+static uintptr_t csize(exw_dtype d) { return d == EXW_F16 ? 2 : 4; }
 static bool size_ok(int W, int H) { return W >= 1 && H >= 1 && W <= 16384 && H <= 16384; }
 static bool dtype_ok(exw_dtype d) { return d == EXW_F32 || d == EXW_F16; }
 static int log2_pow2(int d) {
@@ -123,7 +125,7 @@ size_t exw_workspace_bytes(exw_op op, int W, int H, exw_dtype cdt, int nframes, 
 
 exw_status exw_motion_bounds(const float *depth, const float *mv, int W, int H, float *tile_bounds,
                              float *frame_bounds, void *ws, size_t ws_bytes, exw_stream_t stream) {
-    if (!size_ok(W, H) || !aligned16(depth) || !aligned16(mv) || !aligned16(frame_bounds) ||
+    if (!size_ok(W, H) || !aligned(depth, 4) || !aligned(mv, 4) || !aligned(frame_bounds, 4) ||
         (tile_bounds && !aligned16(tile_bounds)))
         return EXW_ERR_INVALID_ARG;
     const WsLayout l = ws_layout(W, H, 1, 1, false);
@@ -142,7 +144,7 @@ exw_status exw_motion_bounds(const float *depth, const float *mv, int W, int H, 
 exw_status exw_splat_motion(const float *depth, const float *mv, int W, int H, int k, int denom, uint64_t *keys,
                             exw_stream_t stream) {
     const int L = log2_pow2(denom);
-    if (!size_ok(W, H) || L < 0 || k < 0 || k > denom || !aligned16(depth) || !aligned16(mv) || !aligned16(keys))
+    if (!size_ok(W, H) || L < 0 || k < 0 || k > denom || !aligned(depth, 4) || !aligned(mv, 4) || !aligned(keys, 8))
         return EXW_ERR_INVALID_ARG;
     if (entry_check() != EXW_OK) return EXW_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
@@ -154,8 +156,9 @@ exw_status exw_splat_motion(const float *depth, const float *mv, int W, int H, i
 exw_status exw_warp(const void *color, exw_dtype cdt, const float *depth, const float *mv, const uint64_t *keys,
                     int W, int H, int k, int denom, void *out_color, uint8_t *mask, exw_stream_t stream) {
     const int L = log2_pow2(denom);
-    if (!size_ok(W, H) || L < 0 || k < 0 || k > denom || !dtype_ok(cdt) || !aligned16(color) || !aligned16(depth) ||
-        !aligned16(mv) || !aligned16(keys) || !aligned16(out_color) || !aligned16(mask))
+    if (!size_ok(W, H) || L < 0 || k < 0 || k > denom || !dtype_ok(cdt) || !aligned(color, csize(cdt)) ||
+        !aligned(depth, 4) || !aligned(mv, 4) || !aligned(keys, 8) || !aligned(out_color, csize(cdt)) ||
+        !aligned(mask, 1))
         return EXW_ERR_INVALID_ARG;
     if (entry_check() != EXW_OK) return EXW_ERR_CUDA;
     TileParams p{};
@@ -177,7 +180,8 @@ exw_status exw_warp(const void *color, exw_dtype cdt, const float *depth, const 
 
 exw_status exw_fill_holes(void *color, exw_dtype cdt, const uint8_t *mask, int W, int H, void *ws, size_t ws_bytes,
                           exw_stream_t stream) {
-    if (!size_ok(W, H) || !dtype_ok(cdt) || !aligned16(color) || !aligned16(mask)) return EXW_ERR_INVALID_ARG;
+    if (!size_ok(W, H) || !dtype_ok(cdt) || !aligned(color, csize(cdt)) || !aligned(mask, 1))
+        return EXW_ERR_INVALID_ARG;
     const WsLayout l = ws_layout(W, H, 1, 1, false);
     if (!aligned16(ws) || ws_bytes < l.total) return EXW_ERR_WORKSPACE;
     if (entry_check() != EXW_OK) return EXW_ERR_CUDA;
@@ -201,12 +205,12 @@ exw_status exw_extrapolate(const exw_frame *frames, int nframes, int nfrac, unsi
     if (!size_ok(W, H) || !dtype_ok(cdt)) return EXW_ERR_INVALID_ARG;
     for (int f = 0; f < nframes; ++f) {
         const exw_frame &fr = frames[f];
-        if (fr.W != W || fr.H != H || fr.cdt != cdt || !aligned16(fr.color) || !aligned16(fr.depth) ||
-            !aligned16(fr.mv))
+        if (fr.W != W || fr.H != H || fr.cdt != cdt || !aligned(fr.color, csize(cdt)) || !aligned(fr.depth, 4) ||
+            !aligned(fr.mv, 4))
             return EXW_ERR_INVALID_ARG;
         for (int j = 0; j < nfrac; ++j) {
             const exw_frame_out &o = out[(size_t)f * nfrac + j];
-            if (!aligned16(o.color) || !aligned16(o.mask)) return EXW_ERR_INVALID_ARG;
+            if (!aligned(o.color, csize(cdt)) || !aligned(o.mask, 1)) return EXW_ERR_INVALID_ARG;
         }
     }
     const WsLayout l = ws_layout(W, H, nframes, nfrac, false);
@@ -235,9 +239,9 @@ exw_status exw_warp_backward(const float *grad_out, const void *color, exw_dtype
                              const float *mv, const uint64_t *keys, int W, int H, int k, int denom, float *grad_color,
                              float *grad_mv, void *ws, size_t ws_bytes, exw_stream_t stream) {
     const int L = log2_pow2(denom);
-    if (!size_ok(W, H) || L < 0 || k < 0 || k > denom || !dtype_ok(cdt) || !aligned16(grad_out) ||
-        !aligned16(color) || !aligned16(depth) || !aligned16(mv) || !aligned16(grad_color) || !aligned16(grad_mv) ||
-        (keys != nullptr && !aligned16(keys)))
+    if (!size_ok(W, H) || L < 0 || k < 0 || k > denom || !dtype_ok(cdt) || !aligned(grad_out, 4) ||
+        !aligned(color, csize(cdt)) || !aligned(depth, 4) || !aligned(mv, 4) || !aligned(grad_color, 4) ||
+        !aligned(grad_mv, 4) || (keys != nullptr && !aligned(keys, 8)))
         return EXW_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const uint64_t *kp = keys;
@@ -258,8 +262,8 @@ exw_status exw_warp_backward(const float *grad_out, const void *color, exw_dtype
 
 exw_status exw_l2_loss_grad(const void *out, const void *target, exw_dtype cdt, const uint8_t *mask, int W, int H,
                             float *grad_out, float *loss, exw_stream_t stream) {
-    if (!size_ok(W, H) || !dtype_ok(cdt) || !aligned16(out) || !aligned16(target) || !aligned16(mask) ||
-        !aligned16(grad_out) || loss == nullptr || ((uintptr_t)loss & 3u) != 0)
+    if (!size_ok(W, H) || !dtype_ok(cdt) || !aligned(out, csize(cdt)) || !aligned(target, csize(cdt)) ||
+        !aligned(mask, 1) || !aligned(grad_out, 4) || !aligned(loss, 4))
         return EXW_ERR_INVALID_ARG;
     if (entry_check() != EXW_OK) return EXW_ERR_CUDA;
     return from_cuda(launch_l2_loss(out, target, cdt, mask, W, H, grad_out, loss, (cudaStream_t)stream));

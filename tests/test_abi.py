@@ -62,7 +62,7 @@ def test_invalid_arguments_rejected_on_host(lib):
     # null / misaligned pointers and bad sizes return EXW_ERR_INVALID_ARG (1) before touching the GPU
     aligned = 4096
     assert lib.exw_splat_motion(None, None, 8, 8, 1, 4, None, None) == 1
-    assert lib.exw_splat_motion(aligned, aligned, 8, 8, 1, 4, aligned + 8, None) == 1   # misaligned keys
+    assert lib.exw_splat_motion(aligned, aligned, 8, 8, 1, 4, aligned + 4, None) == 1   # misaligned keys
     assert lib.exw_splat_motion(aligned, aligned, 0, 8, 1, 4, aligned, None) == 1       # W = 0
     assert lib.exw_splat_motion(aligned, aligned, 8, 8, 5, 4, aligned, None) == 1       # k > denom
     assert lib.exw_splat_motion(aligned, aligned, 8, 8, 1, 3, aligned, None) == 1       # denom not a power of 2
