@@ -258,7 +258,8 @@ def run_exw(args):
     tot, n = kern[dom]
     avg_ms = tot / n
     c_bytes = 12
-    per_src_px = {"exw_fused": (c_bytes + 4 + 8) + NFRAC * (c_bytes + 1),   # compulsory: source once, 3 outputs
+    compulsory = (c_bytes + 4 + 8) + NFRAC * (c_bytes + 1)                 # source once, 3 outputs
+    per_src_px = {"exw_fused": compulsory, "exw_fused_tma": compulsory,
                   "exw_bounds": 8 + 16.0 / 64,                               # motion read + tile bounds written
                   "exw_fixup": 0.0}
     alg_bytes = per_src_px.get(dom, 0.0) * W * H
@@ -267,7 +268,8 @@ def run_exw(args):
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": alg_bytes, "mean_launch_ms": avg_ms,
-                "kernel_share": {k: v[0] / sum(x[0] for x in kern.values()) for k, v in kern.items()}}
+                "kernel_share": {k: v[0] / sum(x[0] for x in kern.values()) for k, v in kern.items()},
+                "tile_modes_frame0": b.frame_stats(ws, 0)}
 
     # end to end through the C ABI with host buffers
     hc = torch.from_numpy(col).pin_memory()

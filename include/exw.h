@@ -91,6 +91,9 @@ typedef enum exw_op {
 
 /* Flags of exw_extrapolate / exw_extrapolate_batched. */
 #define EXW_FLAG_NO_FILL 1u     /* stop after stage (b): holes stay 0, as exw_warp leaves them */
+#define EXW_FLAG_NO_TMA 2u      /* read the source from global memory instead of TMA-staged shared-memory windows
+                                   (identical results; the TMA path needs 16-byte aligned bases and W a multiple
+                                   of 4 for float32 colour, of 8 for float16 colour, and is used when possible) */
 
 /* One source frame F_t (device pointers, layouts above). */
 typedef struct exw_frame {

@@ -18,6 +18,7 @@ from . import _lib
 F32, F16 = 0, 1
 OP_MOTION_BOUNDS, OP_FILL_HOLES, OP_EXTRAPOLATE, OP_WARP_BACKWARD = 0, 1, 2, 3
 FLAG_NO_FILL = 1
+FLAG_NO_TMA = 2
 MASK_EMPTY, MASK_CRACK = 1, 2
 KEY_EMPTY = -1  # all-ones uint64 as int64
 MAX_FRAC = 3
@@ -146,10 +147,12 @@ def exw_fill_holes(color, mask, ws=None, stream=None):
     return color
 
 
-def exw_extrapolate(color, depth, mv, nfrac: int = 3, fill: bool = True, out=None, mask=None, ws=None, stream=None):
+def exw_extrapolate(color, depth, mv, nfrac: int = 3, fill: bool = True, out=None, mask=None, ws=None, stream=None,
+                    tma: bool = True):
     """Stages (a0)+(a)+(b)+(c) for one frame ([3][H][W] colour) or a sequence ([F][3][H][W]).
 
-    Returns (out [F][nfrac][3][H][W], mask [F][nfrac][H][W]) -- without the F axis for a single frame."""
+    Returns (out [F][nfrac][3][H][W], mask [F][nfrac][H][W]) -- without the F axis for a single frame.
+    ``tma=False`` sets EXW_FLAG_NO_TMA (global-memory source reads; identical results)."""
     single = color.dim() == 3
     if single:
         color, depth, mv = color.unsqueeze(0), depth.unsqueeze(0), mv.unsqueeze(0)
@@ -174,9 +177,10 @@ def exw_extrapolate(color, depth, mv, nfrac: int = 3, fill: bool = True, out=Non
         frames[f] = _lib.ExwFrame(color[f].data_ptr(), depth[f].data_ptr(), mv[f].data_ptr(), W, H, cdt)
         for j in range(nfrac):
             outs[f * nfrac + j] = _lib.ExwFrameOut(out[f, j].data_ptr(), mask[f, j].data_ptr())
-    _check(lib().exw_extrapolate(ctypes.cast(frames, ctypes.c_void_p), F, int(nfrac),
-                                 0 if fill else FLAG_NO_FILL, ctypes.cast(outs, ctypes.c_void_p), ws.data_ptr(),
-                                 ws.numel(), _stream(stream, dev)))
+    flags = (0 if fill else FLAG_NO_FILL) | (0 if tma else FLAG_NO_TMA)
+    _check(lib().exw_extrapolate(ctypes.cast(frames, ctypes.c_void_p), F, int(nfrac), flags,
+                                 ctypes.cast(outs, ctypes.c_void_p), ws.data_ptr(), ws.numel(),
+                                 _stream(stream, dev)))
     if single:
         return out[0], mask[0]
     return out, mask
@@ -221,6 +225,15 @@ def exw_l2_loss_grad(out, target, mask, grad_out=None, loss=None, stream=None):
                                   _dev(grad_out, "grad_out", torch.float32, (3, H, W)),
                                   _dev(loss, "loss", torch.float32), _stream(stream, dev)))
     return loss, grad_out
+
+
+def frame_stats(ws, frame: int = 0) -> dict:
+    """Diagnostics an exw_extrapolate call leaves in its workspace for source frame ``frame``: tiles per staging
+    mode (one TMA window for all fractions / one per fraction / global memory) and, per fraction, tiles without any
+    valid pixel.  Reads the 64-byte frame header at byte 256 + 64 * frame (see csrc/exw_internal.h)."""
+    words = ws[256 + 64 * frame: 256 + 64 * (frame + 1)].view(torch.int32).cpu().tolist()
+    return {"tiles_window_all": words[10], "tiles_window_each": words[11], "tiles_global": words[12],
+            "tiles_without_valid_pixel": words[5:8]}
 
 
 def exw_device_status(ws, stream=None) -> int:

@@ -6,9 +6,70 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "exw_internal.h"
 
 namespace exw {
+
+// ------------------------------------------------------------------------------------------------------------
+// TMA tensor maps (cuTensorMapEncodeTiled, reached through the runtime's driver entry point)
+// ------------------------------------------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> g(mu);
+    if (!tried) {
+        tried = true;
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
+    }
+    return fn;
+}
+
+// A [planes][H][W] array (planes = 1 gives a 2-D map) with box [planes][by][bx].
+static bool encode_map(CUtensorMap *m, CUtensorMapDataType t, const void *base, int W, int H, int planes,
+                       size_t esize, int bx, int by) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (fn == nullptr) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)planes};
+    const cuuint64_t strides[2] = {(cuuint64_t)W * esize, (cuuint64_t)W * H * esize};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)planes};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const cuuint32_t rank = planes > 1 ? 3 : 2;
+    return fn(m, t, rank, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// TMA staging needs 16-byte aligned bases and rows (W * element size a multiple of 16).
+static bool tma_eligible(const void *color, const float *depth, const float *mv, int W, exw_dtype cdt) {
+    const int a = cdt == EXW_F16 ? 8 : 4;
+    return (W % a) == 0 && ((uintptr_t)color & 15u) == 0 && ((uintptr_t)depth & 15u) == 0 &&
+           ((uintptr_t)mv & 15u) == 0 && encode_fn() != nullptr;
+}
+
+static bool make_maps(TmaMaps *m, const void *color, const float *depth, const float *mv, int W, int H,
+                      exw_dtype cdt) {
+    const int bx = cdt == EXW_F16 ? kWinXF16 : kWinXF32, by = cdt == EXW_F16 ? kWinYF16 : kWinYF32;
+    const CUtensorMapDataType ct = cdt == EXW_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    return encode_map(&m->col, ct, color, W, H, 3, cdt == EXW_F16 ? 2 : 4, bx, by) &&
+           encode_map(&m->depth, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, depth, W, H, 1, 4, bx, by) &&
+           encode_map(&m->mv, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, mv, W, H, 2, 4, bx, by);
+}
+
+static int sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess)
+        return 1;
+    return n > 0 ? n : 1;
+}
 
 // ------------------------------------------------------------------------------------------------------------
 // Kernel timing: CUDA event pairs on the launching stream around every launch, while enabled.
@@ -87,6 +148,7 @@ static TileParams tile_params(const WsLayout &l, void *ws, int W, int H, int nfr
     p.n5x = l.n5x;
     p.n5y = l.n5y;
     p.ncoarse = l.ncoarse;
+    p.status = (uint32_t *)ws;
     return p;
 }
 
@@ -198,7 +260,7 @@ exw_status exw_fill_holes(void *color, exw_dtype cdt, const uint8_t *mask, int W
 exw_status exw_extrapolate(const exw_frame *frames, int nframes, int nfrac, unsigned flags, exw_frame_out *out,
                            void *ws, size_t ws_bytes, exw_stream_t stream) {
     if (frames == nullptr || out == nullptr || nframes < 1 || nfrac < 1 || nfrac > EXW_MAX_FRAC ||
-        (flags & ~EXW_FLAG_NO_FILL) != 0)
+        (flags & ~(EXW_FLAG_NO_FILL | EXW_FLAG_NO_TMA)) != 0)
         return EXW_ERR_INVALID_ARG;
     const int W = frames[0].W, H = frames[0].H;
     const exw_dtype cdt = frames[0].cdt;
@@ -229,7 +291,17 @@ exw_status exw_extrapolate(const exw_frame *frames, int nframes, int nfrac, unsi
             p.out_mask[j] = out[(size_t)f * nfrac + j].mask;
         }
         e = launch_bounds(p.depth, p.mv, W, H, (float4 *)p.tile_bounds, p.fh, s);
-        if (e == cudaSuccess) e = launch_fused(p, cdt, fill, s);
+        TmaMaps maps;
+        const bool tma = (flags & EXW_FLAG_NO_TMA) == 0 && tma_eligible(p.color, p.depth, p.mv, W, cdt) &&
+                         make_maps(&maps, p.color, p.depth, p.mv, W, H, cdt);
+        if (e == cudaSuccess) {
+            if (tma) {
+                const int ntiles = l.n5x * l.n5y, g = 2 * sm_count();
+                e = launch_fused_tma(p, maps, cdt, fill, ntiles < g ? ntiles : g, s);
+            } else {
+                e = launch_fused(p, cdt, fill, s);
+            }
+        }
         if (e == cudaSuccess && fill) e = launch_fixup(p, cdt, s);
     }
     return from_cuda(e);

@@ -25,9 +25,9 @@ __global__ void __launch_bounds__(256) splat_global_kernel(const float *__restri
     const uint32_t db = __float_as_uint(__ldg(depth + i));
     const uint32_t ux = __float_as_uint(__ldg(mv + i)), uy = __float_as_uint(__ldg(mv + plane + i));
     if (!depth_ok(db) || !finite_bits(ux) || !finite_bits(uy)) return;
-    const AxisStep sx = axis_step(ux, k, L), sy = axis_step(uy, k, L);
-    if (!sx.ok || !sy.ok) return;
-    const int gx = x + sx.off, gy = y + sy.off;
+    int ox, oy;
+    if (!axis_off(axis_dec(ux, L), k, ox) || !axis_off(axis_dec(uy, L), k, oy)) return;
+    const int gx = x + ox, gy = y + oy;
     if (gx < 0 || gx >= W || gy < 0 || gy >= H) return;
     atomicMin(keys + (size_t)gy * W + gx, (unsigned long long)pack_key_global(db, (uint32_t)i));
 }

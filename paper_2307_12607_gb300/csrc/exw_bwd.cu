@@ -12,7 +12,7 @@
 namespace exw {
 
 constexpr int kBwdThreads = 256;
-constexpr int kBwdRegionN = kRegion * kRegion;
+constexpr int kBwdRegionN = kRegionN;
 
 template <typename CT>
 __global__ void __launch_bounds__(kBwdThreads) backward_kernel(const float *__restrict__ grad_out,
@@ -37,9 +37,10 @@ __global__ void __launch_bounds__(kBwdThreads) backward_kernel(const float *__re
             const uint32_t db = __float_as_uint(__ldg(depth + i));
             const uint32_t ux = __float_as_uint(__ldg(mv + i)), uy = __float_as_uint(__ldg(mv + plane + i));
             if (depth_ok(db) && finite_bits(ux) && finite_bits(uy)) {
-                const AxisStep ax = axis_step(ux, k, L), ay = axis_step(uy, k, L);
-                const int qx = px + ax.off, qy = py + ay.off;
-                if (ax.ok && ay.ok && qx >= 0 && qx < W && qy >= 0 && qy < H) {
+                int ox = 0, oy = 0;
+                const bool lands = axis_off(axis_dec(ux, L), k, ox) && axis_off(axis_dec(uy, L), k, oy);
+                const int qx = px + ox, qy = py + oy;
+                if (lands && qx >= 0 && qx < W && qy >= 0 && qy < H) {
                     const size_t q = (size_t)qy * W + qx;
                     const unsigned long long kq = __ldg(keys + q);
                     if (kq == pack_key_global(db, (uint32_t)i)) {
@@ -47,12 +48,13 @@ __global__ void __launch_bounds__(kBwdThreads) backward_kernel(const float *__re
                         const unsigned long long k1 = qx < W - 1 ? __ldg(keys + q + 1) : kKeyEmpty;
                         const unsigned long long k2 = qy > 0 ? __ldg(keys + q - W) : kKeyEmpty;
                         const unsigned long long k3 = qy < H - 1 ? __ldg(keys + q + W) : kKeyEmpty;
-                        if (!is_crack(kq, k0, k1, k2, k3)) {
+                        if (!is_crack(key_dbits(kq), key_dbits(k0), key_dbits(k1), key_dbits(k2), key_dbits(k3))) {
                             const float Dp = __uint_as_float(db);
-                            const int sx = ax.sgn, sy = ay.sgn;
-                            float wx0 = 1.f, wx1 = 0.f, wy0 = 1.f, wy1 = 0.f;
-                            if (sx) { const float a = fabsf(ax.rho); wx0 = 1.f - a; wx1 = a; }
-                            if (sy) { const float a = fabsf(ay.rho); wy0 = 1.f - a; wy1 = a; }
+                            int sx, sy;
+                            const float rhox = residual(__uint_as_float(ux), k, L, ox, sx);
+                            const float rhoy = residual(__uint_as_float(uy), k, L, oy, sy);
+                            const float wx1 = fabsf(rhox), wy1 = fabsf(rhoy);
+                            const float wx0 = 1.f - wx1, wy0 = 1.f - wy1;
                             const int tx = px + sx, ty = py + sy;
                             const bool inx = sx != 0 && tx >= 0 && tx < W;
                             const bool iny = sy != 0 && ty >= 0 && ty < H;

@@ -1,7 +1,8 @@
 // exw_device.cuh -- device-side building blocks of the warping fast path (sm_103a).
 //
 // Everything a kernel needs per pixel lives here so that the staged kernels (exw_splat_motion, exw_warp,
-// exw_fill_holes) and the fused/batched kernels run literally the same arithmetic and agree bit for bit.
+// exw_fill_holes), the fused kernels and the batched kernel run literally the same arithmetic and agree bit for
+// bit.  Source data is read through an accessor (global memory or a shared-memory window staged by TMA).
 #pragma once
 
 #include <cstdint>
@@ -12,6 +13,7 @@ namespace exw {
 constexpr uint64_t kKeyEmpty = ~0ull;
 constexpr int kFillTile = 32;          // fill tile side: pyramid levels 1..5 live in shared memory
 constexpr int kRegion = kFillTile + 2; // fill tile plus a one-pixel ring (the crack rule reads 4-neighbours)
+constexpr int kRegionN = kRegion * kRegion;
 constexpr int kBoundsBlock = 8;        // side of the motion-bounds tiles
 constexpr int kMaxFrac = 3;
 
@@ -23,58 +25,57 @@ constexpr int kMaxFrac = 3;
 __device__ __forceinline__ bool depth_ok(uint32_t dbits) { return (dbits - 1u) < 0x7F7FFFFFu; }
 __device__ __forceinline__ bool finite_bits(uint32_t b) { return (b & 0x7F800000u) != 0x7F800000u; }
 
-// ------------------------------------------------------------------------------------------------------------
-// Exact target offset: off = floor(1/2 + k * mv / 2^L) and the residual rho = off - k * mv / 2^L.
-//
-// A float mv is (+-)M * 2^(e - 150) with M < 2^24, so k*mv/2^L = (+-)K * 2^-n with K = k*M < 2^30 (k <= 64) and
-// n = 150 + L - e.  Rounding half up is then an arithmetic shift: off = (sK + 2^(n-1)) >> n, and the remainder r
-// of that shift gives rho * 2^n = 2^(n-1) - r exactly in 32 bits.  n >= 32 means |d| < 1/4 (off = 0); n <= 0
-// means |d| >= 2^23, which cannot land in any frame.  All integer, so every thread agrees with exact arithmetic.
-// ------------------------------------------------------------------------------------------------------------
-struct AxisStep {
-    int off;    // the whole-pixel offset (meaningful when ok)
-    float rho;  // residual rounded to float; its sign is exact
-    int sgn;    // sign of the exact residual: -1, 0 or +1
-    bool ok;    // false when |offset| >= 2^23 (cannot land)
-};
-
 __device__ __forceinline__ float pow2_neg(int n) {  // 2^-n for n in [-126, 126]
     return __int_as_float((127 - n) << 23);
 }
 
-__device__ __forceinline__ AxisStep axis_step(uint32_t u, int k, int L) {
-    AxisStep r;
+// ------------------------------------------------------------------------------------------------------------
+// Exact target offset off = floor(1/2 + k * mv / 2^L).
+//
+// A finite float mv is sM * 2^(e - 150) with |sM| < 2^24, so k*mv/2^L = k*sM * 2^-n with n = 150 + L - e.  For
+// k <= 64, |k*sM| < 2^30, and rounding half up is an arithmetic shift: off = (k*sM + 2^(n-1)) >> n.  n >= 32 means
+// |d| < 1/4 (off = 0); n <= 0 means |d| >= 2^23 (cannot land in any frame).  The decomposition is shared by all
+// fractions, so each extra fraction costs one multiply-add and one shift.
+// ------------------------------------------------------------------------------------------------------------
+struct AxisDec {
+    int sM;  // signed significand
+    int n;   // right-shift amount
+};
+
+__device__ __forceinline__ AxisDec axis_dec(uint32_t u, int L) {
     const uint32_t E = (u >> 23) & 0xFFu;
-    const uint32_t m = u & 0x7FFFFFu;
-    const uint32_t M = E ? (m | 0x800000u) : m;
-    const int e = E ? (int)E : 1;
-    const uint32_t K = (uint32_t)k * M;
-    const bool neg = (u >> 31) != 0u;
-    r.off = 0;
-    r.rho = 0.0f;
-    r.sgn = 0;
-    r.ok = true;
-    if (K == 0u) return r;
-    const int n = 150 + L - e;
-    if (n <= 0) {
-        r.ok = false;
-        return r;
+    const int M = (int)((u & 0x7FFFFFu) | (E ? 0x800000u : 0u));
+    AxisDec d;
+    d.sM = (u >> 31) ? -M : M;
+    d.n = 150 + L - (E ? (int)E : 1);
+    return d;
+}
+
+// Returns false when the offset cannot land in any frame (|offset| >= 2^23).
+__device__ __forceinline__ bool axis_off(const AxisDec &d, int k, int &off) {
+    if (d.n >= 32 || d.sM == 0 || k == 0) {
+        off = 0;
+        return true;
     }
-    if (n >= 32) {  // |d| < 1/4: off = 0 and rho = -d
-        float mag = __uint2float_rn(K) * 0x1p-64f;
-        mag = mag * pow2_neg(n - 64);
-        r.rho = neg ? mag : -mag;
-        r.sgn = neg ? 1 : -1;
-        return r;
-    }
-    const int sK = neg ? -(int)K : (int)K;
-    const int half = 1 << (n - 1);
-    const int a = sK + half;
-    r.off = a >> n;
-    const uint32_t rem = (uint32_t)a & ((1u << n) - 1u);
-    const int num = half - (int)rem;
-    r.sgn = (num > 0) - (num < 0);
-    r.rho = __int2float_rn(num) * pow2_neg(n);
+    if (d.n <= 0) return false;
+    off = (k * d.sM + (1 << (d.n - 1))) >> d.n;
+    return true;
+}
+
+__device__ __forceinline__ int axis_off_of(uint32_t bits, int k, int L) {  // for clamped bounds (always lands)
+    int off = 0;
+    axis_off(axis_dec(bits, L), k, off);
+    return off;
+}
+
+// Residual rho = t - k*mv/2^L for a winner displaced by the whole-pixel offset t (|rho| <= 1/2).  One fused
+// multiply-add computes the exact value rounded once, i.e. the correctly rounded residual.  Its sign is exact
+// except when |rho| < 2^-150 rounds to zero, which needs t = 0 and a subnormal mv; then rho = -d has the sign of
+// -mv.  sgn is -1, 0 or +1.
+__device__ __forceinline__ float residual(float mv, int k, int L, int t, int &sgn) {
+    const float r = fmaf(-(float)k * pow2_neg(L), mv, (float)t);
+    sgn = (r > 0.0f) - (r < 0.0f);
+    if (sgn == 0 && t == 0 && k != 0 && mv != 0.0f) sgn = mv > 0.0f ? -1 : 1;
     return r;
 }
 
@@ -89,11 +90,13 @@ __device__ __forceinline__ uint64_t pack_key_global(uint32_t dbits, uint32_t idx
 __device__ __forceinline__ uint32_t key_dbits(uint64_t key) { return (uint32_t)(key >> 32); }
 
 // ------------------------------------------------------------------------------------------------------------
-// Colour access
+// Colour types
 // ------------------------------------------------------------------------------------------------------------
-template <typename CT> __device__ __forceinline__ float load_c(const CT *p);
-template <> __device__ __forceinline__ float load_c<float>(const float *p) { return __ldg(p); }
-template <> __device__ __forceinline__ float load_c<__half>(const __half *p) { return __half2float(__ldg(p)); }
+template <typename CT> __device__ __forceinline__ float to_f(CT v);
+template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
+
+template <typename CT> __device__ __forceinline__ float load_c(const CT *p) { return to_f<CT>(__ldg(p)); }
 
 template <typename CT> __device__ __forceinline__ CT to_storage(float v);
 template <> __device__ __forceinline__ float to_storage<float>(float v) { return v; }
@@ -105,19 +108,55 @@ template <> __device__ __forceinline__ float storage_round<__half>(float v) {
 }
 
 // ------------------------------------------------------------------------------------------------------------
+// Source accessors: global memory, or a shared-memory window [x0, x0 + WX) x [y0, y0 + WY) staged by TMA.
+// ------------------------------------------------------------------------------------------------------------
+template <typename CT>
+struct GlobalAcc {
+    const CT *col;
+    const float *depth;
+    const float *mv;
+    int W;
+    size_t plane;
+    __device__ __forceinline__ size_t at(int x, int y) const { return (size_t)y * W + x; }
+    __device__ __forceinline__ float d(int x, int y) const { return __ldg(depth + at(x, y)); }
+    __device__ __forceinline__ float mx(int x, int y) const { return __ldg(mv + at(x, y)); }
+    __device__ __forceinline__ float my(int x, int y) const { return __ldg(mv + plane + at(x, y)); }
+    __device__ __forceinline__ float c(int ch, int x, int y) const { return load_c<CT>(col + ch * plane + at(x, y)); }
+};
+
+template <typename CT, int WX, int WY>
+struct Window {  // TMA destinations: [y][x] per plane
+    float depth[WY * WX];
+    float mv[2][WY * WX];
+    CT col[3][WY * WX];
+};
+
+template <typename CT, int WX, int WY>
+struct WinAcc {
+    const Window<CT, WX, WY> *w;
+    int x0, y0;
+    __device__ __forceinline__ int at(int x, int y) const { return (y - y0) * WX + (x - x0); }
+    __device__ __forceinline__ float d(int x, int y) const { return w->depth[at(x, y)]; }
+    __device__ __forceinline__ float mx(int x, int y) const { return w->mv[0][at(x, y)]; }
+    __device__ __forceinline__ float my(int x, int y) const { return w->mv[1][at(x, y)]; }
+    __device__ __forceinline__ float c(int ch, int x, int y) const { return to_f<CT>(w->col[ch][at(x, y)]); }
+};
+
+// ------------------------------------------------------------------------------------------------------------
 // Stage (b) for one target pixel
 // ------------------------------------------------------------------------------------------------------------
 
-// Crack rule: at least 3 non-empty 4-neighbours nearer than the target by more than D_q / 32.
-// 32 * (Dq - Dn) > Dq is exact in float: within a factor of 2 the difference is exact (Sterbenz), and outside it
-// both sides are far from the threshold.  Empty neighbours (all-ones key, NaN depth bits) never count.
-__device__ __forceinline__ bool is_crack(uint64_t kq, uint64_t k0, uint64_t k1, uint64_t k2, uint64_t k3) {
-    const float Dq = __uint_as_float(key_dbits(kq));
+// Crack rule: at least 3 non-empty 4-neighbours nearer than the target by more than D_q / 32.  Only the depth
+// words of the keys matter: an empty key's word (all ones) is a NaN and never counts.  32 * (Dq - Dn) > Dq is
+// exact in float: within a factor of 2 the difference is exact (Sterbenz), outside it both sides are far from
+// the threshold.
+__device__ __forceinline__ bool is_crack(uint32_t dq, uint32_t d0, uint32_t d1, uint32_t d2, uint32_t d3) {
+    const float Dq = __uint_as_float(dq);
     int c = 0;
-    c += (k0 != kKeyEmpty) && (32.0f * (Dq - __uint_as_float(key_dbits(k0))) > Dq);
-    c += (k1 != kKeyEmpty) && (32.0f * (Dq - __uint_as_float(key_dbits(k1))) > Dq);
-    c += (k2 != kKeyEmpty) && (32.0f * (Dq - __uint_as_float(key_dbits(k2))) > Dq);
-    c += (k3 != kKeyEmpty) && (32.0f * (Dq - __uint_as_float(key_dbits(k3))) > Dq);
+    c += (32.0f * (Dq - __uint_as_float(d0)) > Dq);
+    c += (32.0f * (Dq - __uint_as_float(d1)) > Dq);
+    c += (32.0f * (Dq - __uint_as_float(d2)) > Dq);
+    c += (32.0f * (Dq - __uint_as_float(d3)) > Dq);
     return c >= 3;
 }
 
@@ -125,60 +164,50 @@ __device__ __forceinline__ bool is_crack(uint64_t kq, uint64_t k0, uint64_t k1, 
 // non-positive tap depth fails it.
 __device__ __forceinline__ bool tap_agrees(float Dt, float Dp) { return 32.0f * fabsf(Dt - Dp) <= Dp; }
 
-// Bilinear gather at the winner (px, py) of target q: taps p, p+sx, p+sy, p+sx+sy (in this order), renormalised
-// over the participating ones.  Returns the colour in out[3].
-template <typename CT>
-__device__ __forceinline__ void gather_pixel(uint32_t dbits, int px, int py, int k, int L, const CT *__restrict__ col,
-                                             const float *__restrict__ depth, const float *__restrict__ mv, int W,
-                                             int H, size_t plane, float out[3]) {
-    const size_t p = (size_t)py * W + px;
-    const AxisStep ax = axis_step(__float_as_uint(__ldg(mv + p)), k, L);
-    const AxisStep ay = axis_step(__float_as_uint(__ldg(mv + plane + p)), k, L);
+// Bilinear gather for target (qx, qy) at its winner (px, py): taps p, p+sx, p+sy, p+sx+sy (in this order),
+// renormalised over the participating ones.  Returns the colour in out[3].
+template <class Acc>
+__device__ __forceinline__ void gather_at(const Acc &a, uint32_t dbits, int px, int py, int qx, int qy, int k, int L,
+                                          int W, int H, float out[3]) {
+    int sx, sy;
+    const float rx = residual(a.mx(px, py), k, L, qx - px, sx);
+    const float ry = residual(a.my(px, py), k, L, qy - py, sy);
     const float Dp = __uint_as_float(dbits);
-    float wx0 = 1.0f, wx1 = 0.0f, wy0 = 1.0f, wy1 = 0.0f;
-    if (ax.sgn) { const float a = fabsf(ax.rho); wx0 = 1.0f - a; wx1 = a; }
-    if (ay.sgn) { const float a = fabsf(ay.rho); wy0 = 1.0f - a; wy1 = a; }
-    const int tx = px + ax.sgn, ty = py + ay.sgn;
-    const bool inx = ax.sgn != 0 && tx >= 0 && tx < W;
-    const bool iny = ay.sgn != 0 && ty >= 0 && ty < H;
+    const float ax = fabsf(rx), ay = fabsf(ry);
+    const float wx0 = 1.0f - ax, wy0 = 1.0f - ay;
+    const int tx = px + sx, ty = py + sy;
+    const bool inx = sx != 0 && (unsigned)tx < (unsigned)W;
+    const bool iny = sy != 0 && (unsigned)ty < (unsigned)H;
     float w = wx0 * wy0;
     float den = w;
-    float n0 = w * load_c<CT>(col + p);
-    float n1 = w * load_c<CT>(col + plane + p);
-    float n2 = w * load_c<CT>(col + 2 * plane + p);
-    if (inx) {
-        const size_t t = (size_t)py * W + tx;
-        if (tap_agrees(__ldg(depth + t), Dp)) {
-            w = wx1 * wy0;
-            den += w;
-            n0 += w * load_c<CT>(col + t);
-            n1 += w * load_c<CT>(col + plane + t);
-            n2 += w * load_c<CT>(col + 2 * plane + t);
-        }
+    float n0 = w * a.c(0, px, py), n1 = w * a.c(1, px, py), n2 = w * a.c(2, px, py);
+    if (inx && tap_agrees(a.d(tx, py), Dp)) {
+        w = ax * wy0;
+        den += w;
+        n0 += w * a.c(0, tx, py);
+        n1 += w * a.c(1, tx, py);
+        n2 += w * a.c(2, tx, py);
     }
     if (iny) {
-        const size_t t = (size_t)ty * W + px;
-        if (tap_agrees(__ldg(depth + t), Dp)) {
-            w = wx0 * wy1;
+        if (tap_agrees(a.d(px, ty), Dp)) {
+            w = wx0 * ay;
             den += w;
-            n0 += w * load_c<CT>(col + t);
-            n1 += w * load_c<CT>(col + plane + t);
-            n2 += w * load_c<CT>(col + 2 * plane + t);
+            n0 += w * a.c(0, px, ty);
+            n1 += w * a.c(1, px, ty);
+            n2 += w * a.c(2, px, ty);
         }
-        if (inx) {
-            const size_t t2 = (size_t)ty * W + tx;
-            if (tap_agrees(__ldg(depth + t2), Dp)) {
-                w = wx1 * wy1;
-                den += w;
-                n0 += w * load_c<CT>(col + t2);
-                n1 += w * load_c<CT>(col + plane + t2);
-                n2 += w * load_c<CT>(col + 2 * plane + t2);
-            }
+        if (inx && tap_agrees(a.d(tx, ty), Dp)) {
+            w = ax * ay;
+            den += w;
+            n0 += w * a.c(0, tx, ty);
+            n1 += w * a.c(1, tx, ty);
+            n2 += w * a.c(2, tx, ty);
         }
     }
-    out[0] = n0 / den;
-    out[1] = n1 / den;
-    out[2] = n2 / den;
+    const float inv = __frcp_rn(den);
+    out[0] = n0 * inv;
+    out[1] = n1 * inv;
+    out[2] = n2 * inv;
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -195,55 +224,46 @@ __device__ __forceinline__ int lv_offset(int l) {  // l in 1..5
     return l == 1 ? 0 : l == 2 ? 256 : l == 3 ? 320 : l == 4 ? 336 : 340;
 }
 
-// Build levels 1..5 from v0/m0.  Children are averaged in the order (0,0),(0,1),(1,0),(1,1) (row, column).
-// Must be called by all threads of the block (contains barriers); v0/m0 must be complete on entry.
+// Mean of the valid children, taken in the order (0,0),(0,1),(1,0),(1,1) (row, column).
+__device__ __forceinline__ float4 mean4(float4 c0, float4 c1, float4 c2, float4 c3) {
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    int cnt = 0;
+    if (c0.w != 0.0f) { a0 += c0.x; a1 += c0.y; a2 += c0.z; ++cnt; }
+    if (c1.w != 0.0f) { a0 += c1.x; a1 += c1.y; a2 += c1.z; ++cnt; }
+    if (c2.w != 0.0f) { a0 += c2.x; a1 += c2.y; a2 += c2.z; ++cnt; }
+    if (c3.w != 0.0f) { a0 += c3.x; a1 += c3.y; a2 += c3.z; ++cnt; }
+    if (cnt == 0) return make_float4(0.f, 0.f, 0.f, 0.f);
+    const float fc = (float)cnt;
+    return make_float4(a0 / fc, a1 / fc, a2 / fc, 1.0f);
+}
+
+// Build levels 1..5 from v0/m0.  Must be called by all threads of the block (contains barriers); v0/m0 must be
+// complete on entry.
 __device__ __forceinline__ void pull_tile(FillSmem &s) {
     const int t = threadIdx.x;
     const int nt = blockDim.x;
     for (int node = t; node < 256; node += nt) {
         const int i = node >> 4, j = node & 15;
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-        int cnt = 0;
+        const int y = 2 * i, x = 2 * j;
+        float4 c[4];
 #pragma unroll
-        for (int a = 0; a < 2; ++a) {
-#pragma unroll
-            for (int b = 0; b < 2; ++b) {
-                const int y = 2 * i + a, x = 2 * j + b;
-                if (s.m0[y][x]) {
-                    a0 += s.v0[0][y][x];
-                    a1 += s.v0[1][y][x];
-                    a2 += s.v0[2][y][x];
-                    ++cnt;
-                }
-            }
+        for (int q = 0; q < 4; ++q) {
+            const int yy = y + (q >> 1), xx = x + (q & 1);
+            c[q] = s.m0[yy][xx] ? make_float4(s.v0[0][yy][xx], s.v0[1][yy][xx], s.v0[2][yy][xx], 1.0f)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        const float fc = (float)cnt;
-        s.lv[node] = cnt ? make_float4(a0 / fc, a1 / fc, a2 / fc, 1.0f) : make_float4(0.f, 0.f, 0.f, 0.f);
+        s.lv[node] = mean4(c[0], c[1], c[2], c[3]);
     }
     __syncthreads();
 #pragma unroll 1
     for (int l = 2; l <= 5; ++l) {
-        const int side = kFillTile >> l, cside = side * 2;
+        const int lg = 5 - l;                 // log2 of this level's side
+        const int side = 1 << lg, cside = side * 2;
         const int po = lv_offset(l), co = lv_offset(l - 1);
         for (int node = t; node < side * side; node += nt) {
-            const int i = node / side, j = node % side;
-            float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-            int cnt = 0;
-#pragma unroll
-            for (int a = 0; a < 2; ++a) {
-#pragma unroll
-                for (int b = 0; b < 2; ++b) {
-                    const float4 c = s.lv[co + (2 * i + a) * cside + (2 * j + b)];
-                    if (c.w != 0.0f) {
-                        a0 += c.x;
-                        a1 += c.y;
-                        a2 += c.z;
-                        ++cnt;
-                    }
-                }
-            }
-            const float fc = (float)cnt;
-            s.lv[po + node] = cnt ? make_float4(a0 / fc, a1 / fc, a2 / fc, 1.0f) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int i = node >> lg, j = node & (side - 1);
+            const float4 *c = s.lv + co + (2 * i) * cside + 2 * j;
+            s.lv[po + node] = mean4(c[0], c[1], c[cside], c[cside + 1]);
         }
         __syncthreads();
     }

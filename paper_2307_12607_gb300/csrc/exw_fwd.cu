@@ -1,293 +1,162 @@
-// exw_fwd.cu -- forward tile kernels: fused splat+gather+fill, staged gather, staged fill, coarse fix-up.
+// exw_fwd.cu -- forward tile kernels: fused splat+gather+fill (persistent TMA and plain), staged gather, staged
+// fill, coarse fix-up.
 //
-// A CTA owns one 32 x 32 target tile Q (grid = ceil(W/32) x ceil(H/32)).  The fused kernel builds the keys of
-// Q plus a one-pixel ring in shared memory by splatting every source 8 x 8 block whose motion bounds can reach
-// it (64-bit shared atomicMin), then gathers colour per pixel with lane = x (coalesced 128-byte rows), builds
-// pyramid levels 1..5 of the tile in shared memory and fills holes from them.  Tiles with no valid pixel are
-// filled afterwards from the coarse levels, which the last CTA to finish computes (a done-counter in the
-// workspace; no grid-wide barrier and no spin).
-#include "exw_device.cuh"
-#include "exw_internal.h"
+// The persistent TMA kernel runs 2 CTAs per SM (about 112 KB of shared memory each).  Each CTA takes 32 x 32 target
+// tiles from a queue.  Per tile it scans the 8 x 8 motion bounds for the source rectangles that can land in the
+// tile (plus its one-pixel ring), then stages the source depth, motion and colour of that rectangle grown by one
+// pixel (the bilinear taps) into shared memory with three TMA loads (cp.async.bulk.tensor, mbarrier completion):
+//   mode A: one window covers the rectangles of all fractions -> one load, splat all fractions, gather each;
+//   mode B: per fraction, a window for that fraction's rectangle;
+//   mode C: a rectangle too large for a window -> the tile is processed from global memory.
+// While one CTA of an SM waits for its TMA load, the other computes.  Tiles without a valid pixel after the fill
+// are finished from the coarse pyramid levels, which the CTA finishing the frame's last tile builds (a done
+// counter in the workspace; no grid-wide barrier and no spin on other CTAs).
+#include "exw_tile.cuh"
+#include "exw_tma.cuh"
 
 namespace exw {
 
-constexpr int kThreads = 256;
-constexpr int kRegionN = kRegion * kRegion;
-
-struct FusedSmem {
-    uint64_t key[kMaxFrac][kRegionN];
-    FillSmem fill;
-    uint32_t cand[kThreads];
-    uint32_t ncand;
-    int last;
-};
-
 // ------------------------------------------------------------------------------------------------------------
-// Stage (b) for one pixel of a tile from shared keys of the region (tile + ring).  Returns the mask; c[] is the
-// colour rounded to the storage type (0 for holes).
-// ------------------------------------------------------------------------------------------------------------
-template <typename CT>
-__device__ __forceinline__ uint8_t warp_pixel(const uint64_t *sk, int x, int y, int k, const TileParams &p, float c[3]) {
-    const uint64_t kq = sk[(y + 1) * kRegion + (x + 1)];
-    c[0] = c[1] = c[2] = 0.0f;
-    if (kq == kKeyEmpty) return (uint8_t)EXW_MASK_EMPTY;
-    if (is_crack(kq, sk[(y + 1) * kRegion + x], sk[(y + 1) * kRegion + x + 2], sk[y * kRegion + x + 1],
-                 sk[(y + 2) * kRegion + x + 1]))
-        return (uint8_t)EXW_MASK_CRACK;
-    const uint32_t lo = (uint32_t)kq;
-    float v[3];
-    gather_pixel<CT>(key_dbits(kq), (int)(lo & 0x3FFFu), (int)(lo >> 14), k, p.L, (const CT *)p.color, p.depth,
-                     p.mv, p.W, p.H, (size_t)p.W * p.H, v);
-    c[0] = storage_round<CT>(v[0]);
-    c[1] = storage_round<CT>(v[1]);
-    c[2] = storage_round<CT>(v[2]);
-    return 0;
-}
-
-// ------------------------------------------------------------------------------------------------------------
-// Coarse levels of the pyramid (above level 5) for every fraction with invalid tiles, and the value each invalid
-// tile receives (its first valid ancestor; 0 when the frame has no valid pixel).  Run by one CTA.
-// ------------------------------------------------------------------------------------------------------------
-__device__ void coarse_pass(const TileParams &p) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int n5 = p.n5x * p.n5y;
-    for (int kk = 0; kk < p.nfrac; ++kk) {
-        const uint32_t cnt = __ldcg(&p.fh->ninvalid[kk]);
-        if (cnt == 0u) continue;
-        const float4 *child = p.nodes + (size_t)kk * n5;
-        float4 *cz = p.coarse + (size_t)kk * p.ncoarse;
-        int cw = p.n5x, ch = p.n5y, off = 0;
-        while (cw > 1 || ch > 1) {
-            const int pw = (cw + 1) / 2, ph = (ch + 1) / 2;
-            float4 *par = cz + off;
-            for (int node = tid; node < pw * ph; node += nt) {
-                const int i = node / pw, j = node - (node / pw) * pw;
-                float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-                int c = 0;
-                for (int a = 0; a < 2; ++a) {
-                    for (int b = 0; b < 2; ++b) {
-                        const int ci = 2 * i + a, cj = 2 * j + b;
-                        if (ci >= ch || cj >= cw) continue;
-                        const float4 v = __ldcg(child + ci * cw + cj);
-                        if (v.w != 0.0f) {
-                            a0 += v.x;
-                            a1 += v.y;
-                            a2 += v.z;
-                            ++c;
-                        }
-                    }
-                }
-                const float fc = (float)c;
-                par[node] = c ? make_float4(a0 / fc, a1 / fc, a2 / fc, 1.0f) : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-            __syncthreads();
-            child = par;
-            off += pw * ph;
-            cw = pw;
-            ch = ph;
-        }
-        for (uint32_t e = tid; e < cnt; e += nt) {
-            const uint32_t tile = __ldcg(p.list + (size_t)kk * n5 + e);
-            int ax = (int)(tile % (uint32_t)p.n5x), ay = (int)(tile / (uint32_t)p.n5x);
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            int w = p.n5x, h = p.n5y, o = 0;
-            while (w > 1 || h > 1) {
-                const int pw = (w + 1) / 2, ph = (h + 1) / 2;
-                ax >>= 1;
-                ay >>= 1;
-                const float4 c = __ldcg(cz + o + ay * pw + ax);
-                if (c.w != 0.0f) {
-                    v = c;
-                    break;
-                }
-                o += pw * ph;
-                w = pw;
-                h = ph;
-            }
-            p.fillval[(size_t)kk * n5 + e] = make_float4(v.x, v.y, v.z, 1.0f);
-        }
-        __syncthreads();
-    }
-}
-
-// Write the level-5 node of this tile for fraction kk; list the tile if it has no valid pixel.
-__device__ __forceinline__ void publish_node(const TileParams &p, const FillSmem &fs, int kk) {
-    const float4 node = fs.lv[340];
-    const int n5 = p.n5x * p.n5y;
-    const int tile = blockIdx.y * p.n5x + blockIdx.x;
-    p.nodes[(size_t)kk * n5 + tile] = node;
-    if (node.w == 0.0f) {
-        const uint32_t slot = atomicAdd(&p.fh->ninvalid[kk], 1u);
-        p.list[(size_t)kk * n5 + slot] = (uint32_t)tile;
-    }
-}
-
-// The last CTA to finish runs the coarse pass.
-__device__ __forceinline__ void finish_grid(const TileParams &p, int *last) {
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const uint32_t total = gridDim.x * gridDim.y;
-        *last = atomicAdd(&p.fh->done, 1u) == total - 1u;
-    }
-    __syncthreads();
-    if (*last) {
-        __threadfence();
-        coarse_pass(p);
-    }
-}
-
-// ------------------------------------------------------------------------------------------------------------
-// Shared-memory splat of every candidate source block into the region keys of all fractions.
-// ------------------------------------------------------------------------------------------------------------
-__device__ __forceinline__ void splat_region(FusedSmem &s, const TileParams &p, int RX0, int RY0) {
-    const int tid = threadIdx.x;
-    const uint32_t a0 = __ldcg(&p.fh->acc[0]), a1 = __ldcg(&p.fh->acc[1]);
-    const uint32_t a2 = __ldcg(&p.fh->acc[2]), a3 = __ldcg(&p.fh->acc[3]);
-    if (a1 == 0u) return;  // no source pixel can land anywhere (block-uniform)
-    const uint32_t fminx = __float_as_uint(-float_unorder(a0)), fmaxx = __float_as_uint(float_unorder(a1));
-    const uint32_t fminy = __float_as_uint(-float_unorder(a2)), fmaxy = __float_as_uint(float_unorder(a3));
-    int xlo = 1 << 30, xhi = -(1 << 30), ylo = 1 << 30, yhi = -(1 << 30);
-    for (int kk = 0; kk < p.nfrac; ++kk) {
-        const int k = p.k0 + kk;
-        const int ox0 = axis_step(fminx, k, p.L).off, ox1 = axis_step(fmaxx, k, p.L).off;
-        const int oy0 = axis_step(fminy, k, p.L).off, oy1 = axis_step(fmaxy, k, p.L).off;
-        xlo = min(xlo, RX0 - ox1);
-        xhi = max(xhi, RX0 + kRegion - 1 - ox0);
-        ylo = min(ylo, RY0 - oy1);
-        yhi = max(yhi, RY0 + kRegion - 1 - oy0);
-    }
-    const int bx0 = max(0, xlo >> 3), bx1 = min(p.nbx - 1, xhi >> 3);
-    const int by0 = max(0, ylo >> 3), by1 = min(p.nby - 1, yhi >> 3);
-    if (bx1 < bx0 || by1 < by0) return;
-    const int nbxr = bx1 - bx0 + 1;
-    const int total = nbxr * (by1 - by0 + 1);
-    const size_t plane = (size_t)p.W * p.H;
-    for (int base = 0; base < total; base += kThreads) {
-        if (tid == 0) s.ncand = 0u;
-        __syncthreads();
-        const int idx = base + tid;
-        if (idx < total) {
-            const int bx = bx0 + idx % nbxr, by = by0 + idx / nbxr;
-            const float4 b = __ldg(p.tile_bounds + (size_t)by * p.nbx + bx);
-            if (b.x <= b.y) {
-                uint32_t fm = 0;
-                for (int kk = 0; kk < p.nfrac; ++kk) {
-                    const int k = p.k0 + kk;
-                    const int tx0 = 8 * bx + axis_step(__float_as_uint(b.x), k, p.L).off;
-                    const int tx1 = 8 * bx + 7 + axis_step(__float_as_uint(b.y), k, p.L).off;
-                    const int ty0 = 8 * by + axis_step(__float_as_uint(b.z), k, p.L).off;
-                    const int ty1 = 8 * by + 7 + axis_step(__float_as_uint(b.w), k, p.L).off;
-                    if (tx1 >= RX0 && tx0 < RX0 + kRegion && ty1 >= RY0 && ty0 < RY0 + kRegion) fm |= 1u << kk;
-                }
-                if (fm) {
-                    const uint32_t slot = atomicAdd(&s.ncand, 1u);
-                    s.cand[slot] = (uint32_t)bx | ((uint32_t)by << 12) | (fm << 24);
-                }
-            }
-        }
-        __syncthreads();
-        const int nc = (int)s.ncand;
-        for (int c0 = 0; c0 < nc; c0 += kThreads / 64) {
-            const int ci = c0 + (tid >> 6);
-            if (ci < nc) {
-                const uint32_t e = s.cand[ci];
-                const int bx = (int)(e & 0xFFFu), by = (int)((e >> 12) & 0xFFFu);
-                const uint32_t fm = e >> 24;
-                const int x = 8 * bx + (tid & 7), y = 8 * by + ((tid >> 3) & 7);
-                if (x < p.W && y < p.H) {
-                    const size_t i = (size_t)y * p.W + x;
-                    const uint32_t db = __float_as_uint(__ldg(p.depth + i));
-                    const uint32_t ux = __float_as_uint(__ldg(p.mv + i));
-                    const uint32_t uy = __float_as_uint(__ldg(p.mv + plane + i));
-                    if (depth_ok(db) && finite_bits(ux) && finite_bits(uy)) {
-                        const uint64_t key = pack_key_local(db, x, y);
-                        for (int kk = 0; kk < p.nfrac; ++kk) {
-                            if (!(fm & (1u << kk))) continue;
-                            const int k = p.k0 + kk;
-                            const AxisStep sx = axis_step(ux, k, p.L), sy = axis_step(uy, k, p.L);
-                            if (!sx.ok || !sy.ok) continue;
-                            const int gx = x + sx.off, gy = y + sy.off;
-                            if (gx < 0 || gx >= p.W || gy < 0 || gy >= p.H) continue;
-                            const int rx = gx - RX0, ry = gy - RY0;
-                            if ((unsigned)rx < (unsigned)kRegion && (unsigned)ry < (unsigned)kRegion)
-                                atomicMin((unsigned long long *)&s.key[kk][ry * kRegion + rx], (unsigned long long)key);
-                        }
-                    }
-                }
-            }
-        }
-        __syncthreads();
-    }
-}
-
-// ------------------------------------------------------------------------------------------------------------
-// Fused stages (a)+(b)+(c) for all fractions of one target tile.
+// Plain fused kernel: one tile per CTA, source read from global memory (any frame width).
 // ------------------------------------------------------------------------------------------------------------
 template <typename CT, bool FILL>
 __global__ void __launch_bounds__(kThreads) fused_kernel(TileParams p) {
-    __shared__ __align__(16) FusedSmem s;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    __shared__ __align__(16) TileSmem s;
+    const int tile = blockIdx.y * p.n5x + blockIdx.x;
     const int X0 = blockIdx.x * kFillTile, Y0 = blockIdx.y * kFillTile;
-    for (int i = tid; i < p.nfrac * kRegionN; i += kThreads) (&s.key[0][0])[i] = kKeyEmpty;
+    init_keys(s, p.nfrac);
     __syncthreads();
-    splat_region(s, p, X0 - 1, Y0 - 1);
+    splat_global(s, p, X0 - 1, Y0 - 1);
     __syncthreads();
-    const size_t plane = (size_t)p.W * p.H;
-    const int gx = X0 + lane;
-    for (int kk = 0; kk < p.nfrac; ++kk) {
-        const int k = p.k0 + kk;
-        CT *oc = (CT *)p.out_color[kk];
-        uint8_t *om = p.out_mask[kk];
-        uint8_t mreg[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int y = wid + 8 * j, gy = Y0 + y;
-            const bool in = gx < p.W && gy < p.H;
-            float c[3] = {0.f, 0.f, 0.f};
-            uint8_t m = 0;
-            if (in) m = warp_pixel<CT>(s.key[kk], lane, y, k, p, c);
-            mreg[j] = m;
-            if (FILL) {
-                s.fill.v0[0][y][lane] = c[0];
-                s.fill.v0[1][y][lane] = c[1];
-                s.fill.v0[2][y][lane] = c[2];
-                s.fill.m0[y][lane] = in && m == 0;
-            } else if (in) {
-                const size_t q = (size_t)gy * p.W + gx;
-                oc[q] = to_storage<CT>(c[0]);
-                oc[plane + q] = to_storage<CT>(c[1]);
-                oc[2 * plane + q] = to_storage<CT>(c[2]);
-                om[q] = m;
-            }
-        }
-        if (FILL) {
-            __syncthreads();
-            pull_tile(s.fill);
-            const bool tile_valid = s.fill.lv[340].w != 0.0f;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int y = wid + 8 * j, gy = Y0 + y;
-                if (gx >= p.W || gy >= p.H) continue;
-                const size_t q = (size_t)gy * p.W + gx;
-                om[q] = mreg[j];
-                if (!tile_valid) continue;  // every pixel is a hole; the coarse fix-up writes them
-                float c0 = s.fill.v0[0][y][lane], c1 = s.fill.v0[1][y][lane], c2 = s.fill.v0[2][y][lane];
-                if (mreg[j]) {
-                    const float4 v = push_value(s.fill, y, lane);
-                    c0 = v.x;
-                    c1 = v.y;
-                    c2 = v.z;
-                }
-                oc[q] = to_storage<CT>(c0);
-                oc[plane + q] = to_storage<CT>(c1);
-                oc[2 * plane + q] = to_storage<CT>(c2);
-            }
-            if (tid == 0) publish_node(p, s.fill, kk);
-            __syncthreads();
-        }
+    const GlobalAcc<CT> a{(const CT *)p.color, p.depth, p.mv, p.W, (size_t)p.W * p.H};
+    for (int kk = 0; kk < p.nfrac; ++kk) finish_fraction<CT, FILL>(s, a, p, kk, X0, Y0, tile);
+    if (FILL) tile_done(p, &s.last);
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Persistent fused kernel with TMA-staged source windows.
+// ------------------------------------------------------------------------------------------------------------
+constexpr uint32_t kWaitLimit = 1u << 22;  // iterations of the bounded mbarrier wait (each >= 128 ns)
+
+template <typename CT, int WX, int WY>
+struct TmaSmem {
+    Window<CT, WX, WY> win;  // first: 128-byte aligned TMA destinations
+    TileSmem t;
+};
+
+template <typename CT, int WX, int WY>
+__device__ __forceinline__ Rect window_rect(Rect U) {  // window origin/extent for rectangle U grown by 1
+    constexpr int kAlign = sizeof(CT) == 2 ? 8 : 4;  // x * element size must be a multiple of 16 bytes
+    Rect w;
+    w.x0 = (U.x0 - 1) & ~(kAlign - 1);
+    w.y0 = U.y0 - 1;
+    w.x1 = w.x0 + WX - 1;
+    w.y1 = w.y0 + WY - 1;
+    return w;
+}
+
+template <typename CT, int WX, int WY>
+__device__ __forceinline__ bool window_fits(Rect U) {
+    const Rect w = window_rect<CT, WX, WY>(U);
+    return U.x1 + 1 <= w.x1 && U.y1 + 1 <= w.y1;
+}
+
+// Stage the window at (x0, y0) and wait for it.  Returns false (with the status word set) if the bounded wait ran
+// out; every thread returns the same value.
+template <typename CT, int WX, int WY>
+__device__ bool load_window(TmaSmem<CT, WX, WY> &s, const TileParams &p, const CUtensorMap *tcol,
+                            const CUtensorMap *tdep, const CUtensorMap *tmv, int x0, int y0, uint32_t &phase) {
+    constexpr uint32_t kBytes = WX * WY * (4 + 8 + 3 * (uint32_t)sizeof(CT));
+    if (threadIdx.x == 0) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&s.t.mbar, kBytes);
+        tma_load_2d(s.win.depth, tdep, x0, y0, &s.t.mbar);
+        tma_load_3d(&s.win.mv[0][0], tmv, x0, y0, 0, &s.t.mbar);
+        tma_load_3d(&s.win.col[0][0], tcol, x0, y0, 0, &s.t.mbar);
     }
-    if (FILL) finish_grid(p, &s.last);
+    const bool ok = mbar_wait_bounded(&s.t.mbar, phase, kWaitLimit);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) atomicExch(p.status, (uint32_t)EXW_ERR_TIMEOUT);
+        mbar_wait_bounded(&s.t.mbar, phase ^ 1u, kWaitLimit);  // let the copy in flight land before leaving
+        return false;
+    }
+    return true;
+}
+
+template <typename CT, int WX, int WY, bool FILL>
+__global__ void __launch_bounds__(kThreads, 2)
+    fused_tma_kernel(TileParams p, const __grid_constant__ CUtensorMap tcol, const __grid_constant__ CUtensorMap tdep,
+                     const __grid_constant__ CUtensorMap tmv) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TmaSmem<CT, WX, WY> &s = *reinterpret_cast<TmaSmem<CT, WX, WY> *>(smem_raw);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&s.t.mbar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    const int ntiles = p.n5x * p.n5y;
+    const GlobalAcc<CT> ga{(const CT *)p.color, p.depth, p.mv, p.W, (size_t)p.W * p.H};
+    for (;;) {
+        if (tid == 0) s.t.tile = (int)atomicAdd(&p.fh->queue, 1u);
+        __syncthreads();
+        const int tile = s.t.tile;
+        if (tile >= ntiles) break;
+        const int X0 = (tile % p.n5x) * kFillTile, Y0 = (tile / p.n5x) * kFillTile;
+        const int RX0 = X0 - 1, RY0 = Y0 - 1;
+        init_keys(s.t, p.nfrac);
+        scan_landing(s.t, p, RX0, RY0);
+        __syncthreads();
+        Rect Uk[kMaxFrac];
+        Rect U{1 << 30, -(1 << 30), 1 << 30, -(1 << 30)};
+        bool all_fit = true;
+        for (int kk = 0; kk < p.nfrac; ++kk) {
+            Uk[kk] = Rect{s.t.urect[kk][0], s.t.urect[kk][1], s.t.urect[kk][2], s.t.urect[kk][3]};
+            if (Uk[kk].empty()) continue;
+            U.x0 = min(U.x0, Uk[kk].x0);
+            U.x1 = max(U.x1, Uk[kk].x1);
+            U.y0 = min(U.y0, Uk[kk].y0);
+            U.y1 = max(U.y1, Uk[kk].y1);
+            all_fit = all_fit && window_fits<CT, WX, WY>(Uk[kk]);
+        }
+        int mode;
+        if (U.empty() || window_fits<CT, WX, WY>(U)) mode = 0;
+        else if (all_fit) mode = 1;
+        else mode = 2;
+        if (tid == 0) atomicAdd(&p.fh->nmode[mode], 1u);
+        if (mode == 0) {
+            if (U.empty()) {
+                for (int kk = 0; kk < p.nfrac; ++kk) finish_fraction<CT, FILL>(s.t, ga, p, kk, X0, Y0, tile);
+            } else {
+                const Rect w = window_rect<CT, WX, WY>(U);
+                if (!load_window(s, p, &tcol, &tdep, &tmv, w.x0, w.y0, phase)) return;
+                const WinAcc<CT, WX, WY> wa{&s.win, w.x0, w.y0};
+                splat_window(s.t, p, wa, U, (1u << p.nfrac) - 1u, RX0, RY0);
+                __syncthreads();
+                for (int kk = 0; kk < p.nfrac; ++kk) finish_fraction<CT, FILL>(s.t, wa, p, kk, X0, Y0, tile);
+            }
+        } else if (mode == 1) {
+            for (int kk = 0; kk < p.nfrac; ++kk) {
+                if (Uk[kk].empty()) {
+                    finish_fraction<CT, FILL>(s.t, ga, p, kk, X0, Y0, tile);
+                    continue;
+                }
+                const Rect w = window_rect<CT, WX, WY>(Uk[kk]);
+                if (!load_window(s, p, &tcol, &tdep, &tmv, w.x0, w.y0, phase)) return;
+                const WinAcc<CT, WX, WY> wa{&s.win, w.x0, w.y0};
+                splat_window(s.t, p, wa, Uk[kk], 1u << kk, RX0, RY0);
+                __syncthreads();
+                finish_fraction<CT, FILL>(s.t, wa, p, kk, X0, Y0, tile);
+            }
+        } else {
+            splat_global(s.t, p, RX0, RY0);
+            __syncthreads();
+            for (int kk = 0; kk < p.nfrac; ++kk) finish_fraction<CT, FILL>(s.t, ga, p, kk, X0, Y0, tile);
+        }
+        if (FILL) tile_done(p, &s.t.last);
+    }
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -295,8 +164,8 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(TileParams p) {
 // ------------------------------------------------------------------------------------------------------------
 template <typename CT>
 __global__ void __launch_bounds__(kThreads) warp_tiles_kernel(TileParams p) {
-    __shared__ uint64_t key[kRegionN];
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    __shared__ __align__(16) TileSmem s;
+    const int tid = threadIdx.x;
     const int X0 = blockIdx.x * kFillTile, Y0 = blockIdx.y * kFillTile;
     const uint32_t npix = (uint32_t)p.W * (uint32_t)p.H;
     for (int i = tid; i < kRegionN; i += kThreads) {
@@ -311,24 +180,11 @@ __global__ void __launch_bounds__(kThreads) warp_tiles_kernel(TileParams p) {
                 kv = pack_key_local(key_dbits(g), (int)px, (int)py);
             }
         }
-        key[i] = kv;
+        s.key[0][i] = kv;
     }
     __syncthreads();
-    const size_t plane = (size_t)p.W * p.H;
-    const int gx = X0 + lane;
-    CT *oc = (CT *)p.out_color[0];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int y = wid + 8 * j, gy = Y0 + y;
-        if (gx >= p.W || gy >= p.H) continue;
-        float c[3];
-        const uint8_t m = warp_pixel<CT>(key, lane, y, p.k0, p, c);
-        const size_t q = (size_t)gy * p.W + gx;
-        oc[q] = to_storage<CT>(c[0]);
-        oc[plane + q] = to_storage<CT>(c[1]);
-        oc[2 * plane + q] = to_storage<CT>(c[2]);
-        p.out_mask[0][q] = m;
-    }
+    const GlobalAcc<CT> a{(const CT *)p.color, p.depth, p.mv, p.W, (size_t)p.W * p.H};
+    finish_fraction<CT, false>(s, a, p, 0, X0, Y0, 0);
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -377,8 +233,8 @@ __global__ void __launch_bounds__(kThreads) fill_tiles_kernel(TileParams p) {
             oc[2 * plane + q] = to_storage<CT>(v.z);
         }
     }
-    if (tid == 0) publish_node(p, fs, 0);
-    finish_grid(p, &last);
+    if (tid == 0) publish_node(p, fs, 0, blockIdx.y * p.n5x + blockIdx.x);
+    tile_done(p, &last);
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -426,6 +282,35 @@ cudaError_t launch_fused(const TileParams &p, exw_dtype cdt, bool fill, cudaStre
     count_launch();
     timing_end("exw_fused", s);
     return cudaGetLastError();
+}
+
+template <typename CT, int WX, int WY, bool FILL>
+static cudaError_t launch_tma_t(const TileParams &p, const TmaMaps &m, int grid, cudaStream_t s) {
+    constexpr size_t kSmem = sizeof(TmaSmem<CT, WX, WY>);
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(fused_tma_kernel<CT, WX, WY, FILL>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    fused_tma_kernel<CT, WX, WY, FILL><<<grid, kThreads, kSmem, s>>>(p, m.col, m.depth, m.mv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fused_tma(const TileParams &p, const TmaMaps &m, exw_dtype cdt, bool fill, int grid,
+                             cudaStream_t s) {
+    timing_begin("exw_fused_tma", s);
+    cudaError_t e;
+    if (cdt == EXW_F32)
+        e = fill ? launch_tma_t<float, kWinXF32, kWinYF32, true>(p, m, grid, s)
+                 : launch_tma_t<float, kWinXF32, kWinYF32, false>(p, m, grid, s);
+    else
+        e = fill ? launch_tma_t<__half, kWinXF16, kWinYF16, true>(p, m, grid, s)
+                 : launch_tma_t<__half, kWinXF16, kWinYF16, false>(p, m, grid, s);
+    count_launch();
+    timing_end("exw_fused_tma", s);
+    return e;
 }
 
 cudaError_t launch_warp_tiles(const TileParams &p, exw_dtype cdt, cudaStream_t s) {

@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/exw.h"
@@ -16,10 +17,12 @@ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 // Per-frame bookkeeping, zeroed at the start of every call that uses it.
 struct FrameHeader {
     uint32_t acc[4];       // ordered-float maxima of -min mv_x, max mv_x, -min mv_y, max mv_y (0 = none)
-    uint32_t done;         // CTAs that finished the tile pass (the last one runs the coarse pyramid)
+    uint32_t done;         // tiles finished (the CTA finishing the last one runs the coarse pyramid)
     uint32_t ninvalid[3];  // fill tiles without any valid pixel, per fraction
-    uint32_t status;       // EXW_OK or an error found on the device
-    uint32_t pad[7];
+    uint32_t status;       // reserved
+    uint32_t queue;        // next tile of the persistent kernel
+    uint32_t nmode[3];     // tiles staged with one window / one window per fraction / from global memory
+    uint32_t pad[3];
 };
 static_assert(sizeof(FrameHeader) == 64, "FrameHeader is 64 bytes");
 
@@ -86,6 +89,16 @@ struct TileParams {
     float4 *fillval;            // [nfrac][n5]
     float4 *coarse;             // [nfrac][ncoarse]
     int n5x, n5y, ncoarse;
+    uint32_t *status;           // workspace status word (EXW_OK, or EXW_ERR_TIMEOUT from a bounded wait)
+};
+
+// Shared-memory source windows of the persistent TMA kernel (x extent, y extent); both are 64,512 bytes.
+constexpr int kWinXF32 = 56, kWinYF32 = 48;
+constexpr int kWinXF16 = 64, kWinYF16 = 56;
+
+// Tensor maps of one source frame: colour [3][H][W], depth [H][W], motion [2][H][W] with the window as box.
+struct TmaMaps {
+    CUtensorMap col, depth, mv;
 };
 
 // Launchers (exw_fwd.cu, exw_aux.cu, exw_bwd.cu).  Each returns the launch error.
@@ -97,6 +110,8 @@ cudaError_t launch_bounds(const float *depth, const float *mv, int W, int H, flo
                           cudaStream_t s);
 cudaError_t launch_bounds_finalize(const FrameHeader *fh, float *frame_bounds, cudaStream_t s);
 cudaError_t launch_fused(const TileParams &p, exw_dtype cdt, bool fill, cudaStream_t s);
+cudaError_t launch_fused_tma(const TileParams &p, const TmaMaps &m, exw_dtype cdt, bool fill, int grid,
+                             cudaStream_t s);
 cudaError_t launch_warp_tiles(const TileParams &p, exw_dtype cdt, cudaStream_t s);
 cudaError_t launch_fill_tiles(const TileParams &p, exw_dtype cdt, cudaStream_t s);
 cudaError_t launch_fixup(const TileParams &p, exw_dtype cdt, cudaStream_t s);

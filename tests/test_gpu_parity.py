@@ -174,6 +174,37 @@ def test_extrapolate_matches_oracle_and_staged(b, case, dtype, fill):
                            out[j].view(torch.int16 if dtype == torch.float16 else torch.int32))
 
 
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
+@pytest.mark.parametrize("case", [("scene", 640, 360, 9), ("scene", 256, 128, 15), ("ties", 96, 64, 16),
+                                  ("invalid", 64, 64, 3)])
+def test_tma_and_plain_paths_identical(b, case, dtype):
+    color, depth, mv = frame_case(case)
+    cs = as_storage(color, dtype)
+    c, d, m = dev(cs), dev(depth), dev(mv)
+    for fill in (True, False):
+        o1, m1 = b.exw_extrapolate(c, d, m, nfrac=3, fill=fill, tma=True)
+        o2, m2 = b.exw_extrapolate(c, d, m, nfrac=3, fill=fill, tma=False)
+        assert torch.equal(m1, m2)
+        iv = torch.int16 if dtype == torch.float16 else torch.int32
+        assert torch.equal(o1.view(iv), o2.view(iv))
+
+
+def test_tma_staging_modes_cover_all_tiles(b):
+    # a fast pixel forces the widest candidate search; wide tiles fall back per fraction or to global memory
+    color, depth, mv = scenes.random_frame(320, 192, 5, mv_scale=1.0)
+    mv[:, 50:60, 100:120] = np.float32(60.0)
+    c, d, m = dev(color), dev(depth), dev(mv)
+    ws = b.workspace(b.exw_workspace_bytes(b.OP_EXTRAPOLATE, 320, 192, b.F32, 1, 3), c.device)
+    out, mask = b.exw_extrapolate(c, d, m, ws=ws)
+    st = b.frame_stats(ws)
+    assert st["tiles_window_all"] + st["tiles_window_each"] + st["tiles_global"] == 10 * 6
+    assert st["tiles_window_all"] > 0 and st["tiles_global"] + st["tiles_window_each"] > 0
+    ref = oracle.extrapolate(color.astype(np.float64), depth, mv, 3)
+    for j, (wo, wm, _) in enumerate(ref):
+        np.testing.assert_array_equal(mask[j].cpu().numpy(), wm)
+        np.testing.assert_allclose(out[j].cpu().numpy(), wo, rtol=0, atol=2e-6)
+
+
 def test_extrapolate_fewer_fractions_and_sequences(b):
     frames = [frame_case(("scene", 96, 64, s)) for s in range(4)]
     c = dev(np.stack([f[0] for f in frames]))
@@ -351,8 +382,8 @@ def test_timing_and_launch_count(b):
     b.exw_timing_enable(True)
     b.exw_extrapolate(dev(color), dev(depth), dev(mv))
     torch.cuda.synchronize()
-    assert "exw_fused" in b.exw_timing_names()
-    ms, n = b.exw_timing_query("exw_fused")
+    assert "exw_fused_tma" in b.exw_timing_names()
+    ms, n = b.exw_timing_query("exw_fused_tma")
     assert n == 1 and ms > 0
     b.exw_timing_enable(False)
     assert b.exw_launch_count() - n0 == 4   # zero, bounds, fused, fixup
