@@ -153,6 +153,20 @@ EXW_API exw_status exw_warp(const void *color, exw_dtype cdt, const float *depth
 EXW_API exw_status exw_fill_holes(void *color, exw_dtype cdt, const uint8_t *mask, int W, int H, void *ws,
                           size_t ws_bytes, exw_stream_t stream);
 
+/* Stage (c) without a workspace: the same pull-push fill as exw_fill_holes (identical results), for callers that
+ * cannot allocate device memory when they fill a frame -- renderers that reserve all GPU memory at start-up and
+ * forbid allocation inside the frame loop, plugins running inside a host application whose allocator they may not
+ * call, code that only receives raw device pointers.  The paper has no counterpart; this is a library facility.
+ * Scratch: one built-in device array of 768 KiB, held by every GPU that loads the library until the process exits;
+ * frames up to 16384 fill tiles of 32 x 32 pixels (for example 4096 x 4096 or 8192 x 2048) fit, larger ones
+ * return EXW_ERR_WORKSPACE.  The call allocates nothing: the first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) and caches it, so make that first call before any stream capture.  All calls
+ * share the one array and each clears the counters it needs at its start: calls that may overlap on the GPU
+ * (different streams, or concurrent host threads) race on it and must be serialised by the caller.
+ * color [3][H][W] (cdt) device, read and written; mask [H][W] device, read. */
+EXW_API exw_status exw_fill_holes_static(void *color, exw_dtype cdt, const uint8_t *mask, int W, int H,
+                                         exw_stream_t stream);
+
 /* Stages (a0)+(a)+(b)+(c) fused: P_1..P_nfrac at t + k/4, k = 1..nfrac (Sec. IV-B; nfrac in [1, 3]), for
  * nframes source frames of one size and colour type.  frames [nframes] and out [nframes * nfrac] (frame-major:
  * out[f * nfrac + (k - 1)]) are HOST arrays of descriptors holding device pointers.  Per frame, one pass reads

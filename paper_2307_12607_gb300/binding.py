@@ -147,6 +147,16 @@ def exw_fill_holes(color, mask, ws=None, stream=None):
     return color
 
 
+def exw_fill_holes_static(color, mask, stream=None):
+    """Stage (c) in place, with the library's built-in scratch array instead of a workspace (for callers that
+    cannot allocate device memory; frames up to 16384 fill tiles of 32 x 32).  Calls that may overlap on the GPU
+    share that array and must be serialised by the caller.  Returns ``color``."""
+    H, W = int(mask.shape[0]), int(mask.shape[1])
+    _check(lib().exw_fill_holes_static(_dev(color, "color", None, (3, H, W)), _cdt(color),
+                                       _dev(mask, "mask", torch.uint8, (H, W)), W, H, _stream(stream, color.device)))
+    return color
+
+
 def exw_extrapolate(color, depth, mv, nfrac: int = 3, fill: bool = True, out=None, mask=None, ws=None, stream=None,
                     tma: bool = True):
     """Stages (a0)+(a)+(b)+(c) for one frame ([3][H][W] colour) or a sequence ([F][3][H][W]).
