@@ -138,6 +138,7 @@ static TileParams tile_params(const WsLayout &l, void *ws, int W, int H, int nfr
     p.L = L;
     p.k0 = k0;
     p.tile_bounds = (const float4 *)(b + l.tile_bounds);
+    p.plans = (TilePlan *)(b + l.plans);
     p.nbx = l.nbx;
     p.nby = l.nby;
     p.fh = (FrameHeader *)(b + l.headers) + frame;
@@ -297,7 +298,8 @@ exw_status exw_extrapolate(const exw_frame *frames, int nframes, int nfrac, unsi
         if (e == cudaSuccess) {
             if (tma) {
                 const int ntiles = l.n5x * l.n5y, g = 2 * sm_count();
-                e = launch_fused_tma(p, maps, cdt, fill, ntiles < g ? ntiles : g, s);
+                e = launch_plan(p, cdt, s);
+                if (e == cudaSuccess) e = launch_fused_tma(p, maps, cdt, fill, ntiles < g ? ntiles : g, s);
             } else {
                 e = launch_fused(p, cdt, fill, s);
             }

@@ -25,9 +25,9 @@ __global__ void __launch_bounds__(256) splat_global_kernel(const float *__restri
     const uint32_t db = __float_as_uint(__ldg(depth + i));
     const uint32_t ux = __float_as_uint(__ldg(mv + i)), uy = __float_as_uint(__ldg(mv + plane + i));
     if (!depth_ok(db) || !finite_bits(ux) || !finite_bits(uy)) return;
-    int ox, oy;
-    if (!axis_off(axis_dec(ux, L), k, ox) || !axis_off(axis_dec(uy, L), k, oy)) return;
-    const int gx = x + ox, gy = y + oy;
+    const AxisDec dx = axis_dec(ux, L), dy = axis_dec(uy, L);
+    if (!dx.land || !dy.land) return;
+    const int gx = x + axis_off(dx, k), gy = y + axis_off(dy, k);
     if (gx < 0 || gx >= W || gy < 0 || gy >= H) return;
     atomicMin(keys + (size_t)gy * W + gx, (unsigned long long)pack_key_global(db, (uint32_t)i));
 }
@@ -88,11 +88,13 @@ __global__ void __launch_bounds__(256) bounds_kernel(const float *__restrict__ d
             b.z = fminf(b.z, __shfl_xor_sync(0xFFFFFFFFu, b.z, o));
             b.w = fmaxf(b.w, __shfl_xor_sync(0xFFFFFFFFu, b.w, o));
         }
-        if (t == 0 && b.x <= b.y) {
-            atomicMax(&fh->acc[0], float_order(-b.x));
-            atomicMax(&fh->acc[1], float_order(b.y));
-            atomicMax(&fh->acc[2], float_order(-b.z));
-            atomicMax(&fh->acc[3], float_order(b.w));
+        if (t < 4 && b.x <= b.y) {
+            // Frame-wide maxima: every CTA would otherwise hit the same four words; an atomic is only needed when
+            // this CTA's value exceeds what is already there (a stale read just costs one unneeded atomic).
+            const float v = t == 0 ? -b.x : t == 1 ? b.y : t == 2 ? -b.z : b.w;
+            const uint32_t code = float_order(v);
+            volatile uint32_t *acc = fh->acc;
+            if (code > acc[t]) atomicMax(&fh->acc[t], code);
         }
     }
 }

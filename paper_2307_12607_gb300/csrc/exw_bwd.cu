@@ -37,8 +37,9 @@ __global__ void __launch_bounds__(kBwdThreads) backward_kernel(const float *__re
             const uint32_t db = __float_as_uint(__ldg(depth + i));
             const uint32_t ux = __float_as_uint(__ldg(mv + i)), uy = __float_as_uint(__ldg(mv + plane + i));
             if (depth_ok(db) && finite_bits(ux) && finite_bits(uy)) {
-                int ox = 0, oy = 0;
-                const bool lands = axis_off(axis_dec(ux, L), k, ox) && axis_off(axis_dec(uy, L), k, oy);
+                const AxisDec dx = axis_dec(ux, L), dy = axis_dec(uy, L);
+                const bool lands = dx.land && dy.land;
+                const int ox = axis_off(dx, k), oy = axis_off(dy, k);
                 const int qx = px + ox, qy = py + oy;
                 if (lands && qx >= 0 && qx < W && qy >= 0 && qy < H) {
                     const size_t q = (size_t)qy * W + qx;

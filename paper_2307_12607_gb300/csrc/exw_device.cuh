@@ -33,39 +33,34 @@ __device__ __forceinline__ float pow2_neg(int n) {  // 2^-n for n in [-126, 126]
 // Exact target offset off = floor(1/2 + k * mv / 2^L).
 //
 // A finite float mv is sM * 2^(e - 150) with |sM| < 2^24, so k*mv/2^L = k*sM * 2^-n with n = 150 + L - e.  For
-// k <= 64, |k*sM| < 2^30, and rounding half up is an arithmetic shift: off = (k*sM + 2^(n-1)) >> n.  n >= 32 means
-// |d| < 1/4 (off = 0); n <= 0 means |d| >= 2^23 (cannot land in any frame).  The decomposition is shared by all
-// fractions, so each extra fraction costs one multiply-add and one shift.
+// k <= 64, |k*sM| < 2^30, and rounding half up is an arithmetic shift: off = (k*sM + 2^(n-1)) >> n.  For n >= 32
+// (|d| < 1/4) the same expression with n clamped to 31 gives 0, since |k*sM| < 2^30; n <= 0 means |d| >= 2^23,
+// which cannot land in any frame.  The decomposition is shared by all fractions, so each fraction costs one
+// multiply-add and one shift, without branches.
 // ------------------------------------------------------------------------------------------------------------
 struct AxisDec {
-    int sM;  // signed significand
-    int n;   // right-shift amount
+    int sM;     // signed significand
+    int n;      // right-shift amount, clamped to [1, 31]
+    int half;   // 2^(n-1)
+    bool land;  // false when the motion is too large to land in any frame
 };
 
 __device__ __forceinline__ AxisDec axis_dec(uint32_t u, int L) {
     const uint32_t E = (u >> 23) & 0xFFu;
     const int M = (int)((u & 0x7FFFFFu) | (E ? 0x800000u : 0u));
+    const int n = 150 + L - (E ? (int)E : 1);
     AxisDec d;
     d.sM = (u >> 31) ? -M : M;
-    d.n = 150 + L - (E ? (int)E : 1);
+    d.land = n > 0;
+    d.n = min(max(n, 1), 31);
+    d.half = 1 << (d.n - 1);
     return d;
 }
 
-// Returns false when the offset cannot land in any frame (|offset| >= 2^23).
-__device__ __forceinline__ bool axis_off(const AxisDec &d, int k, int &off) {
-    if (d.n >= 32 || d.sM == 0 || k == 0) {
-        off = 0;
-        return true;
-    }
-    if (d.n <= 0) return false;
-    off = (k * d.sM + (1 << (d.n - 1))) >> d.n;
-    return true;
-}
+__device__ __forceinline__ int axis_off(const AxisDec &d, int k) { return (k * d.sM + d.half) >> d.n; }
 
 __device__ __forceinline__ int axis_off_of(uint32_t bits, int k, int L) {  // for clamped bounds (always lands)
-    int off = 0;
-    axis_off(axis_dec(bits, L), k, off);
-    return off;
+    return axis_off(axis_dec(bits, L), k);
 }
 
 // Residual rho = t - k*mv/2^L for a winner displaced by the whole-pixel offset t (|rho| <= 1/2).  One fused
@@ -118,10 +113,13 @@ struct GlobalAcc {
     int W;
     size_t plane;
     __device__ __forceinline__ size_t at(int x, int y) const { return (size_t)y * W + x; }
-    __device__ __forceinline__ float d(int x, int y) const { return __ldg(depth + at(x, y)); }
-    __device__ __forceinline__ float mx(int x, int y) const { return __ldg(mv + at(x, y)); }
-    __device__ __forceinline__ float my(int x, int y) const { return __ldg(mv + plane + at(x, y)); }
-    __device__ __forceinline__ float c(int ch, int x, int y) const { return load_c<CT>(col + ch * plane + at(x, y)); }
+    __device__ __forceinline__ size_t stride() const { return (size_t)W; }
+    __device__ __forceinline__ int safe_x() const { return 0; }  // a pixel every access may use
+    __device__ __forceinline__ int safe_y() const { return 0; }
+    __device__ __forceinline__ float d(size_t i) const { return __ldg(depth + i); }
+    __device__ __forceinline__ float mx(size_t i) const { return __ldg(mv + i); }
+    __device__ __forceinline__ float my(size_t i) const { return __ldg(mv + plane + i); }
+    __device__ __forceinline__ float c(int ch, size_t i) const { return load_c<CT>(col + ch * plane + i); }
 };
 
 template <typename CT, int WX, int WY>
@@ -136,10 +134,13 @@ struct WinAcc {
     const Window<CT, WX, WY> *w;
     int x0, y0;
     __device__ __forceinline__ int at(int x, int y) const { return (y - y0) * WX + (x - x0); }
-    __device__ __forceinline__ float d(int x, int y) const { return w->depth[at(x, y)]; }
-    __device__ __forceinline__ float mx(int x, int y) const { return w->mv[0][at(x, y)]; }
-    __device__ __forceinline__ float my(int x, int y) const { return w->mv[1][at(x, y)]; }
-    __device__ __forceinline__ float c(int ch, int x, int y) const { return to_f<CT>(w->col[ch][at(x, y)]); }
+    __device__ __forceinline__ int stride() const { return WX; }
+    __device__ __forceinline__ int safe_x() const { return x0 + 1; }  // its taps stay inside the window
+    __device__ __forceinline__ int safe_y() const { return y0 + 1; }
+    __device__ __forceinline__ float d(int i) const { return w->depth[i]; }
+    __device__ __forceinline__ float mx(int i) const { return w->mv[0][i]; }
+    __device__ __forceinline__ float my(int i) const { return w->mv[1][i]; }
+    __device__ __forceinline__ float c(int ch, int i) const { return to_f<CT>(w->col[ch][i]); }
 };
 
 // ------------------------------------------------------------------------------------------------------------
@@ -169,39 +170,42 @@ __device__ __forceinline__ bool tap_agrees(float Dt, float Dp) { return 32.0f * 
 template <class Acc>
 __device__ __forceinline__ void gather_at(const Acc &a, uint32_t dbits, int px, int py, int qx, int qy, int k, int L,
                                           int W, int H, float out[3]) {
+    const auto i00 = a.at(px, py);
     int sx, sy;
-    const float rx = residual(a.mx(px, py), k, L, qx - px, sx);
-    const float ry = residual(a.my(px, py), k, L, qy - py, sy);
+    const float rx = residual(a.mx(i00), k, L, qx - px, sx);
+    const float ry = residual(a.my(i00), k, L, qy - py, sy);
     const float Dp = __uint_as_float(dbits);
     const float ax = fabsf(rx), ay = fabsf(ry);
     const float wx0 = 1.0f - ax, wy0 = 1.0f - ay;
-    const int tx = px + sx, ty = py + sy;
-    const bool inx = sx != 0 && (unsigned)tx < (unsigned)W;
-    const bool iny = sy != 0 && (unsigned)ty < (unsigned)H;
+    const bool inx = sx != 0 && (unsigned)(px + sx) < (unsigned)W;
+    const bool iny = sy != 0 && (unsigned)(py + sy) < (unsigned)H;
+    const auto i10 = i00 + sx;
+    const auto i01 = sy > 0 ? i00 + a.stride() : i00 - a.stride();
+    const auto i11 = i01 + sx;
     float w = wx0 * wy0;
     float den = w;
-    float n0 = w * a.c(0, px, py), n1 = w * a.c(1, px, py), n2 = w * a.c(2, px, py);
-    if (inx && tap_agrees(a.d(tx, py), Dp)) {
+    float n0 = w * a.c(0, i00), n1 = w * a.c(1, i00), n2 = w * a.c(2, i00);
+    if (inx && tap_agrees(a.d(i10), Dp)) {
         w = ax * wy0;
         den += w;
-        n0 += w * a.c(0, tx, py);
-        n1 += w * a.c(1, tx, py);
-        n2 += w * a.c(2, tx, py);
+        n0 += w * a.c(0, i10);
+        n1 += w * a.c(1, i10);
+        n2 += w * a.c(2, i10);
     }
     if (iny) {
-        if (tap_agrees(a.d(px, ty), Dp)) {
+        if (tap_agrees(a.d(i01), Dp)) {
             w = wx0 * ay;
             den += w;
-            n0 += w * a.c(0, px, ty);
-            n1 += w * a.c(1, px, ty);
-            n2 += w * a.c(2, px, ty);
+            n0 += w * a.c(0, i01);
+            n1 += w * a.c(1, i01);
+            n2 += w * a.c(2, i01);
         }
-        if (inx && tap_agrees(a.d(tx, ty), Dp)) {
+        if (inx && tap_agrees(a.d(i11), Dp)) {
             w = ax * ay;
             den += w;
-            n0 += w * a.c(0, tx, ty);
-            n1 += w * a.c(1, tx, ty);
-            n2 += w * a.c(2, tx, ty);
+            n0 += w * a.c(0, i11);
+            n1 += w * a.c(1, i11);
+            n2 += w * a.c(2, i11);
         }
     }
     const float inv = __frcp_rn(den);
@@ -211,20 +215,12 @@ __device__ __forceinline__ void gather_at(const Acc &a, uint32_t dbits, int px, 
 }
 
 // ------------------------------------------------------------------------------------------------------------
-// Pull-push inside one 32 x 32 fill tile (levels 1..5 of the frame's pyramid: tiles are aligned to 32, so every
-// ancestor up to level 5 of a tile pixel is computed from that tile alone; out-of-frame pixels are invalid,
-// which reproduces the ceil-halving level sizes).
+// Pull-push inside one 32 x 32 fill tile.  Tiles are aligned to 32, so every ancestor up to level 5 of a tile pixel
+// is computed from that tile alone; out-of-frame pixels are invalid, which reproduces the ceil-halving level sizes.
+// Warp w of 16 owns tile rows 2w and 2w+1 (lane = column).
 // ------------------------------------------------------------------------------------------------------------
-struct FillSmem {
-    float v0[3][kFillTile][kFillTile];  // level 0 colour (already rounded to the storage type)
-    uint8_t m0[kFillTile][kFillTile];   // level 0 validity
-    float4 lv[341];                     // levels 1..5: 16x16, 8x8, 4x4, 2x2, 1x1 (rgb, validity)
-};
-__device__ __forceinline__ int lv_offset(int l) {  // l in 1..5
-    return l == 1 ? 0 : l == 2 ? 256 : l == 3 ? 320 : l == 4 ? 336 : 340;
-}
 
-// Mean of the valid children, taken in the order (0,0),(0,1),(1,0),(1,1) (row, column).
+// Mean of the valid children, taken in the order (0,0),(0,1),(1,0),(1,1) (row, column); .w = validity.
 __device__ __forceinline__ float4 mean4(float4 c0, float4 c1, float4 c2, float4 c3) {
     float a0 = 0.f, a1 = 0.f, a2 = 0.f;
     int cnt = 0;
@@ -233,52 +229,71 @@ __device__ __forceinline__ float4 mean4(float4 c0, float4 c1, float4 c2, float4 
     if (c2.w != 0.0f) { a0 += c2.x; a1 += c2.y; a2 += c2.z; ++cnt; }
     if (c3.w != 0.0f) { a0 += c3.x; a1 += c3.y; a2 += c3.z; ++cnt; }
     if (cnt == 0) return make_float4(0.f, 0.f, 0.f, 0.f);
-    const float fc = (float)cnt;
-    return make_float4(a0 / fc, a1 / fc, a2 / fc, 1.0f);
+    const float inv = cnt == 1 ? 1.0f : cnt == 2 ? 0.5f : cnt == 3 ? (1.0f / 3.0f) : 0.25f;
+    return make_float4(a0 * inv, a1 * inv, a2 * inv, 1.0f);
 }
 
-// Build levels 1..5 from v0/m0.  Must be called by all threads of the block (contains barriers); v0/m0 must be
-// complete on entry.
-__device__ __forceinline__ void pull_tile(FillSmem &s) {
-    const int t = threadIdx.x;
-    const int nt = blockDim.x;
-    for (int node = t; node < 256; node += nt) {
-        const int i = node >> 4, j = node & 15;
-        const int y = 2 * i, x = 2 * j;
-        float4 c[4];
+__device__ __forceinline__ float4 shfl4_xor(float4 v, int m) {
+    return make_float4(__shfl_xor_sync(0xFFFFFFFFu, v.x, m), __shfl_xor_sync(0xFFFFFFFFu, v.y, m),
+                       __shfl_xor_sync(0xFFFFFFFFu, v.z, m), __shfl_xor_sync(0xFFFFFFFFu, v.w, m));
+}
+
+// Pyramid levels 1..5 of one 32 x 32 tile in shared memory: 16x16, 8x8, 4x4, 2x2, 1x1 nodes.
+struct TilePyr {
+    float4 l1[256];
+    float4 l2[64];
+    float4 l3[16];
+    float4 l4[4];
+    float4 l5;
+};
+
+// Build the pyramid from this thread's two pixels (tile rows 2w and 2w+1 of column lane; .w = validity) with
+// 16 warps per CTA.  Level 1 is formed in registers (warp shuffle with the neighbouring column), levels 2..5 by
+// warp 0.  Contains two block barriers, which every thread must reach.  Returns this thread's level-1 node.
+__device__ __forceinline__ float4 build_pyramid(TilePyr &t, float4 top, float4 bot) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const float4 ptop = shfl4_xor(top, 1), pbot = shfl4_xor(bot, 1);
+    const float4 n1 = (lane & 1) ? mean4(ptop, top, pbot, bot) : mean4(top, ptop, bot, pbot);
+    if ((lane & 1) == 0) t.l1[wid * 16 + (lane >> 1)] = n1;
+    __syncthreads();
+    if (wid == 0) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int yy = y + (q >> 1), xx = x + (q & 1);
-            c[q] = s.m0[yy][xx] ? make_float4(s.v0[0][yy][xx], s.v0[1][yy][xx], s.v0[2][yy][xx], 1.0f)
-                                : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int h = 0; h < 2; ++h) {
+            const int node = lane + 32 * h, i = node >> 3, j = node & 7;
+            const float4 *c = t.l1 + (2 * i) * 16 + 2 * j;
+            t.l2[node] = mean4(c[0], c[1], c[16], c[17]);
         }
-        s.lv[node] = mean4(c[0], c[1], c[2], c[3]);
+        __syncwarp();
+        if (lane < 16) {
+            const int i = lane >> 2, j = lane & 3;
+            const float4 *c = t.l2 + (2 * i) * 8 + 2 * j;
+            t.l3[lane] = mean4(c[0], c[1], c[8], c[9]);
+        }
+        __syncwarp();
+        if (lane < 4) {
+            const int i = lane >> 1, j = lane & 1;
+            const float4 *c = t.l3 + (2 * i) * 4 + 2 * j;
+            t.l4[lane] = mean4(c[0], c[1], c[4], c[5]);
+        }
+        __syncwarp();
+        if (lane == 0) t.l5 = mean4(t.l4[0], t.l4[1], t.l4[2], t.l4[3]);
     }
     __syncthreads();
-#pragma unroll 1
-    for (int l = 2; l <= 5; ++l) {
-        const int lg = 5 - l;                 // log2 of this level's side
-        const int side = 1 << lg, cside = side * 2;
-        const int po = lv_offset(l), co = lv_offset(l - 1);
-        for (int node = t; node < side * side; node += nt) {
-            const int i = node >> lg, j = node & (side - 1);
-            const float4 *c = s.lv + co + (2 * i) * cside + 2 * j;
-            s.lv[po + node] = mean4(c[0], c[1], c[cside], c[cside + 1]);
-        }
-        __syncthreads();
-    }
+    return n1;
 }
 
-// Value pushed down to tile pixel (y, x): its first valid ancestor among levels 1..5; .w = 0 when the whole
-// tile is invalid (the coarse levels decide).
-__device__ __forceinline__ float4 push_value(const FillSmem &s, int y, int x) {
-#pragma unroll
-    for (int l = 1; l <= 5; ++l) {
-        const int side = kFillTile >> l;
-        const float4 v = s.lv[lv_offset(l) + (y >> l) * side + (x >> l)];
-        if (v.w != 0.0f) return v;
-    }
-    return make_float4(0.f, 0.f, 0.f, 0.f);
+// Value pushed down to a pixel of this thread (tile row 2w or 2w+1, column lane): its first valid ancestor; .w = 0
+// when the whole tile is invalid.  n1 is the thread's level-1 node.
+__device__ __forceinline__ float4 push_value(const TilePyr &t, float4 n1) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (n1.w != 0.0f) return n1;
+    const float4 v2 = t.l2[(wid >> 1) * 8 + (lane >> 2)];
+    if (v2.w != 0.0f) return v2;
+    const float4 v3 = t.l3[(wid >> 2) * 4 + (lane >> 3)];
+    if (v3.w != 0.0f) return v3;
+    const float4 v4 = t.l4[(wid >> 3) * 2 + (lane >> 4)];
+    if (v4.w != 0.0f) return v4;
+    return t.l5;
 }
 
 // Ordered encoding of a non-NaN float for unsigned atomicMax: larger float <-> larger code, and 0 is below every

@@ -21,14 +21,25 @@ struct FrameHeader {
     uint32_t ninvalid[3];  // fill tiles without any valid pixel, per fraction
     uint32_t status;       // reserved
     uint32_t queue;        // next tile of the persistent kernel
-    uint32_t nmode[3];     // tiles staged with one window / one window per fraction / from global memory
-    uint32_t pad[3];
+    uint32_t nmode[4];     // tiles done as uniform / one window / one window per fraction / from global memory
+    uint32_t pad[2];
 };
 static_assert(sizeof(FrameHeader) == 64, "FrameHeader is 64 bytes");
 
+// Per target tile, how the fused pass stages its sources (written by the plan kernel).
+struct TilePlan {
+    int mode;          // 0 uniform motion, 1 one window, 2 one window per fraction, 3 global memory, 4 nothing lands
+    int wx0, wy0;      // window origin (modes 0 and 1)
+    int pad0;
+    int rect[3][4];    // per fraction, landing rectangle x0, x1, y0, y1 (source pixels; empty if x1 < x0)
+    uint32_t umx, umy; // the one motion of a uniform tile (float bits)
+    int pad1[2];
+};
+static_assert(sizeof(TilePlan) == 80, "TilePlan is 80 bytes");
+
 // Byte offsets of the workspace sections for nframes frames of W x H with nfrac fractions.
 struct WsLayout {
-    size_t headers, tile_bounds, nodes, list, fillval, coarse, keys, total;
+    size_t headers, tile_bounds, plans, nodes, list, fillval, coarse, keys, total;
     int nbx, nby;       // motion-bounds tiles
     int n5x, n5y;       // fill tiles (level-5 nodes of the pyramid)
     int ncoarse;        // pyramid nodes above level 5, per fraction
@@ -57,6 +68,8 @@ inline WsLayout ws_layout(int W, int H, int nframes, int nfrac, bool with_keys) 
     off += align_up((size_t)nframes * sizeof(FrameHeader));
     l.tile_bounds = off;
     off += align_up((size_t)l.nbx * l.nby * 16);
+    l.plans = off;
+    off += align_up(n5 * sizeof(TilePlan));
     l.nodes = off;
     off += align_up((size_t)nfrac * n5 * 16);
     l.list = off;
@@ -82,6 +95,7 @@ struct TileParams {
     void *out_color[3];
     uint8_t *out_mask[3];
     const float4 *tile_bounds;
+    TilePlan *plans;            // [n5] staging plan per target tile (persistent TMA kernel)
     int nbx, nby;
     FrameHeader *fh;
     float4 *nodes;              // [nfrac][n5]
@@ -112,6 +126,7 @@ cudaError_t launch_bounds_finalize(const FrameHeader *fh, float *frame_bounds, c
 cudaError_t launch_fused(const TileParams &p, exw_dtype cdt, bool fill, cudaStream_t s);
 cudaError_t launch_fused_tma(const TileParams &p, const TmaMaps &m, exw_dtype cdt, bool fill, int grid,
                              cudaStream_t s);
+cudaError_t launch_plan(const TileParams &p, exw_dtype cdt, cudaStream_t s);
 cudaError_t launch_warp_tiles(const TileParams &p, exw_dtype cdt, cudaStream_t s);
 cudaError_t launch_fill_tiles(const TileParams &p, exw_dtype cdt, cudaStream_t s);
 cudaError_t launch_fixup(const TileParams &p, exw_dtype cdt, cudaStream_t s);

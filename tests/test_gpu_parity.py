@@ -197,12 +197,39 @@ def test_tma_staging_modes_cover_all_tiles(b):
     ws = b.workspace(b.exw_workspace_bytes(b.OP_EXTRAPOLATE, 320, 192, b.F32, 1, 3), c.device)
     out, mask = b.exw_extrapolate(c, d, m, ws=ws)
     st = b.frame_stats(ws)
-    assert st["tiles_window_all"] + st["tiles_window_each"] + st["tiles_global"] == 10 * 6
+    assert st["tiles_uniform"] + st["tiles_window_all"] + st["tiles_window_each"] + st["tiles_global"] == 10 * 6
     assert st["tiles_window_all"] > 0 and st["tiles_global"] + st["tiles_window_each"] > 0
     ref = oracle.extrapolate(color.astype(np.float64), depth, mv, 3)
     for j, (wo, wm, _) in enumerate(ref):
         np.testing.assert_array_equal(mask[j].cpu().numpy(), wm)
         np.testing.assert_allclose(out[j].cpu().numpy(), wo, rtol=0, atol=2e-6)
+
+
+def test_uniform_tiles_with_foreign_motion_inside_their_source(b):
+    # a uniformly panning background holds a small object moving so fast that it lands far away: tiles whose
+    # candidate sources all pan are uniform, yet their source window contains the object's pixels, which must not
+    # be taken as winners
+    W, H = 256, 128
+    color = np.random.default_rng(7).uniform(size=(3, H, W)).astype(np.float32)
+    depth = np.full((H, W), 50.0, np.float32)
+    mv = np.zeros((2, H, W), np.float32)
+    mv[0] = 2.0
+    depth[40:60, 100:120] = 10.0
+    mv[0, 40:60, 100:120] = 40.0
+    mv[1, 40:60, 100:120] = -1.5
+    depth[5, 5] = np.nan                       # an invalid source pixel inside a uniform tile
+    mv[0, 90, 200] = -2.0                      # and one with a different (slow) motion
+    c, d, m = dev(color), dev(depth), dev(mv)
+    ws = b.workspace(b.exw_workspace_bytes(b.OP_EXTRAPOLATE, W, H, b.F32, 1, 3), c.device)
+    for fill in (True, False):
+        out, mask = b.exw_extrapolate(c, d, m, fill=fill, ws=ws)
+        assert b.frame_stats(ws)["tiles_uniform"] > 0
+        ref = oracle.extrapolate(color.astype(np.float64), depth, mv, 3, fill=fill)
+        for j, (wo, wm, _) in enumerate(ref):
+            np.testing.assert_array_equal(mask[j].cpu().numpy(), wm)
+            np.testing.assert_allclose(out[j].cpu().numpy(), wo, rtol=0, atol=2e-6)
+        o2, m2 = b.exw_extrapolate(c, d, m, fill=fill, tma=False)
+        assert torch.equal(m2, mask) and torch.equal(o2.view(torch.int32), out.view(torch.int32))
 
 
 def test_extrapolate_fewer_fractions_and_sequences(b):
@@ -351,6 +378,8 @@ def test_full_size_4k_fp16(b):
             np.testing.assert_array_equal(mask[j].cpu().numpy(), wm)
             np.testing.assert_allclose(out[j].float().cpu().numpy().astype(np.float64), wo, rtol=0, atol=1e-3)
         assert (mask != 0).float().mean().item() > 0.01      # the occluders open real holes
+        o2, m2 = b.exw_extrapolate(c, d, m, nfrac=3, fill=fill, tma=False)
+        assert torch.equal(m2, mask) and torch.equal(o2.view(torch.int16), out.view(torch.int16))
 
 
 def test_full_size_1080p_sequence_sampled(b):
@@ -386,4 +415,4 @@ def test_timing_and_launch_count(b):
     ms, n = b.exw_timing_query("exw_fused_tma")
     assert n == 1 and ms > 0
     b.exw_timing_enable(False)
-    assert b.exw_launch_count() - n0 == 4   # zero, bounds, fused, fixup
+    assert b.exw_launch_count() - n0 == 5   # zero, bounds, plan, fused, fixup
