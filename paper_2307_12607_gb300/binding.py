@@ -196,6 +196,63 @@ def exw_extrapolate(color, depth, mv, nfrac: int = 3, fill: bool = True, out=Non
     return out, mask
 
 
+def exw_tuner_create() -> int:
+    """Host-side autotuner handle for exw_extrapolate_batched (free it with exw_tuner_destroy)."""
+    return int(lib().exw_tuner_create())
+
+
+def exw_tuner_destroy(tuner: int):
+    lib().exw_tuner_destroy(tuner)
+
+
+def exw_tuner_report(tuner: int) -> str:
+    need = int(lib().exw_tuner_report(tuner, None, 0))
+    buf = ctypes.create_string_buffer(need)
+    lib().exw_tuner_report(tuner, buf, need)
+    return buf.value.decode()
+
+
+def _stream_descs(streams, outs, nfrac):
+    descs = (_lib.ExwStreamDesc * len(streams))()
+    for i, ((color, depth, mv), (out, mask)) in enumerate(zip(streams, outs)):
+        H, W = int(depth.shape[0]), int(depth.shape[1])
+        _dev(color, "color", None, (3, H, W))
+        _dev(depth, "depth", torch.float32, (H, W))
+        _dev(mv, "mv", torch.float32, (2, H, W))
+        _dev(out, "out", color.dtype, (nfrac, 3, H, W))
+        _dev(mask, "mask", torch.uint8, (nfrac, H, W))
+        descs[i].src = _lib.ExwFrame(color.data_ptr(), depth.data_ptr(), mv.data_ptr(), W, H, _cdt(color))
+        for j in range(nfrac):
+            descs[i].out[j] = _lib.ExwFrameOut(out[j].data_ptr(), mask[j].data_ptr())
+    return descs
+
+
+def exw_batched_workspace_bytes(streams, nfrac: int = 3) -> int:
+    descs = (_lib.ExwStreamDesc * len(streams))()
+    for i, (color, depth, mv) in enumerate(streams):
+        descs[i].src = _lib.ExwFrame(0, 0, 0, int(depth.shape[1]), int(depth.shape[0]), _cdt(color))
+    return int(lib().exw_batched_workspace_bytes(ctypes.cast(descs, ctypes.c_void_p), len(streams), int(nfrac)))
+
+
+def exw_extrapolate_batched(streams, nfrac: int = 3, fill: bool = True, outs=None, ws=None, tuner=None, stream=None,
+                            tma: bool = True):
+    """All stages for many independent streams in one persistent launch.  ``streams`` is a list of (colour
+    [3][H][W], depth [H][W], motion [2][H][W]) with per-stream sizes and colour types.  Returns a list of
+    (out [nfrac][3][H][W], mask [nfrac][H][W]).  ``tuner``: handle from exw_tuner_create (or None)."""
+    dev = streams[0][0].device
+    if outs is None:
+        outs = [(torch.empty((nfrac,) + tuple(c.shape), dtype=c.dtype, device=dev),
+                 torch.empty((nfrac,) + tuple(d.shape), dtype=torch.uint8, device=dev)) for c, d, _ in streams]
+    descs = _stream_descs(streams, outs, nfrac)
+    need = int(lib().exw_batched_workspace_bytes(ctypes.cast(descs, ctypes.c_void_p), len(streams), int(nfrac)))
+    if ws is None:
+        ws = workspace(need, dev)
+    flags = (0 if fill else FLAG_NO_FILL) | (0 if tma else FLAG_NO_TMA)
+    _check(lib().exw_extrapolate_batched(ctypes.cast(descs, ctypes.c_void_p), len(streams), int(nfrac), flags,
+                                         ws.data_ptr(), ws.numel(), tuner or None, _stream(stream, dev)))
+    return outs
+
+
 def exw_warp_backward(grad_out, color, depth, mv, keys, k: int, denom: int = 4, grad_color=None, grad_mv=None,
                       ws=None, stream=None):
     """Adjoint of stage (b); accumulates into (and returns) grad_color [3][H][W] and grad_mv [2][H][W] float32.

@@ -1,6 +1,5 @@
 // exw_aux.cu -- global-memory splat, motion bounds, workspace clearing and the L2 loss.
-#include "exw_device.cuh"
-#include "exw_internal.h"
+#include "exw_items.cuh"
 
 namespace exw {
 
@@ -32,71 +31,11 @@ __global__ void __launch_bounds__(256) splat_global_kernel(const float *__restri
     atomicMin(keys + (size_t)gy * W + gx, (unsigned long long)pack_key_global(db, (uint32_t)i));
 }
 
-// Stage (a0): per 8x8 tile and per frame, min/max of each motion component over pixels that can land, clamped
-// to [-65536, 65536] (for k/4 fractions, |d| >= 16384 beyond that: no landing in any frame) and -0 read as +0.
-// CTA = 32 x 32 source pixels; lane = x (coalesced rows), warp w covers rows 4w .. 4w+3 (one 8-row tile band).
+// Stage (a0): one 32 x 32 source region per CTA.
 __global__ void __launch_bounds__(256) bounds_kernel(const float *__restrict__ depth, const float *__restrict__ mv,
                                                      int W, int H, float4 *tile_bounds, FrameHeader *fh) {
-    __shared__ float4 part[8][4];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int X0 = blockIdx.x * 32, Y0 = blockIdx.y * 32;
-    const size_t plane = (size_t)W * H;
-    float mnx = __int_as_float(0x7F800000), mxx = -mnx, mny = mnx, mxy = -mnx;
-    const int x = X0 + lane;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int y = Y0 + 4 * w + r;
-        if (x < W && y < H) {
-            const size_t i = (size_t)y * W + x;
-            const uint32_t db = __float_as_uint(__ldg(depth + i));
-            const float fx = __ldg(mv + i), fy = __ldg(mv + plane + i);
-            if (depth_ok(db) && finite_bits(__float_as_uint(fx)) && finite_bits(__float_as_uint(fy))) {
-                const float cx = fminf(fmaxf(fx, -65536.0f), 65536.0f) + 0.0f;
-                const float cy = fminf(fmaxf(fy, -65536.0f), 65536.0f) + 0.0f;
-                mnx = fminf(mnx, cx);
-                mxx = fmaxf(mxx, cx);
-                mny = fminf(mny, cy);
-                mxy = fmaxf(mxy, cy);
-            }
-        }
-    }
-#pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
-        mnx = fminf(mnx, __shfl_xor_sync(0xFFFFFFFFu, mnx, o));
-        mxx = fmaxf(mxx, __shfl_xor_sync(0xFFFFFFFFu, mxx, o));
-        mny = fminf(mny, __shfl_xor_sync(0xFFFFFFFFu, mny, o));
-        mxy = fmaxf(mxy, __shfl_xor_sync(0xFFFFFFFFu, mxy, o));
-    }
-    if ((lane & 7) == 0) part[w][lane >> 3] = make_float4(mnx, mxx, mny, mxy);
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        const int t = threadIdx.x;
-        float4 b = make_float4(__int_as_float(0x7F800000), __int_as_float(0xFF800000), __int_as_float(0x7F800000),
-                               __int_as_float(0xFF800000));
-        if (t < 16) {
-            const int bxl = t & 3, byl = t >> 2;
-            const float4 u = part[2 * byl][bxl], v = part[2 * byl + 1][bxl];
-            b = make_float4(fminf(u.x, v.x), fmaxf(u.y, v.y), fminf(u.z, v.z), fmaxf(u.w, v.w));
-            const int gbx = X0 / 8 + bxl, gby = Y0 / 8 + byl;
-            const int nbx = (W + 7) / 8, nby = (H + 7) / 8;
-            if (gbx < nbx && gby < nby) tile_bounds[(size_t)gby * nbx + gbx] = b;
-        }
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            b.x = fminf(b.x, __shfl_xor_sync(0xFFFFFFFFu, b.x, o));
-            b.y = fmaxf(b.y, __shfl_xor_sync(0xFFFFFFFFu, b.y, o));
-            b.z = fminf(b.z, __shfl_xor_sync(0xFFFFFFFFu, b.z, o));
-            b.w = fmaxf(b.w, __shfl_xor_sync(0xFFFFFFFFu, b.w, o));
-        }
-        if (t < 4 && b.x <= b.y) {
-            // Frame-wide maxima: every CTA would otherwise hit the same four words; an atomic is only needed when
-            // this CTA's value exceeds what is already there (a stale read just costs one unneeded atomic).
-            const float v = t == 0 ? -b.x : t == 1 ? b.y : t == 2 ? -b.z : b.w;
-            const uint32_t code = float_order(v);
-            volatile uint32_t *acc = fh->acc;
-            if (code > acc[t]) atomicMax(&fh->acc[t], code);
-        }
-    }
+    __shared__ float4 part[32];
+    bounds_region(depth, mv, W, H, tile_bounds, fh, blockIdx.x, blockIdx.y, part);
 }
 
 __global__ void bounds_finalize_kernel(const FrameHeader *fh, float *out) {

@@ -19,10 +19,11 @@ struct FrameHeader {
     uint32_t acc[4];       // ordered-float maxima of -min mv_x, max mv_x, -min mv_y, max mv_y (0 = none)
     uint32_t done;         // tiles finished (the CTA finishing the last one runs the coarse pyramid)
     uint32_t ninvalid[3];  // fill tiles without any valid pixel, per fraction
-    uint32_t status;       // reserved
+    uint32_t cready;       // batched path: the coarse values of this frame are written
     uint32_t queue;        // next tile of the persistent kernel
     uint32_t nmode[4];     // tiles done as uniform / one window / one window per fraction / from global memory
-    uint32_t pad[2];
+    uint32_t bdone;        // batched path: bounds regions finished
+    uint32_t pdone;        // batched path: plan groups finished
 };
 static_assert(sizeof(FrameHeader) == 64, "FrameHeader is 64 bytes");
 

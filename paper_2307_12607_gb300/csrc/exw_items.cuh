@@ -1,0 +1,381 @@
+// exw_items.cuh -- the work items of the forward pass as device functions of a whole CTA (or warp): a bounds
+// region, a tile plan, a fused tile (TMA windows or global memory), a fix-up slice.  The per-frame kernels launch
+// them one item per CTA or in a persistent loop; the batched kernel takes them from a work queue.
+#pragma once
+
+#include "exw_tile.cuh"
+#include "exw_tma.cuh"
+
+namespace exw {
+
+constexpr uint32_t kWaitLimit = 1u << 22;  // iterations of the bounded mbarrier wait (each >= 128 ns)
+
+template <typename CT, int WX, int WY>
+struct TmaSmem {
+    Window<CT, WX, WY> win;  // first: 128-byte aligned TMA destinations
+    TileSmem t;
+};
+
+template <typename CT, int WX, int WY>
+__device__ __forceinline__ Rect window_rect(Rect U) {  // window origin/extent for rectangle U grown by 1
+    constexpr int kAlign = sizeof(CT) == 2 ? 8 : 4;  // x * element size must be a multiple of 16 bytes
+    Rect w;
+    w.x0 = (U.x0 - 1) & ~(kAlign - 1);
+    w.y0 = U.y0 - 1;
+    w.x1 = w.x0 + WX - 1;
+    w.y1 = w.y0 + WY - 1;
+    return w;
+}
+
+template <typename CT, int WX, int WY>
+__device__ __forceinline__ bool window_fits(Rect U) {
+    const Rect w = window_rect<CT, WX, WY>(U);
+    return U.x1 + 1 <= w.x1 && U.y1 + 1 <= w.y1;
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Plan of one target tile (one warp): scans the 8 x 8 motion bounds that can reach the tile's region and
+// records the landing rectangle of every fraction, whether all candidate sources share one motion, and the
+// staging mode and window the fused kernel will use.
+// ------------------------------------------------------------------------------------------------------------
+template <typename CT, int WX, int WY>
+__device__ inline void plan_tile(const TileParams &p, int tile) {  // called by one whole warp
+    const int lane = threadIdx.x & 31;
+    const int X0 = (tile % p.n5x) * kFillTile, Y0 = (tile / p.n5x) * kFillTile;
+    const int RX0 = X0 - 1, RY0 = Y0 - 1;
+    int r[kMaxFrac][4];
+#pragma unroll
+    for (int kk = 0; kk < kMaxFrac; ++kk) {
+        r[kk][0] = r[kk][2] = 1 << 30;
+        r[kk][1] = r[kk][3] = -(1 << 30);
+    }
+    bool uni = true, has = false;
+    uint32_t mx = 0u, my = 0u;
+    int bx0, bx1, by0, by1;
+    if (frame_window(p, RX0, RY0, bx0, bx1, by0, by1)) {
+        const int nbxr = bx1 - bx0 + 1;
+        const int total = nbxr * (by1 - by0 + 1);
+        for (int idx = lane; idx < total; idx += 32) {
+            const int by = by0 + idx / nbxr, bx = bx0 + idx % nbxr;
+            const float4 b = __ldcg(p.tile_bounds + (size_t)by * p.nbx + bx);
+            if (!(b.x <= b.y)) continue;
+            bool cand = false;
+#pragma unroll
+            for (int kk = 0; kk < kMaxFrac; ++kk) {
+                if (kk >= p.nfrac) break;
+                int ox0, ox1, oy0, oy1;
+                tile_offsets(b, p.k0 + kk, p.L, ox0, ox1, oy0, oy1);
+                const int lx0 = max(8 * bx, RX0 - ox1), lx1 = min(min(8 * bx + 7, p.W - 1), RX0 + kRegion - 1 - ox0);
+                const int ly0 = max(8 * by, RY0 - oy1), ly1 = min(min(8 * by + 7, p.H - 1), RY0 + kRegion - 1 - oy0);
+                if (lx0 > lx1 || ly0 > ly1) continue;
+                cand = true;
+                r[kk][0] = min(r[kk][0], lx0);
+                r[kk][1] = max(r[kk][1], lx1);
+                r[kk][2] = min(r[kk][2], ly0);
+                r[kk][3] = max(r[kk][3], ly1);
+            }
+            if (cand) {
+                const uint32_t bxb = __float_as_uint(b.x), byb = __float_as_uint(b.z);
+                if (b.x != b.y || b.z != b.w) uni = false;
+                else if (!has) { has = true; mx = bxb; my = byb; }
+                else if (mx != bxb || my != byb) uni = false;
+            }
+        }
+    }
+#pragma unroll
+    for (int kk = 0; kk < kMaxFrac; ++kk) {
+        r[kk][0] = __reduce_min_sync(0xFFFFFFFFu, r[kk][0]);
+        r[kk][1] = __reduce_max_sync(0xFFFFFFFFu, r[kk][1]);
+        r[kk][2] = __reduce_min_sync(0xFFFFFFFFu, r[kk][2]);
+        r[kk][3] = __reduce_max_sync(0xFFFFFFFFu, r[kk][3]);
+    }
+    const unsigned hasm = __ballot_sync(0xFFFFFFFFu, has);
+    uni = __all_sync(0xFFFFFFFFu, uni) != 0;
+    if (hasm) {
+        const int src = __ffs(hasm) - 1;
+        const uint32_t m0 = __shfl_sync(0xFFFFFFFFu, mx, src), m1 = __shfl_sync(0xFFFFFFFFu, my, src);
+        uni = uni && __all_sync(0xFFFFFFFFu, !has || (mx == m0 && my == m1)) != 0;
+        mx = m0;
+        my = m1;
+    }
+    if (lane != 0) return;
+    TilePlan pl{};
+    Rect U{1 << 30, -(1 << 30), 1 << 30, -(1 << 30)};
+    bool all_fit = true;
+    for (int kk = 0; kk < p.nfrac; ++kk) {
+        const Rect R{r[kk][0], r[kk][1], r[kk][2], r[kk][3]};
+        pl.rect[kk][0] = R.x0;
+        pl.rect[kk][1] = R.x1;
+        pl.rect[kk][2] = R.y0;
+        pl.rect[kk][3] = R.y1;
+        if (R.empty()) continue;
+        U.x0 = min(U.x0, R.x0);
+        U.x1 = max(U.x1, R.x1);
+        U.y0 = min(U.y0, R.y0);
+        U.y1 = max(U.y1, R.y1);
+        all_fit = all_fit && window_fits<CT, WX, WY>(R);
+    }
+    constexpr int kAlign = sizeof(CT) == 2 ? 8 : 4;
+    pl.mode = -1;
+    pl.umx = mx;
+    pl.umy = my;
+    if (U.empty()) {
+        pl.mode = 4;
+    } else if (uni && hasm) {
+        // uniform: fraction kk's sources are R - o_kk; stage their union grown by one pixel (the taps)
+        Rect N{1 << 30, -(1 << 30), 1 << 30, -(1 << 30)};
+        for (int kk = 0; kk < p.nfrac; ++kk) {
+            const int ox = axis_off_of(mx, p.k0 + kk, p.L), oy = axis_off_of(my, p.k0 + kk, p.L);
+            N.x0 = min(N.x0, RX0 - ox - 1);
+            N.x1 = max(N.x1, RX0 + kRegion - ox);
+            N.y0 = min(N.y0, RY0 - oy - 1);
+            N.y1 = max(N.y1, RY0 + kRegion - oy);
+        }
+        N.x0 = max(N.x0, 0);
+        N.y0 = max(N.y0, 0);
+        N.x1 = min(N.x1, p.W - 1);
+        N.y1 = min(N.y1, p.H - 1);
+        if (!N.empty() && N.x1 < (N.x0 & ~(kAlign - 1)) + WX && N.y1 < N.y0 + WY) {
+            pl.mode = 0;
+            pl.wx0 = N.x0 & ~(kAlign - 1);
+            pl.wy0 = N.y0;
+        }
+    }
+    if (pl.mode < 0) {
+        if (window_fits<CT, WX, WY>(U)) {
+            const Rect w = window_rect<CT, WX, WY>(U);
+            pl.mode = 1;
+            pl.wx0 = w.x0;
+            pl.wy0 = w.y0;
+        } else {
+            pl.mode = all_fit ? 2 : 3;
+        }
+    }
+    p.plans[tile] = pl;
+}
+
+__device__ __forceinline__ Rect union_rect(const TilePlan &pl, int nfrac) {
+    Rect U{1 << 30, -(1 << 30), 1 << 30, -(1 << 30)};
+    for (int kk = 0; kk < nfrac; ++kk) {
+        const Rect R{__ldcg(&pl.rect[kk][0]), __ldcg(&pl.rect[kk][1]), __ldcg(&pl.rect[kk][2]),
+                     __ldcg(&pl.rect[kk][3])};
+        if (R.empty()) continue;
+        U.x0 = min(U.x0, R.x0);
+        U.x1 = max(U.x1, R.x1);
+        U.y0 = min(U.y0, R.y0);
+        U.y1 = max(U.y1, R.y1);
+    }
+    return U;
+}
+
+// Stage the window at (x0, y0) and wait for it.  Returns false (with the status word set) if the bounded wait ran
+// out; every thread returns the same value.  The leading barrier makes every thread finish with the previous
+// contents of the window before the copy overwrites them.
+template <typename CT, int WX, int WY>
+__device__ inline bool load_window(TmaSmem<CT, WX, WY> &s, const TileParams &p, const CUtensorMap *tcol,
+                            const CUtensorMap *tdep, const CUtensorMap *tmv, int x0, int y0, uint32_t &phase) {
+    constexpr uint32_t kBytes = WX * WY * (4 + 8 + 3 * (uint32_t)sizeof(CT));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&s.t.mbar, kBytes);
+        tma_load_2d(s.win.depth, tdep, x0, y0, &s.t.mbar);
+        tma_load_3d(&s.win.mv[0][0], tmv, x0, y0, 0, &s.t.mbar);
+        tma_load_3d(&s.win.col[0][0], tcol, x0, y0, 0, &s.t.mbar);
+    }
+    const bool ok = mbar_wait_bounded(&s.t.mbar, phase, kWaitLimit);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) atomicExch(p.status, (uint32_t)EXW_ERR_TIMEOUT);
+        mbar_wait_bounded(&s.t.mbar, phase ^ 1u, kWaitLimit);  // let the copy in flight land before leaving
+        return false;
+    }
+    return true;
+}
+
+// One target tile of the fused pass with TMA-staged windows (all threads of the CTA).  Returns false when a bounded
+// wait ran out (the status word is set).
+template <typename CT, int WX, int WY, bool FILL>
+__device__ bool tma_tile(TmaSmem<CT, WX, WY> &s, const TileParams &p, const CUtensorMap &tcol, const CUtensorMap &tdep,
+                         const CUtensorMap &tmv, int tile, uint32_t &phase) {
+    const int tid = threadIdx.x;
+    const GlobalAcc<CT> ga{(const CT *)p.color, p.depth, p.mv, p.W, (size_t)p.W * p.H};
+    const int X0 = (tile % p.n5x) * kFillTile, Y0 = (tile / p.n5x) * kFillTile;
+    const int RX0 = X0 - 1, RY0 = Y0 - 1;
+    const TilePlan &pl = p.plans[tile];
+    const int mode = __ldcg(&pl.mode);
+    if (tid == 0) atomicAdd(&p.fh->nmode[mode < 4 ? mode : 1], 1u);
+    if (mode == 0) {
+        const int x0 = __ldcg(&pl.wx0), y0 = __ldcg(&pl.wy0);
+        const uint32_t umx = __ldcg(&pl.umx), umy = __ldcg(&pl.umy);
+        if (!load_window(s, p, &tcol, &tdep, &tmv, x0, y0, phase)) return false;
+        const WinAcc<CT, WX, WY> wa{&s.win, x0, y0};
+        uint32_t *dw = reinterpret_cast<uint32_t *>(&s.t.key[0][0]);
+        for (int kk = 0; kk < p.nfrac; ++kk)
+            uniform_words(dw + kk * kRegionN, p, wa, axis_off_of(umx, p.k0 + kk, p.L),
+                          axis_off_of(umy, p.k0 + kk, p.L), __uint_as_float(umx), __uint_as_float(umy), RX0, RY0);
+        __syncthreads();
+        for (int kk = 0; kk < p.nfrac; ++kk)
+            finish_fraction<CT, FILL>(s.t, wa,
+                                      UniformSource{dw + kk * kRegionN, __uint_as_float(umx),
+                                                    __uint_as_float(umy), axis_off_of(umx, p.k0 + kk, p.L),
+                                                    axis_off_of(umy, p.k0 + kk, p.L)},
+                                      p, kk, X0, Y0, tile);
+    } else if (mode == 1) {
+        const int x0 = __ldcg(&pl.wx0), y0 = __ldcg(&pl.wy0);
+        const Rect U = union_rect(pl, p.nfrac);
+        init_keys(s.t, p.nfrac);
+        if (!load_window(s, p, &tcol, &tdep, &tmv, x0, y0, phase)) return false;
+        const WinAcc<CT, WX, WY> wa{&s.win, x0, y0};
+        splat_window(s.t, p, wa, U, (1u << p.nfrac) - 1u, RX0, RY0);
+        __syncthreads();
+        for (int kk = 0; kk < p.nfrac; ++kk)
+            finish_fraction<CT, FILL>(s.t, wa, key_source(s.t, kk), p, kk, X0, Y0, tile);
+    } else if (mode == 2) {
+        init_keys(s.t, p.nfrac);
+        for (int kk = 0; kk < p.nfrac; ++kk) {
+            const Rect R{__ldcg(&pl.rect[kk][0]), __ldcg(&pl.rect[kk][1]), __ldcg(&pl.rect[kk][2]),
+                         __ldcg(&pl.rect[kk][3])};
+            if (R.empty()) {
+                __syncthreads();
+                finish_fraction<CT, FILL>(s.t, ga, key_source(s.t, kk), p, kk, X0, Y0, tile);
+                continue;
+            }
+            const Rect w = window_rect<CT, WX, WY>(R);
+            if (!load_window(s, p, &tcol, &tdep, &tmv, w.x0, w.y0, phase)) return false;
+            const WinAcc<CT, WX, WY> wa{&s.win, w.x0, w.y0};
+            splat_window(s.t, p, wa, R, 1u << kk, RX0, RY0);
+            __syncthreads();
+            finish_fraction<CT, FILL>(s.t, wa, key_source(s.t, kk), p, kk, X0, Y0, tile);
+        }
+    } else {  // 3: too wide for a window; 4: nothing lands (every key stays empty)
+        init_keys(s.t, p.nfrac);
+        __syncthreads();
+        if (mode == 3) {
+            splat_global(s.t, p, RX0, RY0);
+            __syncthreads();
+        }
+        for (int kk = 0; kk < p.nfrac; ++kk)
+            finish_fraction<CT, FILL>(s.t, ga, key_source(s.t, kk), p, kk, X0, Y0, tile);
+    }
+    if (FILL) tile_done(p, &s.t.last);
+    return true;
+}
+
+// One target tile of the fused pass reading its sources from global memory (all threads of the CTA).
+template <typename CT, bool FILL>
+__device__ void plain_tile(TileSmem &s, const TileParams &p, int tile) {
+    const int X0 = (tile % p.n5x) * kFillTile, Y0 = (tile / p.n5x) * kFillTile;
+    init_keys(s, p.nfrac);
+    __syncthreads();
+    splat_global(s, p, X0 - 1, Y0 - 1);
+    __syncthreads();
+    const GlobalAcc<CT> a{(const CT *)p.color, p.depth, p.mv, p.W, (size_t)p.W * p.H};
+    for (int kk = 0; kk < p.nfrac; ++kk) finish_fraction<CT, FILL>(s, a, key_source(s, kk), p, kk, X0, Y0, tile);
+    if (FILL) tile_done(p, &s.last);
+}
+
+// Fix-up of the tiles without a valid pixel: this CTA takes list entries first, first + stride, ...
+template <typename CT>
+__device__ void fixup_slice(const TileParams &p, uint32_t first, uint32_t stride) {
+    const int n5 = p.n5x * p.n5y;
+    const size_t plane = (size_t)p.W * p.H;
+    for (int kk = 0; kk < p.nfrac; ++kk) {
+        const uint32_t cnt = __ldcg(&p.fh->ninvalid[kk]);
+        CT *oc = (CT *)p.out_color[kk];
+        for (uint32_t e = first; e < cnt; e += stride) {
+            const uint32_t tile = __ldcg(p.list + (size_t)kk * n5 + e);
+            const float4 v = __ldcg(p.fillval + (size_t)kk * n5 + e);
+            const int X0 = (int)(tile % (uint32_t)p.n5x) * kFillTile, Y0 = (int)(tile / (uint32_t)p.n5x) * kFillTile;
+            const CT c0 = to_storage<CT>(v.x), c1 = to_storage<CT>(v.y), c2 = to_storage<CT>(v.z);
+            for (int i = threadIdx.x; i < kFillTile * kFillTile; i += blockDim.x) {
+                const int gx = X0 + (i & 31), gy = Y0 + (i >> 5);
+                if (gx >= p.W || gy >= p.H) continue;
+                const size_t q = (size_t)gy * p.W + gx;
+                oc[q] = c0;
+                oc[plane + q] = c1;
+                oc[2 * plane + q] = c2;
+            }
+        }
+    }
+}
+
+// Stage (a0) for one 32 x 32 source region (all threads of the CTA, any multiple of 128 threads up to 1024):
+// per 8 x 8 tile the min/max of each motion component over pixels that can land, clamped to [-65536, 65536] (for
+// k/4 fractions |d| >= 16384 beyond that: no landing in any frame) and -0 read as +0; frame-wide maxima in fh.
+// Warp w covers the rows w*rpw .. w*rpw + rpw - 1 of the region (rpw = 32 / warps), lane = column.
+__device__ inline void bounds_region(const float *__restrict__ depth, const float *__restrict__ mv, int W, int H,
+                              float4 *tile_bounds, FrameHeader *fh, int rx, int ry, float4 *part) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int rpw = 32 / nw;
+    const int X0 = rx * 32, Y0 = ry * 32;
+    const size_t plane = (size_t)W * H;
+    float mnx = __int_as_float(0x7F800000), mxx = -mnx, mny = mnx, mxy = -mnx;
+    const int x = X0 + lane;
+    float fx[8], fy[8];
+    uint32_t db[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {  // issue every load of the thread before using any
+        db[r] = 0u;
+        fx[r] = fy[r] = 0.0f;
+        const int y = Y0 + w * rpw + r;
+        if (r < rpw && x < W && y < H) {
+            const size_t i = (size_t)y * W + x;
+            db[r] = __float_as_uint(__ldg(depth + i));
+            fx[r] = __ldg(mv + i);
+            fy[r] = __ldg(mv + plane + i);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        if (depth_ok(db[r]) && finite_bits(__float_as_uint(fx[r])) && finite_bits(__float_as_uint(fy[r]))) {
+            const float cx = fminf(fmaxf(fx[r], -65536.0f), 65536.0f) + 0.0f;
+            const float cy = fminf(fmaxf(fy[r], -65536.0f), 65536.0f) + 0.0f;
+            mnx = fminf(mnx, cx);
+            mxx = fmaxf(mxx, cx);
+            mny = fminf(mny, cy);
+            mxy = fmaxf(mxy, cy);
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        mnx = fminf(mnx, __shfl_xor_sync(0xFFFFFFFFu, mnx, o));
+        mxx = fmaxf(mxx, __shfl_xor_sync(0xFFFFFFFFu, mxx, o));
+        mny = fminf(mny, __shfl_xor_sync(0xFFFFFFFFu, mny, o));
+        mxy = fmaxf(mxy, __shfl_xor_sync(0xFFFFFFFFu, mxy, o));
+    }
+    if ((lane & 7) == 0) part[w * 4 + (lane >> 3)] = make_float4(mnx, mxx, mny, mxy);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int t = threadIdx.x;
+        float4 b = make_float4(__int_as_float(0x7F800000), __int_as_float(0xFF800000), __int_as_float(0x7F800000),
+                               __int_as_float(0xFF800000));
+        if (t < 16) {
+            const int bxl = t & 3, byl = t >> 2, per = nw / 4;  // warps per 8-row band
+            for (int i = 0; i < per; ++i) {
+                const float4 u = part[(byl * per + i) * 4 + bxl];
+                b = make_float4(fminf(b.x, u.x), fmaxf(b.y, u.y), fminf(b.z, u.z), fmaxf(b.w, u.w));
+            }
+            const int gbx = X0 / 8 + bxl, gby = Y0 / 8 + byl;
+            const int nbx = (W + 7) / 8, nby = (H + 7) / 8;
+            if (gbx < nbx && gby < nby) tile_bounds[(size_t)gby * nbx + gbx] = b;
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            b.x = fminf(b.x, __shfl_xor_sync(0xFFFFFFFFu, b.x, o));
+            b.y = fmaxf(b.y, __shfl_xor_sync(0xFFFFFFFFu, b.y, o));
+            b.z = fminf(b.z, __shfl_xor_sync(0xFFFFFFFFu, b.z, o));
+            b.w = fmaxf(b.w, __shfl_xor_sync(0xFFFFFFFFu, b.w, o));
+        }
+        if (t < 4 && b.x <= b.y) {
+            // Frame-wide maxima: an atomic only when this region's value exceeds what is already there (a stale
+            // read just costs one unneeded atomic).
+            const float v = t == 0 ? -b.x : t == 1 ? b.y : t == 2 ? -b.z : b.w;
+            const uint32_t code = float_order(v);
+            volatile uint32_t *acc = fh->acc;
+            if (code > acc[t]) atomicMax(&fh->acc[t], code);
+        }
+    }
+}
+
+}  // namespace exw

@@ -102,7 +102,7 @@ __device__ __forceinline__ void splat_window(TileSmem &s, const TileParams &p, c
 }
 
 // Splat from global memory: candidate 8 x 8 tiles (those whose bounds reach R), 64 threads per candidate.
-__device__ void splat_global(TileSmem &s, const TileParams &p, int RX0, int RY0) {
+__device__ inline void splat_global(TileSmem &s, const TileParams &p, int RX0, int RY0) {
     const int tid = threadIdx.x;
     int bx0, bx1, by0, by1;
     if (!frame_window(p, RX0, RY0, bx0, bx1, by0, by1)) return;
@@ -181,7 +181,7 @@ __device__ __forceinline__ void uniform_words(uint32_t *dw, const TileParams &p,
 
 // Coarse levels of the pyramid (above level 5) for every fraction with invalid tiles, and the value each invalid
 // tile receives (its first valid ancestor; 0 when the frame has no valid pixel).  Run by one CTA.
-__device__ void coarse_pass(const TileParams &p) {
+__device__ inline void coarse_pass(const TileParams &p) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int n5 = p.n5x * p.n5y;
     for (int kk = 0; kk < p.nfrac; ++kk) {

@@ -1,0 +1,131 @@
+"""GPU tests of the batched persistent path: results bit-identical to exw_extrapolate per stream (mixed sizes, colour
+types and widths that do or do not allow TMA staging), the autotuner, replay from a CUDA graph, and a bounded wait
+that runs out (injected on the host with EXW_FAULT=timeout) reporting EXW_ERR_TIMEOUT without faulting the GPU."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2307_12607_gb300 import scenes  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def b():
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA GPU is required for the gpu-marked tests")
+    from paper_2307_12607_gb300 import build, binding
+    build.build()
+    return binding
+
+
+SIZES = [(256, 144, torch.float16), (320, 180, torch.float32), (200, 120, torch.float16), (97, 61, torch.float32),
+         (640, 360, torch.float16), (130, 77, torch.float16), (96, 64, torch.float32)]
+
+
+def make_streams(seed=0, sizes=SIZES):
+    streams = []
+    for i, (W, H, dt) in enumerate(sizes):
+        s = scenes.make_scene(W, H, 1000 + seed * 100 + i, 10, vmax=10.0, pan_max=3.0, sliver_fraction=0.1)
+        c, d, m = scenes.render(s, 0.0)
+        streams.append((torch.from_numpy(c).to(dt).cuda(), torch.from_numpy(d).cuda(), torch.from_numpy(m).cuda()))
+    return streams
+
+
+def same(a, b_):
+    iv = torch.int16 if a.dtype == torch.float16 else torch.int32
+    return torch.equal(a.view(iv), b_.view(iv))
+
+
+@pytest.mark.parametrize("fill", [True, False])
+@pytest.mark.parametrize("tma", [True, False])
+def test_batched_matches_single_stream(b, fill, tma):
+    streams = make_streams()
+    outs = b.exw_extrapolate_batched(streams, nfrac=3, fill=fill, tma=tma)
+    for (c, d, m), (o, k) in zip(streams, outs):
+        o1, k1 = b.exw_extrapolate(c, d, m, nfrac=3, fill=fill)
+        assert torch.equal(k, k1)
+        assert same(o, o1)
+
+
+def test_batched_with_tuner_and_fewer_fractions(b):
+    streams = make_streams(seed=1)
+    t = b.exw_tuner_create()
+    try:
+        for nfrac in (3, 2):
+            outs = b.exw_extrapolate_batched(streams, nfrac=nfrac, tuner=t)
+            for (c, d, m), (o, k) in zip(streams, outs):
+                o1, k1 = b.exw_extrapolate(c, d, m, nfrac=nfrac)
+                assert torch.equal(k, k1) and same(o, o1)
+        rep = b.exw_tuner_report(t)
+        assert rep.count("best") == 2 and "ctas_per_sm" in rep
+    finally:
+        b.exw_tuner_destroy(t)
+
+
+def test_batched_graph_capture_and_replay(b):
+    streams = make_streams(seed=2)
+    nfrac = 3
+    outs = [(torch.empty((nfrac,) + tuple(c.shape), dtype=c.dtype, device="cuda"),
+             torch.empty((nfrac,) + tuple(d.shape), dtype=torch.uint8, device="cuda")) for c, d, _ in streams]
+    ws = b.workspace(b.exw_batched_workspace_bytes([s for s in streams], nfrac), "cuda")
+    t = b.exw_tuner_create()
+    try:
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            b.exw_extrapolate_batched(streams, nfrac, outs=outs, ws=ws, tuner=t)   # tunes outside the capture
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            b.exw_extrapolate_batched(streams, nfrac, outs=outs, ws=ws, tuner=t)
+        for rep in range(2):
+            fresh = make_streams(seed=10 + rep)
+            for (c, d, m), (c2, d2, m2) in zip(streams, fresh):
+                c.copy_(c2)
+                d.copy_(d2)
+                m.copy_(m2)
+            g.replay()
+            torch.cuda.synchronize()
+            assert b.exw_device_status(ws) == 0
+            for (c, d, m), (o, k) in zip(streams, outs):
+                o1, k1 = b.exw_extrapolate(c, d, m, nfrac=nfrac)
+                assert torch.equal(k, k1) and same(o, o1)
+    finally:
+        b.exw_tuner_destroy(t)
+
+
+def test_batched_bounded_wait_times_out_and_context_survives(b):
+    streams = make_streams(seed=3, sizes=SIZES[:4])
+    ws = b.workspace(b.exw_batched_workspace_bytes(streams, 3), "cuda")
+    os.environ["EXW_FAULT"] = "timeout"
+    try:
+        b.exw_extrapolate_batched(streams, 3, ws=ws)
+        torch.cuda.synchronize()
+        assert b.exw_device_status(ws) == 4          # EXW_ERR_TIMEOUT
+    finally:
+        del os.environ["EXW_FAULT"]
+    outs = b.exw_extrapolate_batched(streams, 3, ws=ws)  # the context is intact: a normal call succeeds
+    torch.cuda.synchronize()
+    assert b.exw_device_status(ws) == 0
+    for (c, d, m), (o, k) in zip(streams, outs):
+        o1, k1 = b.exw_extrapolate(c, d, m, nfrac=3)
+        assert torch.equal(k, k1) and same(o, o1)
+
+
+def test_batched_full_config_sampled(b):
+    # the 48-stream workload: 12 each of 720p, 1080p, 1440p and 4K, FP16 colour; four streams checked in full
+    scs = scenes.batched_scenes()
+    streams = []
+    for s in scs:
+        c, d, m = scenes.render(s, 0.0, np.float16)
+        streams.append((torch.from_numpy(c).cuda(), torch.from_numpy(d).cuda(), torch.from_numpy(m).cuda()))
+    outs = b.exw_extrapolate_batched(streams, 3)
+    for i in (0, 13, 30, 47):
+        c, d, m = streams[i]
+        o1, k1 = b.exw_extrapolate(c, d, m, nfrac=3)
+        assert torch.equal(outs[i][1], k1) and same(outs[i][0], o1)
