@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--case", choices=EXTRAS, default=None,
+                    help="time only this one configuration and print its JSON (for profiling)")
     return ap.parse_args()
 
 
@@ -56,6 +59,31 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a kernel from one ncu capture, with the
+# hash of the kernel sources it was taken on: reported only while the sources are unchanged, else null.
+MEASURED_TRAFFIC = {
+    ("exw_fused_tma", "sequence_1080p_fp32"): (81.15e6, "577b833f1042bf27"),
+    ("exw_fused_tma", "warp_4k_fp16"): (286.10e6, "577b833f1042bf27"),
+}
+
+
+def csrc_hash() -> str:
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2307_12607_gb300", "csrc", "*"))):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(os.path.basename(f).encode())
+            with open(f, "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str, workload: str):
+    t = MEASURED_TRAFFIC.get((kernel, workload))
+    return t[0] if t is not None and t[1] == csrc_hash() else None
 
 
 def peaks():
@@ -187,6 +215,158 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _event_ms(fn, reps):
+    import torch
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _kernel_means(b, fn):
+    b.exw_timing_enable(True)
+    fn()
+    import torch
+    torch.cuda.synchronize()
+    out = {k: 1000.0 * b.exw_timing_query(k)[0] / max(1, b.exw_timing_query(k)[1]) for k in b.exw_timing_names()}
+    b.exw_timing_enable(False)
+    return {k: round(v, 2) for k, v in out.items()}
+
+
+EXTRAS = ("warp_4k_fp16", "extrapolate_4k_fp16_fill", "batched_48_streams", "fwd_bwd_1080p")
+
+
+def run_extras(b, devc, names=EXTRAS):
+    """The other configurations of the metric, each timed with CUDA events on the current stream:
+    4K FP16 forward warp (no fill) and full extrapolation, the 48-stream batched launch against a loop of
+    single-stream calls over the same frames, and forward+backward of the differentiation workload."""
+    import torch
+    from paper_2307_12607_gb300 import scenes
+    peak, _ = peaks()
+    ex = {}
+    if "warp_4k_fp16" in names or "extrapolate_4k_fp16_fill" in names:
+        _extras_4k(b, devc, names, peak, ex)
+    if "batched_48_streams" in names:
+        _extras_batched(b, devc, ex)
+    if "fwd_bwd_1080p" in names:
+        _extras_diff(b, devc, ex)
+    return ex
+
+
+def _extras_4k(b, devc, names, peak, ex):
+    import torch
+    from paper_2307_12607_gb300 import scenes
+    # 4K FP16: 3840x2160, 64 objects, |mv| <= 64, fast occluders
+    s4 = scenes.frame_4k_scene()
+    c4, d4, m4 = (torch.from_numpy(x).to(devc) for x in scenes.render(s4, 0.0, np.float16))
+    npx = 3840 * 2160
+    o4 = torch.empty((1, 3, 3, 2160, 3840), dtype=torch.float16, device=devc)
+    k4 = torch.empty((1, 3, 2160, 3840), dtype=torch.uint8, device=devc)
+    ws4 = b.workspace(b.exw_workspace_bytes(b.OP_EXTRAPOLATE, 3840, 2160, b.F16, 1, 3), devc)
+    for fill, name in ((False, "warp_4k_fp16"), (True, "extrapolate_4k_fp16_fill")):
+        if name not in names:
+            continue
+        fn = lambda: b.exw_extrapolate(c4[None], d4[None], m4[None], 3, fill, o4, k4, ws4)
+        ms = _event_ms(fn, 10)
+        km = _kernel_means(b, fn)
+        compulsory = (6 + 4 + 8) + 3 * (6 + 1)
+        ex[name] = {"value": 3 * npx / ms / 1e3, "unit": "Mpixel/s", "ms_per_frame": ms,
+                    "compulsory_bytes_per_source_px": compulsory,
+                    "hbm_frac_compulsory": compulsory * npx / (ms / 1e3) / 1e9 / peak, "kernel_us": km,
+                    "tile_modes": b.frame_stats(ws4, 0),
+                    "traffic_fused_tma": measured_traffic("exw_fused_tma", name),
+                    "workload": "3840x2160 FP16 colour, 64 rectangles, |mv| <= 64 px, occluders ~20%; P_1..P_3"
+                                + (" with hole fill" if fill else " without fill (the forward warp)")}
+
+
+def _extras_batched(b, devc, ex):
+    import torch
+    from paper_2307_12607_gb300 import scenes
+    # batched: 48 streams (12 each of 720p/1080p/1440p/4K), FP16, own scenes
+    streams = []
+    for sc in scenes.batched_scenes():
+        c, d, m = scenes.render(sc, 0.0, np.float16)
+        streams.append((torch.from_numpy(c).to(devc), torch.from_numpy(d).to(devc), torch.from_numpy(m).to(devc)))
+    outs = [(torch.empty((3,) + tuple(c.shape), dtype=c.dtype, device=devc),
+             torch.empty((3,) + tuple(d.shape), dtype=torch.uint8, device=devc)) for c, d, _ in streams]
+    wsb = b.workspace(b.exw_batched_workspace_bytes(streams, 3), devc)
+    tuner = b.exw_tuner_create()
+    b.exw_extrapolate_batched(streams, 3, outs=outs, ws=wsb, tuner=tuner)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b.exw_extrapolate_batched(streams, 3, outs=outs, ws=wsb, tuner=tuner)
+    ms_b = _event_ms(g.replay, 5)
+    wss = {}
+    for c, d, _ in streams:
+        key = (int(d.shape[1]), int(d.shape[0]))
+        if key not in wss:
+            wss[key] = b.workspace(b.exw_workspace_bytes(b.OP_EXTRAPOLATE, key[0], key[1], b.F16, 1, 3), devc)
+
+    def single():
+        for (c, d, m), (o, k) in zip(streams, outs):
+            b.exw_extrapolate(c[None], d[None], m[None], 3, True, o[None], k[None],
+                              wss[(int(d.shape[1]), int(d.shape[0]))])
+    ms_s = _event_ms(single, 3)
+    tot = sum(3 * int(d.shape[0]) * int(d.shape[1]) for _, d, _ in streams)
+    ex["batched_48_streams"] = {"value": tot / ms_b / 1e3, "unit": "Mpixel/s", "ms_per_launch": ms_b,
+                                "single_stream_loop": tot / ms_s / 1e3, "ratio_vs_single_stream": ms_s / ms_b,
+                                "tuner": b.exw_tuner_report(tuner).strip(),
+                                "workload": "48 streams: 12 each of 1280x720, 1920x1080, 2560x1440, 3840x2160, FP16 "
+                                            "colour, 16-64 objects each, P_1..P_3 with fill, one persistent launch "
+                                            "replayed from a CUDA graph"}
+    b.exw_tuner_destroy(tuner)
+
+
+def _extras_diff(b, devc, ex):
+    import torch
+    from paper_2307_12607_gb300 import scenes
+    # differentiation: 8 frames 1080p FP32, k = 1..3, L2 loss against the ground truth at t + k/4
+    sd = scenes.diff_scene()
+    frames = [scenes.render(sd, float(f)) for f in range(8)]
+    targets = [[torch.from_numpy(scenes.ground_truth(sd, float(f), k)).to(devc) for k in (1, 2, 3)] for f in range(8)]
+    fr = [tuple(torch.from_numpy(x).to(devc) for x in f) for f in frames]
+    H, W = 1080, 1920
+    keys = torch.empty((H, W), dtype=torch.int64, device=devc)
+    out = torch.empty((3, H, W), device=devc)
+    mask = torch.empty((H, W), dtype=torch.uint8, device=devc)
+    gout = torch.empty((3, H, W), device=devc)
+    loss = torch.zeros(1, device=devc)
+    gc = torch.zeros((3, H, W), device=devc)
+    gm = torch.zeros((2, H, W), device=devc)
+    wsd = b.workspace(b.exw_workspace_bytes(b.OP_WARP_BACKWARD, W, H), devc)
+
+    def fwd():
+        for f in range(8):
+            c, d, m = fr[f]
+            for k in (1, 2, 3):
+                b.exw_splat_motion(d, m, k, 4, keys)
+                b.exw_warp(c, d, m, keys, k, 4, out, mask)
+                b.exw_l2_loss_grad(out, targets[f][k - 1], mask, gout, loss)
+
+    def fwd_bwd():
+        for f in range(8):
+            c, d, m = fr[f]
+            for k in (1, 2, 3):
+                b.exw_splat_motion(d, m, k, 4, keys)
+                b.exw_warp(c, d, m, keys, k, 4, out, mask)
+                b.exw_l2_loss_grad(out, targets[f][k - 1], mask, gout, loss)
+                b.exw_warp_backward(gout, c, d, m, None, k, 4, gc, gm, wsd)   # keys recomputed (checkpointing)
+    ms_f = _event_ms(fwd, 3)
+    ms_fb = _event_ms(fwd_bwd, 3)
+    px = 8 * 3 * W * H
+    ex["fwd_bwd_1080p"] = {"value": px / ms_fb / 1e3, "unit": "Mpixel/s", "fwd_only": px / ms_f / 1e3,
+                           "ms_per_step": ms_fb, "kernel_us": _kernel_means(b, fwd_bwd),
+                           "workload": "8 frames 1920x1080 FP32, k = 1..3: splat + warp + L2 loss against the ground "
+                                       "truth at t + k/4 + adjoint w.r.t. colour and motion with the splat keys "
+                                       "recomputed in the backward (activation checkpointing)"}
+
+
 def run_exw(args):
     import torch
     import torch.distributed as dist
@@ -266,7 +446,8 @@ def run_exw(args):
     peak, peak_kind = peaks()
     achieved = alg_bytes / (avg_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                "frac": achieved / peak, "traffic": measured_traffic(dom, "sequence_1080p_fp32"),
+                "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": alg_bytes, "mean_launch_ms": avg_ms,
                 "kernel_share": {k: v[0] / sum(x[0] for x in kern.values()) for k, v in kern.items()},
                 "tile_modes_frame0": b.frame_stats(ws, 0)}
@@ -302,6 +483,8 @@ def run_exw(args):
     h2d = (hc.numel() * 4 + hd.numel() * 4 + hm.numel() * 4)
     d2h = ho.numel() * 4 + hmask.numel()
 
+    extras = {} if (args.no_extras or world > 1) else run_extras(b, devc)
+
     if rank == 0:
         cpu = None if args.no_cpu_baseline else cpu_baseline(args.cpu_seconds, seq)
         line = {"metric": "extrapolated Mpixel/s (fwd) at 1080p", "value": value, "unit": "Mpixel/s",
@@ -319,7 +502,8 @@ def run_exw(args):
                 "roofline": roofline,
                 "cpu_baseline": cpu,
                 "e2e": {"value": world * out_px / e2e_s / 1e6, "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
-                        "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3}}
+                        "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
+                "extras": extras}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -327,7 +511,13 @@ def run_exw(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.case is not None:
+        import torch
+        from paper_2307_12607_gb300 import binding as b, build
+        build.build()
+        devc = torch.device("cuda", 0)
+        print(json.dumps({"case": args.case, **run_extras(b, devc, (args.case,))}), flush=True)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_exw(args)
