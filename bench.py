@@ -63,10 +63,7 @@ def dist_env():
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a kernel from one ncu capture, with the
 # hash of the kernel sources it was taken on: reported only while the sources are unchanged, else null.
-MEASURED_TRAFFIC = {
-    ("exw_fused_tma", "sequence_1080p_fp32"): (81.15e6, "577b833f1042bf27"),
-    ("exw_fused_tma", "warp_4k_fp16"): (286.10e6, "577b833f1042bf27"),
-}
+MEASURED_TRAFFIC = {}
 
 
 def csrc_hash() -> str:
@@ -280,7 +277,7 @@ def _extras_4k(b, devc, names, peak, ex):
                     "compulsory_bytes_per_source_px": compulsory,
                     "hbm_frac_compulsory": compulsory * npx / (ms / 1e3) / 1e9 / peak, "kernel_us": km,
                     "tile_modes": b.frame_stats(ws4, 0),
-                    "traffic_fused_tma": measured_traffic("exw_fused_tma", name),
+                    "traffic_engine": measured_traffic("exw_engine", name),
                     "workload": "3840x2160 FP16 colour, 64 rectangles, |mv| <= 64 px, occluders ~20%; P_1..P_3"
                                 + (" with hole fill" if fill else " without fill (the forward warp)")}
 
@@ -439,7 +436,7 @@ def run_exw(args):
     avg_ms = tot / n
     c_bytes = 12
     compulsory = (c_bytes + 4 + 8) + NFRAC * (c_bytes + 1)                 # source once, 3 outputs
-    per_src_px = {"exw_fused": compulsory, "exw_fused_tma": compulsory,
+    per_src_px = {"exw_fused": compulsory, "exw_engine": compulsory,
                   "exw_bounds": 8 + 16.0 / 64,                               # motion read + tile bounds written
                   "exw_fixup": 0.0}
     alg_bytes = per_src_px.get(dom, 0.0) * W * H

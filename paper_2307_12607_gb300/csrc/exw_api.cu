@@ -138,6 +138,8 @@ static TileParams tile_params(const WsLayout &l, void *ws, int W, int H, int nfr
     p.L = L;
     p.k0 = k0;
     p.tile_bounds = (const float4 *)(b + l.tile_bounds);
+    p.tile_depth = (const float2 *)(b + l.tile_depth);
+    p.region_bounds = (const float4 *)(b + l.region_bounds);
     p.plans = (TilePlan *)(b + l.plans);
     p.nbx = l.nbx;
     p.nby = l.nby;
@@ -199,7 +201,8 @@ exw_status exw_motion_bounds(const float *depth, const float *mv, int W, int H, 
     FrameHeader *fh = (FrameHeader *)(b + l.headers);
     float4 *tb = tile_bounds ? (float4 *)tile_bounds : (float4 *)(b + l.tile_bounds);
     cudaError_t e = launch_zero(ws, l.headers + sizeof(FrameHeader), s);
-    if (e == cudaSuccess) e = launch_bounds(depth, mv, W, H, tb, fh, s);
+    if (e == cudaSuccess)
+        e = launch_bounds(depth, mv, W, H, tb, (float2 *)(b + l.tile_depth), (float4 *)(b + l.region_bounds), fh, s);
     if (e == cudaSuccess) e = launch_bounds_finalize(fh, frame_bounds, s);
     return from_cuda(e);
 }
@@ -291,15 +294,19 @@ exw_status exw_extrapolate(const exw_frame *frames, int nframes, int nfrac, unsi
             p.out_color[j] = out[(size_t)f * nfrac + j].color;
             p.out_mask[j] = out[(size_t)f * nfrac + j].mask;
         }
-        e = launch_bounds(p.depth, p.mv, W, H, (float4 *)p.tile_bounds, p.fh, s);
+        e = launch_bounds(p.depth, p.mv, W, H, (float4 *)p.tile_bounds, (float2 *)p.tile_depth,
+                          (float4 *)p.region_bounds, p.fh, s);
         TmaMaps maps;
         const bool tma = (flags & EXW_FLAG_NO_TMA) == 0 && tma_eligible(p.color, p.depth, p.mv, W, cdt) &&
                          make_maps(&maps, p.color, p.depth, p.mv, W, H, cdt);
         if (e == cudaSuccess) {
             if (tma) {
-                const int ntiles = l.n5x * l.n5y, g = 2 * sm_count();
+                const int ntiles = l.n5x * l.n5y, g = sm_count();
+                bool vec = (W % 2) == 0;
+                for (int j = 0; j < nfrac; ++j)
+                    vec = vec && aligned(p.out_color[j], 2 * csize(cdt)) && aligned(p.out_mask[j], 2);
                 e = launch_plan(p, cdt, s);
-                if (e == cudaSuccess) e = launch_fused_tma(p, maps, cdt, fill, ntiles < g ? ntiles : g, s);
+                if (e == cudaSuccess) e = launch_engine(p, maps, cdt, fill, ntiles < g ? ntiles : g, vec, s);
             } else {
                 e = launch_fused(p, cdt, fill, s);
             }

@@ -31,11 +31,12 @@ __global__ void __launch_bounds__(256) splat_global_kernel(const float *__restri
     atomicMin(keys + (size_t)gy * W + gx, (unsigned long long)pack_key_global(db, (uint32_t)i));
 }
 
-// Stage (a0): one 32 x 32 source region per CTA.
-__global__ void __launch_bounds__(256) bounds_kernel(const float *__restrict__ depth, const float *__restrict__ mv,
-                                                     int W, int H, float4 *tile_bounds, FrameHeader *fh) {
-    __shared__ float4 part[32];
-    bounds_region(depth, mv, W, H, tile_bounds, fh, blockIdx.x, blockIdx.y, part);
+// Stage (a0): one 32 x 32 source region per CTA of 8 warps (4 rows each), up to 8 CTAs per SM.
+__global__ void __launch_bounds__(256, 8) bounds_kernel(const float *__restrict__ depth, const float *__restrict__ mv,
+                                                        int W, int H, float4 *tile_bounds, float2 *tile_depth,
+                                                        float4 *region_bounds, FrameHeader *fh) {
+    __shared__ float4 part[64];
+    bounds_region<8>(depth, mv, W, H, tile_bounds, tile_depth, region_bounds, fh, blockIdx.x, blockIdx.y, part, true);
 }
 
 __global__ void bounds_finalize_kernel(const FrameHeader *fh, float *out) {
@@ -109,11 +110,11 @@ cudaError_t launch_splat_global(const float *depth, const float *mv, int W, int 
     return cudaGetLastError();
 }
 
-cudaError_t launch_bounds(const float *depth, const float *mv, int W, int H, float4 *tile_bounds, FrameHeader *fh,
-                          cudaStream_t s) {
+cudaError_t launch_bounds(const float *depth, const float *mv, int W, int H, float4 *tile_bounds, float2 *tile_depth,
+                          float4 *region_bounds, FrameHeader *fh, cudaStream_t s) {
     const dim3 g((unsigned)ceil_div(W, 32), (unsigned)ceil_div(H, 32), 1);
     timing_begin("exw_bounds", s);
-    bounds_kernel<<<g, 256, 0, s>>>(depth, mv, W, H, tile_bounds, fh);
+    bounds_kernel<<<g, 256, 0, s>>>(depth, mv, W, H, tile_bounds, tile_depth, region_bounds, fh);
     count_launch();
     timing_end("exw_bounds", s);
     return cudaGetLastError();

@@ -39,9 +39,9 @@ struct BatchStream {
 };
 
 struct BatchSeg {
-    int start;   // first queue index of the segment
-    int stream;
-    int stage;   // 0 bounds, 1 plans, 2 tiles, 3 fix-up
+    int start;          // first queue index of the segment
+    uint16_t stream;
+    uint16_t stage;     // 0 bounds, 1 plans, 2 tiles, 3 fix-up
 };
 
 struct BatchParams {
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kThreads, 2) batched_kernel(const __grid_const
     TmaSmem<float, kWinXF32, kWinYF32> &sf = *reinterpret_cast<TmaSmem<float, kWinXF32, kWinYF32> *>(smem_raw);
     TmaSmem<__half, kWinXF16, kWinYF16> &sh = *reinterpret_cast<TmaSmem<__half, kWinXF16, kWinYF16> *>(smem_raw);
     TileSmem &ts = sf.t;  // the same bytes in both views (equal window sizes)
-    __shared__ float4 part[kWarps * 4];
+    __shared__ float4 part[kWarps * 8];
     if (threadIdx.x == 0) {
         mbar_init(&ts.mbar, 1);
         fence_mbar_init();
@@ -117,8 +117,9 @@ __global__ void __launch_bounds__(kThreads, 2) batched_kernel(const __grid_const
         const TileParams &p = st.p;
         FrameHeader *fh = p.fh;
         if (sg.stage == 0) {
-            bounds_region(p.depth, p.mv, p.W, p.H, const_cast<float4 *>(p.tile_bounds), fh, local % st.nrx,
-                          local / st.nrx, part);
+            bounds_region<kWarps>(p.depth, p.mv, p.W, p.H, const_cast<float4 *>(p.tile_bounds),
+                          const_cast<float2 *>(p.tile_depth), const_cast<float4 *>(p.region_bounds), fh,
+                          local % st.nrx, local / st.nrx, part, true);
             batch_signal(&fh->bdone);
         } else if (sg.stage == 1) {
             if (!batch_wait(bp, &fh->bdone, (uint32_t)st.nregions, kBatchWaitLimit, &ts.flag)) return;
@@ -242,6 +243,8 @@ static bool build_params(BatchParams *bp, const exw_stream_desc *d, int n, int n
             p.out_mask[j] = d[i].out[j].mask;
         }
         p.tile_bounds = (const float4 *)(sb + l.tile_bounds);
+        p.tile_depth = (const float2 *)(sb + l.tile_depth);
+        p.region_bounds = (const float4 *)(sb + l.region_bounds);
         p.plans = (TilePlan *)(sb + l.plans);
         p.nbx = l.nbx;
         p.nby = l.nby;
@@ -283,7 +286,7 @@ static bool build_params(BatchParams *bp, const exw_stream_desc *d, int n, int n
             const BatchStream &st = bp->st[s];
             const int cnt = stage == 0 ? st.nregions : stage == 1 ? st.nplans : stage == 2 ? st.ntiles : st.nfix;
             if (cnt == 0) continue;
-            bp->seg[nseg] = BatchSeg{total, s, stage};
+            bp->seg[nseg] = BatchSeg{total, (uint16_t)s, (uint16_t)stage};
             ++nseg;
             total += cnt;
         }

@@ -238,6 +238,11 @@ __device__ __forceinline__ float4 shfl4_xor(float4 v, int m) {
                        __shfl_xor_sync(0xFFFFFFFFu, v.z, m), __shfl_xor_sync(0xFFFFFFFFu, v.w, m));
 }
 
+__device__ __forceinline__ float4 shfl4_idx(float4 v, int src) {
+    return make_float4(__shfl_sync(0xFFFFFFFFu, v.x, src), __shfl_sync(0xFFFFFFFFu, v.y, src),
+                       __shfl_sync(0xFFFFFFFFu, v.z, src), __shfl_sync(0xFFFFFFFFu, v.w, src));
+}
+
 // Pyramid levels 1..5 of one 32 x 32 tile in shared memory: 16x16, 8x8, 4x4, 2x2, 1x1 nodes.
 struct TilePyr {
     float4 l1[256];

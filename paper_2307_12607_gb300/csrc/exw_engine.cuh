@@ -1,0 +1,896 @@
+// exw_engine.cuh -- the fused forward pass (stages (b) and (c) for P_1..P_3, Sec. IV-B) as a warp-specialised
+// persistent kernel: one CTA per SM, 25 warps.
+//
+//   producer warp:   takes 32 x 32 target tiles from the frame's queue, reads each tile's plan and stages the
+//                    tile's source window (depth, motion, colour) into one of two shared-memory buffers with three
+//                    TMA loads (cp.async.bulk.tensor, mbarrier completion), one tile ahead of the consumers;
+//   3 x 8 consumer warps: group g computes fraction k0 + g of the tile -- each thread a 2 x 2 pixel block --
+//                    then fills and stores it.  A consumer warp releases the buffer through a second mbarrier.
+//
+// Tiles whose candidate sources all carry one motion (plan mode 0) are pure translations: the winner of target q
+// is the source q - o_k when that pixel is valid and carries the tile's motion, so no splat is needed.  The
+// consumers first rewrite the staged depth plane in place into one word per source pixel -- its depth bits when
+// the pixel is valid with the tile's motion, the bits with the sign set when it is valid with another motion, all
+// ones when its depth is not valid -- and every fraction then reads its winners, crack neighbours and tap depths
+// off that plane with whole-pixel offsets, with bilinear weights that are constant over the tile.  Other tiles
+// splat their candidate sources into per-fraction region keys (from the window, or from global memory when the
+// landing rectangle is wider than a window) and gather through the keys.
+//
+// Every result is bit-identical to the per-tile passes of exw_tile.cuh (same arithmetic in the same order).
+#pragma once
+
+#include "exw_items.cuh"
+
+namespace exw {
+
+constexpr int kGroupThreads = 256;                          // one fraction: 16 x 16 blocks of 2 x 2 pixels
+constexpr int kConsumerThreads = kMaxFrac * kGroupThreads;  // 768
+constexpr int kConsumerWarps = kConsumerThreads / 32;       // 24
+constexpr int kEngineThreads = kConsumerThreads + 32;       // + the producer warp
+constexpr int kBarConsumers = 1;                            // named barriers: 1 all consumers, 2 + g group g
+constexpr int kModeEnd = -1;                                // plan slot mode: no more tiles
+
+// Per-fraction constants of a uniform tile (computed by the producer).
+struct UniformFrac {
+    int ox, oy;               // whole-pixel offset o_k
+    uint32_t flags;           // kTapX, kTapY: a tap column / row exists; kMirX, kMirY: taps at -1; kInterior
+    float W00, W10, W01, W11; // bilinear weights, constant over the tile
+    float inv[8];             // 1 / (sum of the weights of tap subset j), j = a10 | a01 << 1 | a11 << 2
+};
+constexpr uint32_t kTapX = 1u, kTapY = 2u, kMirX = 4u, kMirY = 8u, kInterior = 16u;
+
+// What the producer hands the consumers with each buffer.
+struct TileSlot {
+    TilePlan plan;
+    int tile, X0, Y0;
+    Rect N;                   // mode 0: the source rectangle the fractions read
+    UniformFrac u[kMaxFrac];  // mode 0
+};
+
+template <typename CT, int WX, int WY>
+struct EngineSmem {
+    Window<CT, WX, WY> win[2];            // TMA destinations, double-buffered
+    uint64_t key[kMaxFrac][kRegionN];     // region keys per fraction (modes 1-3)
+    float4 l2[kMaxFrac][2][64];           // pyramid level 2 (8 x 8 nodes) per group, by tile parity
+    TileSlot slot[2];                     // the tile in each buffer
+    uint32_t cand[kConsumerThreads];      // candidate 8 x 8 source tiles of the global-memory splat
+    uint32_t ncand;
+    int last[kMaxFrac];                   // group g finished the frame's last (tile, fraction)
+    int abort;                            // a bounded wait ran out: every warp leaves
+    uint64_t full[2], empty[2];
+};
+
+// ------------------------------------------------------------------------------------------------------------
+// Barriers
+// ------------------------------------------------------------------------------------------------------------
+__device__ __forceinline__ void bar_sync(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+// Barrier over n threads that also returns whether any of them passed v = true.
+__device__ __forceinline__ bool bar_red_or(int id, int n, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n"
+        " .reg .pred p, q;\n"
+        " setp.ne.u32 p, %1, 0;\n"
+        " bar.red.or.pred q, %2, %3, p;\n"
+        " selp.u32 %0, 1, 0, q;\n"
+        "}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(n)
+        : "memory");
+    return r != 0u;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mbar)) : "memory");
+}
+// Bounded wait on an mbarrier phase that also gives up when another warp raised the abort flag.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *mbar, uint32_t parity, const volatile int *abort) {
+    for (uint32_t i = 1; i <= kWaitLimit; ++i) {
+        if (mbar_try_wait(mbar, parity)) return true;
+        if ((i & 15u) == 0u) {
+            if (*abort) return false;
+            __nanosleep(64);
+        }
+    }
+    return false;
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Producer
+// ------------------------------------------------------------------------------------------------------------
+__device__ __forceinline__ Rect uniform_sources(const TileParams &p, uint32_t umx, uint32_t umy, int RX0, int RY0);
+
+// Constants of fraction kk of a uniform tile, by the lanes 8 kk .. 8 kk + 7 of the producer warp (lane 8 kk + j
+// writes inv[j]).
+__device__ __forceinline__ void uniform_frac(UniformFrac &u, const TileParams &p, uint32_t umx, uint32_t umy, int kk,
+                                             int RX0, int RY0, int j) {
+    const int k = p.k0 + kk;
+    const int ox = axis_off_of(umx, k, p.L), oy = axis_off_of(umy, k, p.L);
+    int sx, sy;
+    const float rx = residual(__uint_as_float(umx), k, p.L, ox, sx);
+    const float ry = residual(__uint_as_float(umy), k, p.L, oy, sy);
+    const float wx1 = fabsf(rx), wy1 = fabsf(ry);
+    const float wx0 = 1.0f - wx1, wy0 = 1.0f - wy1;
+    const float W00 = wx0 * wy0, W10 = wx1 * wy0, W01 = wx0 * wy1, W11 = wx1 * wy1;
+    u.inv[j] = __frcp_rn(((W00 + ((j & 1) ? W10 : 0.0f)) + ((j & 2) ? W01 : 0.0f)) + ((j & 4) ? W11 : 0.0f));
+    if (j == 0) {
+        const bool interior = RX0 >= 0 && RY0 >= 0 && RX0 + kRegion <= p.W && RY0 + kRegion <= p.H &&
+                              RX0 - ox >= 0 && RY0 - oy >= 0 && RX0 + kRegion - ox <= p.W && RY0 + kRegion - oy <= p.H;
+        u.ox = ox;
+        u.oy = oy;
+        u.flags = (sx != 0 ? kTapX : 0u) | (sy != 0 ? kTapY : 0u) | (sx < 0 ? kMirX : 0u) | (sy < 0 ? kMirY : 0u) |
+                  (interior ? kInterior : 0u);
+        u.W00 = W00;
+        u.W10 = W10;
+        u.W01 = W01;
+        u.W11 = W11;
+    }
+}
+
+template <typename CT, int WX, int WY>
+__device__ void engine_producer(EngineSmem<CT, WX, WY> &s, const TileParams &p, const CUtensorMap *tcol,
+                                const CUtensorMap *tdep, const CUtensorMap *tmv) {
+    constexpr uint32_t kBytes = WX * WY * (4 + 8 + 3 * (uint32_t)sizeof(CT));
+    constexpr uint32_t kColourBytes = WX * WY * 3 * (uint32_t)sizeof(CT);
+    constexpr int kWords = (int)(sizeof(TilePlan) / 4);
+    const int lane = threadIdx.x & 31;
+    const int ntiles = p.n5x * p.n5y;
+    // Two tiles of look-ahead: the queue position of tile i + 2 and the plan of tile i + 1 are requested while
+    // tile i is staged.
+    int qnext = 0;
+    if (lane == 0) {
+        qnext = (int)atomicAdd(&p.fh->queue, 1u);
+    }
+    int tile = __shfl_sync(0xFFFFFFFFu, qnext, 0);
+    if (lane == 0 && tile < ntiles) qnext = (int)atomicAdd(&p.fh->queue, 1u);
+    int word = (tile < ntiles && lane < kWords) ? __ldcg(reinterpret_cast<const int *>(p.plans + tile) + lane) : 0;
+    for (uint32_t i = 0;; ++i) {
+        const int b = (int)(i & 1u);
+        const int tnext = tile < ntiles ? __shfl_sync(0xFFFFFFFFu, qnext, 0) : ntiles;
+        if (lane == 0 && tnext < ntiles) qnext = (int)atomicAdd(&p.fh->queue, 1u);
+        const int wnext =
+            (tnext < ntiles && lane < kWords) ? __ldcg(reinterpret_cast<const int *>(p.plans + tnext) + lane) : 0;
+        bool ok = true;
+        if (i >= 2) {  // the consumers' release of this buffer's previous use
+            if (lane == 0) ok = mbar_wait_or_abort(&s.empty[b], ((i >> 1) - 1u) & 1u, &s.abort);
+            ok = __shfl_sync(0xFFFFFFFFu, (int)ok, 0) != 0;
+        }
+        if (!ok) {
+            if (lane == 0) {
+                atomicExch(p.status, (uint32_t)EXW_ERR_TIMEOUT);
+                *(volatile int *)&s.abort = 1;
+            }
+            return;
+        }
+        TileSlot &sl = s.slot[b];
+        if (tile >= ntiles) {
+            if (lane == 0) {
+                sl.plan.mode = kModeEnd;
+                mbar_arrive(&s.full[b]);
+            }
+            return;
+        }
+        if (lane < kWords) reinterpret_cast<int *>(&sl.plan)[lane] = word;
+        const int mode = __shfl_sync(0xFFFFFFFFu, word, 0);
+        const int wx0 = __shfl_sync(0xFFFFFFFFu, word, 1), wy0 = __shfl_sync(0xFFFFFFFFu, word, 2);
+        const int X0 = (tile % p.n5x) * kFillTile, Y0 = (tile / p.n5x) * kFillTile;
+        if (mode == 0 || mode == 5) {
+            const uint32_t umx = (uint32_t)__shfl_sync(0xFFFFFFFFu, word, 16);
+            const uint32_t umy = (uint32_t)__shfl_sync(0xFFFFFFFFu, word, 17);
+            if (lane < 8 * p.nfrac) uniform_frac(sl.u[lane >> 3], p, umx, umy, lane >> 3, X0 - 1, Y0 - 1, lane & 7);
+            if (lane == 0) sl.N = uniform_sources(p, umx, umy, X0 - 1, Y0 - 1);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            sl.tile = tile;
+            sl.X0 = X0;
+            sl.Y0 = Y0;
+            atomicAdd(&p.fh->nmode[mode], 1u);
+            if (mode == 5) {  // smooth: only the colour is read
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&s.full[b], kColourBytes);
+                tma_load_3d(&s.win[b].col[0][0], tcol, wx0, wy0, 0, &s.full[b]);
+            } else if (mode == 0 || mode == 1) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&s.full[b], kBytes);
+                tma_load_2d(s.win[b].depth, tdep, wx0, wy0, &s.full[b]);
+                tma_load_3d(&s.win[b].mv[0][0], tmv, wx0, wy0, 0, &s.full[b]);
+                tma_load_3d(&s.win[b].col[0][0], tcol, wx0, wy0, 0, &s.full[b]);
+            } else {
+                mbar_arrive(&s.full[b]);
+            }
+        }
+        tile = tnext;
+        word = wnext;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Uniform tiles
+// ------------------------------------------------------------------------------------------------------------
+
+// Source rectangle N a uniform tile reads (the union over fractions of R - o_k grown by one, inside the frame).
+__device__ __forceinline__ Rect uniform_sources(const TileParams &p, uint32_t umx, uint32_t umy, int RX0, int RY0) {
+    Rect N{1 << 30, -(1 << 30), 1 << 30, -(1 << 30)};
+    for (int kk = 0; kk < p.nfrac; ++kk) {
+        const int ox = axis_off_of(umx, p.k0 + kk, p.L), oy = axis_off_of(umy, p.k0 + kk, p.L);
+        N.x0 = min(N.x0, RX0 - ox - 1);
+        N.x1 = max(N.x1, RX0 + kRegion - ox);
+        N.y0 = min(N.y0, RY0 - oy - 1);
+        N.y1 = max(N.y1, RY0 + kRegion - oy);
+    }
+    N.x0 = max(N.x0, 0);
+    N.y0 = max(N.y0, 0);
+    N.x1 = min(N.x1, p.W - 1);
+    N.y1 = min(N.y1, p.H - 1);
+    return N;
+}
+
+// Rewrite the window's depth plane (over N) into source words: depth bits of a valid pixel with motion (mx, my),
+// the bits with the sign set for a valid pixel with another motion, all ones for a pixel without valid depth.
+// Four pixels per step (16-byte shared-memory accesses); all consumer threads.
+template <typename CT, int WX, int WY>
+__device__ __forceinline__ void build_source_words(Window<CT, WX, WY> &w, int wx0, int wy0, Rect N, float mx, float my,
+                                                   int tid) {
+    const int qx0 = max((N.x0 - wx0) >> 2, 0), qx1 = min((N.x1 - wx0) >> 2, WX / 4 - 1);
+    const int ry0 = max(N.y0 - wy0, 0), ry1 = min(N.y1 - wy0, WY - 1);
+    static_assert(WX / 4 <= 16, "one half warp covers a window row");
+    const int q = qx0 + (tid & 15);  // a half warp per row, a quad per lane (WX / 4 <= 16)
+    if (q > qx1) return;
+    for (int row = ry0 + (tid >> 4); row <= ry1; row += kConsumerThreads / 16) {
+        const int idx = row * WX + 4 * q;
+        uint4 d = *reinterpret_cast<const uint4 *>(&w.depth[idx]);
+        const float4 vx = *reinterpret_cast<const float4 *>(&w.mv[0][idx]);
+        const float4 vy = *reinterpret_cast<const float4 *>(&w.mv[1][idx]);
+        auto word = [&](uint32_t db, float ux, float uy) -> uint32_t {
+            if (!depth_ok(db)) return 0xFFFFFFFFu;
+            return (ux == mx && uy == my) ? db : (db | 0x80000000u);
+        };
+        d.x = word(d.x, vx.x, vy.x);
+        d.y = word(d.y, vx.y, vy.y);
+        d.z = word(d.z, vx.z, vy.z);
+        d.w = word(d.w, vx.w, vy.w);
+        *reinterpret_cast<uint4 *>(&w.depth[idx]) = d;
+    }
+}
+
+// One 2 x 2 block of a uniform tile for one fraction.  The block's cells are addressed in a frame mirrored so that
+// the taps lie at +1 in x and y: mirrored column j <-> source column SX + c(j), c(j) = MX ? 2 - j : j - 1 (rows
+// likewise), pixels at j, i in {1, 2}.  EDGE adds the frame checks of tiles near the border (and keeps every
+// shared-memory index inside the window).  Results c[], m[] are in true pixel order (dy * 2 + dx).
+template <typename CT, int WX, int WY, bool EDGE, bool MX, bool MY>
+__device__ __forceinline__ void uniform_block(const Window<CT, WX, WY> &w, int wx0, int wy0, const TileParams &p,
+                                              const UniformFrac &u, int TX, int TY, float4 c[4], uint8_t m[4]) {
+    const int SX = TX - u.ox, SY = TY - u.oy;
+    int cidx[4], ridx[4];
+    bool fc[4], fr[4], sc[4], sr[4], tc[4], tr[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int dcol = MX ? 2 - j : j - 1, drow = MY ? 2 - j : j - 1;
+        const int sx = SX + dcol, tx = TX + dcol;
+        sc[j] = (unsigned)sx < (unsigned)p.W;
+        tc[j] = (unsigned)tx < (unsigned)p.W;
+        fc[j] = sc[j] && tc[j];
+        cidx[j] = min(max(sx, wx0), wx0 + WX - 1) - wx0;  // a no-op inside the frame: keeps any index in the window
+        const int sy = SY + drow, ty = TY + drow;
+        sr[j] = (unsigned)sy < (unsigned)p.H;
+        tr[j] = (unsigned)ty < (unsigned)p.H;
+        fr[j] = sr[j] && tr[j];
+        ridx[j] = (min(max(sy, wy0), wy0 + WY - 1) - wy0) * WX;
+    }
+    const uint32_t *wd = reinterpret_cast<const uint32_t *>(w.depth);
+    auto V = [&](int i, int j) -> uint32_t { return wd[ridx[i] + cidx[j]]; };
+    // validated word of a target cell: the source word if it is a winner, else all ones
+    auto D = [&](uint32_t v, int i, int j) -> uint32_t {
+        const uint32_t x = v | (uint32_t)((int32_t)v >> 31);
+        return (!EDGE || (fc[j] && fr[i])) ? x : 0xFFFFFFFFu;
+    };
+    const uint32_t v01 = V(0, 1), v02 = V(0, 2);
+    const uint32_t v10 = V(1, 0), v11 = V(1, 1), v12 = V(1, 2), v13 = V(1, 3);
+    const uint32_t v20 = V(2, 0), v21 = V(2, 1), v22 = V(2, 2), v23 = V(2, 3);
+    const uint32_t v31 = V(3, 1), v32 = V(3, 2), v33 = V(3, 3);
+    const uint32_t d01 = D(v01, 0, 1), d02 = D(v02, 0, 2);
+    const uint32_t d10 = D(v10, 1, 0), d11 = D(v11, 1, 1), d12 = D(v12, 1, 2), d13 = D(v13, 1, 3);
+    const uint32_t d20 = D(v20, 2, 0), d21 = D(v21, 2, 1), d22 = D(v22, 2, 2), d23 = D(v23, 2, 3);
+    const uint32_t d31 = D(v31, 3, 1), d32 = D(v32, 3, 2);
+
+    // Decisions of the four pixels (mirrored positions (1,1), (1,2), (2,1), (2,2)).
+    bool ok[4];
+    int sel[4];
+    uint8_t mk[4];
+    auto decide = [&](int q, uint32_t dq, uint32_t dl, uint32_t dr, uint32_t du, uint32_t dd, uint32_t tx_,
+                      uint32_t ty_, uint32_t txy, bool in, bool exj, bool eyi) {
+        const bool empty = dq == 0xFFFFFFFFu;
+        const bool crack = !empty && is_crack(dq, dl, dr, du, dd);
+        ok[q] = in && !empty && !crack;
+        mk[q] = !in ? (uint8_t)0 : empty ? (uint8_t)EXW_MASK_EMPTY : crack ? (uint8_t)EXW_MASK_CRACK : (uint8_t)0;
+        const float Dp = __uint_as_float(dq);
+        const bool a10 = exj && tap_agrees(fabsf(__uint_as_float(tx_)), Dp);
+        const bool a01 = eyi && tap_agrees(fabsf(__uint_as_float(ty_)), Dp);
+        const bool a11 = exj && eyi && tap_agrees(fabsf(__uint_as_float(txy)), Dp);
+        sel[q] = (a10 ? 1 : 0) | (a01 ? 2 : 0) | (a11 ? 4 : 0);
+    };
+    const bool tx = (u.flags & kTapX) != 0, ty = (u.flags & kTapY) != 0;
+    const bool ex2 = tx && (!EDGE || sc[2]), ex3 = tx && (!EDGE || sc[3]);
+    const bool ey2 = ty && (!EDGE || sr[2]), ey3 = ty && (!EDGE || sr[3]);
+    decide(0, d11, d10, d12, d01, d21, v12, v21, v22, !EDGE || (tc[1] && tr[1]), ex2, ey2);
+    decide(1, d12, d11, d13, d02, d22, v13, v22, v23, !EDGE || (tc[2] && tr[1]), ex3, ey2);
+    decide(2, d21, d20, d22, d11, d31, v22, v31, v32, !EDGE || (tc[1] && tr[2]), ex2, ey3);
+    decide(3, d22, d21, d23, d12, d32, v23, v32, v33, !EDGE || (tc[2] && tr[2]), ex3, ey3);
+    float inv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) inv[q] = u.inv[sel[q]];
+
+    // Colour, one channel at a time (9 cells: mirrored rows / columns 1..3).
+    float out[4][3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        const CT *cp = w.col[ch];
+        float C[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) C[i][j] = to_f<CT>(cp[ridx[i + 1] + cidx[j + 1]]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = q >> 1, j = q & 1;  // mirrored pixel (i + 1, j + 1)
+            float n = u.W00 * C[i][j];
+            n = (sel[q] & 1) ? fmaf(u.W10, C[i][j + 1], n) : n;
+            n = (sel[q] & 2) ? fmaf(u.W01, C[i + 1][j], n) : n;
+            n = (sel[q] & 4) ? fmaf(u.W11, C[i + 1][j + 1], n) : n;
+            out[q][ch] = ok[q] ? storage_round<CT>(n * inv[q]) : 0.0f;
+        }
+    }
+    // mirrored pixel q = (i, j) -> true pixel (MY ? 1 - i : i, MX ? 1 - j : j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = q >> 1, j = q & 1;
+        const int t = ((MY ? 1 - i : i) << 1) | (MX ? 1 - j : j);
+        c[t] = make_float4(out[q][0], out[q][1], out[q][2], ok[q] ? 1.0f : 0.0f);
+        m[t] = mk[q];
+    }
+}
+
+template <typename CT, int WX, int WY, bool EDGE>
+__device__ __forceinline__ void uniform_block_any(const Window<CT, WX, WY> &w, int wx0, int wy0, const TileParams &p,
+                                                  const UniformFrac &u, int TX, int TY, float4 c[4], uint8_t m[4]) {
+    if (u.flags & kMirX) {
+        if (u.flags & kMirY) uniform_block<CT, WX, WY, EDGE, true, true>(w, wx0, wy0, p, u, TX, TY, c, m);
+        else uniform_block<CT, WX, WY, EDGE, true, false>(w, wx0, wy0, p, u, TX, TY, c, m);
+    } else {
+        if (u.flags & kMirY) uniform_block<CT, WX, WY, EDGE, false, true>(w, wx0, wy0, p, u, TX, TY, c, m);
+        else uniform_block<CT, WX, WY, EDGE, false, false>(w, wx0, wy0, p, u, TX, TY, c, m);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Tiles through splat keys (modes 1-3)
+// ------------------------------------------------------------------------------------------------------------
+__device__ __forceinline__ void engine_splat_pixel(uint64_t (*key)[kRegionN], const TileParams &p, int x, int y,
+                                                   uint32_t db, uint32_t ux, uint32_t uy, uint32_t fm, int RX0,
+                                                   int RY0) {
+    if (!depth_ok(db) || !finite_bits(ux) || !finite_bits(uy)) return;
+    const AxisDec dx = axis_dec(ux, p.L), dy = axis_dec(uy, p.L);
+    if (!dx.land || !dy.land) return;
+    const uint64_t kv = pack_key_local(db, x, y);
+    for (int kk = 0; kk < p.nfrac; ++kk) {
+        if (!(fm & (1u << kk))) continue;
+        const int k = p.k0 + kk;
+        const int gx = x + axis_off(dx, k), gy = y + axis_off(dy, k);
+        if ((unsigned)gx >= (unsigned)p.W || (unsigned)gy >= (unsigned)p.H) continue;
+        const int rx = gx - RX0, ry = gy - RY0;
+        if ((unsigned)rx < (unsigned)kRegion && (unsigned)ry < (unsigned)kRegion)
+            atomicMin((unsigned long long *)&key[kk][ry * kRegion + rx], (unsigned long long)kv);
+    }
+}
+
+// Union of the landing rectangles of a plan held in shared memory.
+__device__ __forceinline__ Rect plan_union(const TilePlan &pl, int nfrac) {
+    Rect U{1 << 30, -(1 << 30), 1 << 30, -(1 << 30)};
+    for (int kk = 0; kk < nfrac; ++kk) {
+        const Rect R{pl.rect[kk][0], pl.rect[kk][1], pl.rect[kk][2], pl.rect[kk][3]};
+        if (R.empty()) continue;
+        U.x0 = min(U.x0, R.x0);
+        U.x1 = max(U.x1, R.x1);
+        U.y0 = min(U.y0, R.y0);
+        U.y1 = max(U.y1, R.y1);
+    }
+    return U;
+}
+
+// Splat every window pixel of rectangle U for all fractions (all consumer threads).
+template <typename CT, int WX, int WY>
+__device__ __forceinline__ void engine_splat_window(uint64_t (*key)[kRegionN], const TileParams &p,
+                                                    const WinAcc<CT, WX, WY> &a, Rect U, int RX0, int RY0, int tid) {
+    const int lane = tid & 31, wid = tid >> 5;
+    const uint32_t fm = (1u << p.nfrac) - 1u;
+    for (int y = U.y0 + wid; y <= U.y1; y += kConsumerWarps)
+        for (int x = U.x0 + lane; x <= U.x1; x += 32) {
+            const int i = a.at(x, y);
+            engine_splat_pixel(key, p, x, y, __float_as_uint(a.w->depth[i]), __float_as_uint(a.w->mv[0][i]),
+                               __float_as_uint(a.w->mv[1][i]), fm, RX0, RY0);
+        }
+}
+
+// Splat from global memory: the 8 x 8 source tiles whose bounds reach R, 64 threads per tile (all consumers).
+template <typename CT, int WX, int WY>
+__device__ inline void engine_splat_global(EngineSmem<CT, WX, WY> &s, const TileParams &p, int RX0, int RY0,
+                                           int tid) {
+    int bx0, bx1, by0, by1;
+    if (!frame_window(p, RX0, RY0, bx0, bx1, by0, by1)) return;
+    const int nbxr = bx1 - bx0 + 1;
+    const int total = nbxr * (by1 - by0 + 1);
+    const size_t plane = (size_t)p.W * p.H;
+    for (int base = 0; base < total; base += kConsumerThreads) {
+        if (tid == 0) s.ncand = 0u;
+        bar_sync(kBarConsumers, kConsumerThreads);
+        const int idx = base + tid;
+        if (idx < total) {
+            const int by = by0 + idx / nbxr, bx = bx0 + idx % nbxr;
+            const float4 b = __ldcg(p.tile_bounds + (size_t)by * p.nbx + bx);
+            if (b.x <= b.y) {
+                uint32_t fm = 0;
+                for (int kk = 0; kk < p.nfrac; ++kk) {
+                    int ox0, ox1, oy0, oy1;
+                    tile_offsets(b, p.k0 + kk, p.L, ox0, ox1, oy0, oy1);
+                    const int tx0 = 8 * bx + ox0, tx1 = 8 * bx + 7 + ox1;
+                    const int ty0 = 8 * by + oy0, ty1 = 8 * by + 7 + oy1;
+                    if (tx1 >= RX0 && tx0 < RX0 + kRegion && ty1 >= RY0 && ty0 < RY0 + kRegion) fm |= 1u << kk;
+                }
+                if (fm) {
+                    const uint32_t slot = atomicAdd(&s.ncand, 1u);
+                    s.cand[slot] = (uint32_t)bx | ((uint32_t)by << 12) | (fm << 24);
+                }
+            }
+        }
+        bar_sync(kBarConsumers, kConsumerThreads);
+        const int nc = (int)s.ncand;
+        for (int c0 = 0; c0 < nc; c0 += kConsumerThreads / 64) {
+            const int ci = c0 + (tid >> 6);
+            if (ci < nc) {
+                const uint32_t e = s.cand[ci];
+                const int bx = (int)(e & 0xFFFu), by = (int)((e >> 12) & 0xFFFu);
+                const int x = 8 * bx + (tid & 7), y = 8 * by + ((tid >> 3) & 7);
+                if (x < p.W && y < p.H) {
+                    const size_t i = (size_t)y * p.W + x;
+                    engine_splat_pixel(s.key, p, x, y, __float_as_uint(__ldg(p.depth + i)),
+                                       __float_as_uint(__ldg(p.mv + i)), __float_as_uint(__ldg(p.mv + plane + i)),
+                                       e >> 24, RX0, RY0);
+                }
+            }
+        }
+        bar_sync(kBarConsumers, kConsumerThreads);
+    }
+}
+
+// Stage (b) for one target pixel (gx, gy) at region cell r from the keys kw (as 32-bit words) through accessor a.
+template <typename CT, class Acc>
+__device__ __forceinline__ void gather_pixel(const uint32_t *kw, const Acc &a, const TileParams &p, int k, int gx,
+                                             int gy, int r, float4 &c, uint8_t &m) {
+    const bool in = gx < p.W && gy < p.H;
+    const uint32_t dq = kw[2 * r + 1];
+    const bool empty = dq == 0xFFFFFFFFu;
+    const bool crack = !empty && is_crack(dq, kw[2 * (r - 1) + 1], kw[2 * (r + 1) + 1], kw[2 * (r - kRegion) + 1],
+                                          kw[2 * (r + kRegion) + 1]);
+    m = !in ? (uint8_t)0 : empty ? (uint8_t)EXW_MASK_EMPTY : crack ? (uint8_t)EXW_MASK_CRACK : (uint8_t)0;
+    const bool ok = in && !empty && !crack;
+    const uint32_t lo = kw[2 * r];
+    int px = (int)(lo & 0x3FFFu), py = (int)(lo >> 14);
+    if (!ok) {
+        px = a.safe_x();
+        py = a.safe_y();
+    }
+    const auto i00 = a.at(px, py);
+    int sx, sy;
+    const float rx = residual(a.mx(i00), k, p.L, gx - px, sx);
+    const float ry = residual(a.my(i00), k, p.L, gy - py, sy);
+    const float wx1 = fabsf(rx), wy1 = fabsf(ry);
+    const float wx0 = 1.0f - wx1, wy0 = 1.0f - wy1;
+    const bool ex = sx != 0 && (unsigned)(px + sx) < (unsigned)p.W;
+    const bool ey = sy != 0 && (unsigned)(py + sy) < (unsigned)p.H;
+    const auto i10 = ex ? i00 + sx : i00;
+    const auto ir = sy > 0 ? i00 + a.stride() : i00 - a.stride();
+    const auto i01 = ey ? ir : i00;
+    const auto i11 = (ex && ey) ? ir + sx : i00;
+    const float Dp = __uint_as_float(dq);
+    const bool a10 = ex && tap_agrees(a.d(i10), Dp);
+    const bool a01 = ey && tap_agrees(a.d(i01), Dp);
+    const bool a11 = ex && ey && tap_agrees(a.d(i11), Dp);
+    const float w00 = wx0 * wy0;
+    const float w10 = a10 ? wx1 * wy0 : 0.0f;
+    const float w01 = a01 ? wx0 * wy1 : 0.0f;
+    const float w11 = a11 ? wx1 * wy1 : 0.0f;
+    const float den = ((w00 + w10) + w01) + w11;
+    float v[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        float n = w00 * a.c(ch, i00);
+        const float c10 = a.c(ch, i10), c01 = a.c(ch, i01), c11 = a.c(ch, i11);
+        n = a10 ? fmaf(w10, c10, n) : n;
+        n = a01 ? fmaf(w01, c01, n) : n;
+        n = a11 ? fmaf(w11, c11, n) : n;
+        v[ch] = n;
+    }
+    const float inv = __frcp_rn(den);
+    c = make_float4(ok ? storage_round<CT>(v[0] * inv) : 0.0f, ok ? storage_round<CT>(v[1] * inv) : 0.0f,
+                    ok ? storage_round<CT>(v[2] * inv) : 0.0f, ok ? 1.0f : 0.0f);
+}
+
+template <typename CT, class Acc>
+__device__ __forceinline__ void gather_block(const uint64_t *keys, const Acc &a, const TileParams &p, int k, int TX,
+                                             int TY, int bx, int by, float4 c[4], uint8_t m[4]) {
+    const uint32_t *kw = reinterpret_cast<const uint32_t *>(keys);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int dy = t >> 1, dx = t & 1;
+        const int r = (2 * by + dy + 1) * kRegion + (2 * bx + dx + 1);
+        gather_pixel<CT>(kw, a, p, k, TX + dx, TY + dy, r, c[t], m[t]);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Epilogue: fill (pull-push levels 1..5 of the tile, Sec. IV-B stage (c)) and stores
+// ------------------------------------------------------------------------------------------------------------
+
+// Levels 3, 4 and 5 of a group's tile from its level-2 nodes (one warp; every lane returns l5, lane L < 16 its
+// level-3 node L = (L >> 2, L & 3), lane L < 4 its level-4 node).
+__device__ __forceinline__ void upper_levels(const float4 *l2, float4 &l3, float4 &l4, float4 &l5) {
+    const int lane = threadIdx.x & 31;
+    const int L = lane & 15;
+    const int I = L >> 2, J = L & 3;
+    const float4 *c = l2 + (2 * I) * 8 + 2 * J;
+    l3 = mean4(c[0], c[1], c[8], c[9]);
+    const int b4 = 8 * ((lane & 3) >> 1) + 2 * (lane & 1);
+    const float4 q0 = shfl4_idx(l3, b4), q1 = shfl4_idx(l3, b4 + 1), q2 = shfl4_idx(l3, b4 + 4),
+                 q3 = shfl4_idx(l3, b4 + 5);
+    l4 = mean4(q0, q1, q2, q3);
+    l5 = mean4(shfl4_idx(l4, 0), shfl4_idx(l4, 1), shfl4_idx(l4, 2), shfl4_idx(l4, 3));
+}
+
+template <typename CT>
+__device__ __forceinline__ void store_block(const TileParams &p, int kk, int TX, int TY, const float4 c[4],
+                                            const uint8_t m[4], const bool write[4], bool vec) {
+    const size_t plane = (size_t)p.W * p.H;
+    CT *oc = (CT *)p.out_color[kk];
+    uint8_t *om = p.out_mask[kk];
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy) {
+        const int gy = TY + dy;
+        if (gy >= p.H || TX >= p.W) continue;
+        const size_t q = (size_t)gy * p.W + TX;
+        const float4 a = c[2 * dy], b = c[2 * dy + 1];
+        if (vec) {  // both pixels in the frame (W even), 2-element aligned rows
+            *reinterpret_cast<uint16_t *>(om + q) = (uint16_t)(m[2 * dy] | (m[2 * dy + 1] << 8));
+            if (write[2 * dy]) {
+                if (sizeof(CT) == 2) {
+                    *reinterpret_cast<__half2 *>(oc + q) = __floats2half2_rn(a.x, b.x);
+                    *reinterpret_cast<__half2 *>(oc + plane + q) = __floats2half2_rn(a.y, b.y);
+                    *reinterpret_cast<__half2 *>(oc + 2 * plane + q) = __floats2half2_rn(a.z, b.z);
+                } else {
+                    *reinterpret_cast<float2 *>(oc + q) = make_float2(a.x, b.x);
+                    *reinterpret_cast<float2 *>(oc + plane + q) = make_float2(a.y, b.y);
+                    *reinterpret_cast<float2 *>(oc + 2 * plane + q) = make_float2(a.z, b.z);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                if (TX + dx >= p.W) continue;
+                const float4 v = dx ? b : a;
+                om[q + dx] = m[2 * dy + dx];
+                if (!write[2 * dy + dx]) continue;
+                oc[q + dx] = to_storage<CT>(v.x);
+                oc[plane + q + dx] = to_storage<CT>(v.y);
+                oc[2 * plane + q + dx] = to_storage<CT>(v.z);
+            }
+        }
+    }
+}
+
+// Fill and store one fraction of the tile for the calling group (contains one group barrier).  c[] .w = validity.
+template <typename CT, int WX, int WY>
+__device__ __forceinline__ void fill_store_block(EngineSmem<CT, WX, WY> &s, const TileParams &p, int g, int kk,
+                                                 int tile, int buf, int TX, int TY, float4 c[4], const uint8_t m[4],
+                                                 bool vec) {
+    const int tg = threadIdx.x & (kGroupThreads - 1);
+    const int lane = tg & 31, w = tg >> 5;
+    const float4 n1 = mean4(c[0], c[1], c[2], c[3]);
+    const float4 a1 = shfl4_xor(n1, 1), a16 = shfl4_xor(n1, 16), a17 = shfl4_xor(n1, 17);
+    const float4 n2o = mean4(n1, a1, a16, a17);  // meaningful on lanes with even block x and even block y
+    float4 *l2 = s.l2[g][buf];
+    if ((lane & 17) == 0) l2[w * 8 + (lane >> 1)] = n2o;
+    const float4 n2 = shfl4_idx(n2o, lane & ~17);
+    bar_sync(2 + g, kGroupThreads);
+    bool deep = false;  // a hole whose level-1 and level-2 ancestors are both invalid
+#pragma unroll
+    for (int t = 0; t < 4; ++t) deep = deep || (m[t] != 0 && n1.w == 0.0f && n2.w == 0.0f);
+    float4 l3 = n2, l4 = n2, l5 = n2;
+    if (w == 0 || __any_sync(0xFFFFFFFFu, deep)) upper_levels(l2, l3, l4, l5);
+    if (w == 0 && lane == 0) publish_node(p, l5, kk, tile);  // counted (after a fence) when the group finishes
+    // push: first valid ancestor (tile rows 4w..4w+3: level-3 node (w >> 1, bx >> 2), level-4 (w >> 2, bx >> 3))
+    const int bx = lane & 15;
+    const float4 v3 = shfl4_idx(l3, (w >> 1) * 4 + (bx >> 2));
+    const float4 v4 = shfl4_idx(l4, (w >> 2) * 2 + (bx >> 3));
+    const float4 push = n1.w != 0.0f ? n1 : n2.w != 0.0f ? n2 : v3.w != 0.0f ? v3 : v4.w != 0.0f ? v4 : l5;
+    bool write[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const bool hole = m[t] != 0;
+        if (hole) c[t] = push;
+        write[t] = !hole || push.w != 0.0f;
+    }
+    store_block<CT>(p, kk, TX, TY, c, m, write, vec);
+}
+
+// Coarse levels of the pyramid and the value of every tile without a valid pixel, run by one group.
+__device__ inline void engine_coarse_pass(const TileParams &p, int g) {
+    const int tid = threadIdx.x & (kGroupThreads - 1), nt = kGroupThreads;
+    const int n5 = p.n5x * p.n5y;
+    for (int kk = 0; kk < p.nfrac; ++kk) {
+        const uint32_t cnt = __ldcg(&p.fh->ninvalid[kk]);
+        if (cnt == 0u) continue;
+        const float4 *child = p.nodes + (size_t)kk * n5;
+        float4 *cz = p.coarse + (size_t)kk * p.ncoarse;
+        int cw = p.n5x, ch = p.n5y, off = 0;
+        while (cw > 1 || ch > 1) {
+            const int pw = (cw + 1) / 2, ph = (ch + 1) / 2;
+            float4 *par = cz + off;
+            for (int node = tid; node < pw * ph; node += nt) {
+                const int i = node / pw, j = node - i * pw;
+                float4 c[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int ci = 2 * i + (q >> 1), cj = 2 * j + (q & 1);
+                    c[q] = (ci < ch && cj < cw) ? __ldcg(child + ci * cw + cj) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                par[node] = mean4(c[0], c[1], c[2], c[3]);
+            }
+            __threadfence_block();
+            bar_sync(2 + g, kGroupThreads);
+            child = par;
+            off += pw * ph;
+            cw = pw;
+            ch = ph;
+        }
+        for (uint32_t e = tid; e < cnt; e += nt) {
+            const uint32_t tile = __ldcg(p.list + (size_t)kk * n5 + e);
+            int ax = (int)(tile % (uint32_t)p.n5x), ay = (int)(tile / (uint32_t)p.n5x);
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            int w = p.n5x, h = p.n5y, o = 0;
+            while (w > 1 || h > 1) {
+                const int pw = (w + 1) / 2, ph = (h + 1) / 2;
+                ax >>= 1;
+                ay >>= 1;
+                const float4 c = __ldcg(cz + o + ay * pw + ax);
+                if (c.w != 0.0f) {
+                    v = c;
+                    break;
+                }
+                o += pw * ph;
+                w = pw;
+                h = ph;
+            }
+            p.fillval[(size_t)kk * n5 + e] = make_float4(v.x, v.y, v.z, 1.0f);
+        }
+        bar_sync(2 + g, kGroupThreads);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Smooth uniform tiles (plan mode 5): every target is its source's bilinear resampling with all taps
+// ------------------------------------------------------------------------------------------------------------
+
+// One column of four pixels (tile rows 4w..4w+3 of column lane; w = warp in the group): out[r] = colour of row r.
+// Lanes are consecutive columns, so every shared-memory access of a warp is conflict-free.
+template <typename CT, int WX, int WY, bool MY, bool EX, bool EY>
+__device__ __forceinline__ void smooth_column_t(const Window<CT, WX, WY> &win, int wx0, int wy0, const UniformFrac &u,
+                                                int X0, int Y0, CT out[4][3]) {
+    const int tg = threadIdx.x & (kGroupThreads - 1);
+    const int lane = tg & 31, w = tg >> 5;
+    const int sx = EX ? ((u.flags & kMirX) ? -1 : 1) : 0;
+    const int cx = X0 + lane - u.ox - wx0;                          // window column of the source
+    const int ry = Y0 + 4 * w - u.oy - wy0 + (MY ? -1 : 0);         // window row of loaded row 0
+    const float inv = u.inv[(EX ? 1 : 0) | (EY ? 2 : 0) | (EX && EY ? 4 : 0)];
+    const float W00 = u.W00, W10 = u.W10, W01 = u.W01, W11 = u.W11;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        const CT *cp = win.col[ch] + ry * WX + cx;
+        float C[5][2];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            if (!EY && i == (MY ? 0 : 4)) continue;  // the tap row is not read without a y tap
+            C[i][0] = to_f<CT>(cp[i * WX]);
+            if (EX) C[i][1] = to_f<CT>(cp[i * WX + sx]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int ic = MY ? r + 1 : r, it = MY ? r : r + 1;  // centre row, tap row
+            float n = W00 * C[ic][0];
+            if (EX) n = fmaf(W10, C[ic][1], n);
+            if (EY) n = fmaf(W01, C[it][0], n);
+            if (EX && EY) n = fmaf(W11, C[it][1], n);
+            out[r][ch] = to_storage<CT>(n * inv);
+        }
+    }
+}
+
+template <typename CT, int WX, int WY>
+__device__ __forceinline__ void smooth_column(const Window<CT, WX, WY> &win, int wx0, int wy0, const UniformFrac &u,
+                                              int X0, int Y0, CT out[4][3]) {
+    const bool my = (u.flags & kMirY) != 0;
+    switch (u.flags & (kTapX | kTapY)) {
+        case kTapX | kTapY:
+            if (my) smooth_column_t<CT, WX, WY, true, true, true>(win, wx0, wy0, u, X0, Y0, out);
+            else smooth_column_t<CT, WX, WY, false, true, true>(win, wx0, wy0, u, X0, Y0, out);
+            break;
+        case kTapX: smooth_column_t<CT, WX, WY, false, true, false>(win, wx0, wy0, u, X0, Y0, out); break;
+        case kTapY:
+            if (my) smooth_column_t<CT, WX, WY, true, false, true>(win, wx0, wy0, u, X0, Y0, out);
+            else smooth_column_t<CT, WX, WY, false, false, true>(win, wx0, wy0, u, X0, Y0, out);
+            break;
+        default: smooth_column_t<CT, WX, WY, false, false, false>(win, wx0, wy0, u, X0, Y0, out); break;
+    }
+}
+
+template <typename CT>
+__device__ __forceinline__ void store_column(const TileParams &p, int kk, int X0, int Y0, const CT out[4][3]) {
+    const int tg = threadIdx.x & (kGroupThreads - 1);
+    const int lane = tg & 31, w = tg >> 5;
+    const int x = X0 + lane;
+    if (x >= p.W) return;
+    const size_t plane = (size_t)p.W * p.H;
+    CT *oc = (CT *)p.out_color[kk];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int y = Y0 + 4 * w + r;
+        if (y >= p.H) continue;
+        const size_t q = (size_t)y * p.W + x;
+        oc[q] = out[r][0];
+        oc[plane + q] = out[r][1];
+        oc[2 * plane + q] = out[r][2];
+        p.out_mask[kk][q] = 0;
+    }
+}
+
+// Level-5 node of a tile whose pixels are all valid, from columns of four pixels (same pyramid as mean4 over
+// valid children): levels 1 and 2 by shuffles, the level-2 row of each warp to shared memory, levels 3-5 by
+// warp 0, which publishes it.  The other warps only arrive at the group barrier.
+template <typename CT, int WX, int WY>
+__device__ __forceinline__ void smooth_publish(EngineSmem<CT, WX, WY> &s, const TileParams &p, int g, int kk, int tile,
+                                               int buf, const CT out[4][3]) {
+    const int tg = threadIdx.x & (kGroupThreads - 1);
+    const int lane = tg & 31, w = tg >> 5;
+    float4 px[4], pp[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        px[r] = make_float4(to_f<CT>(out[r][0]), to_f<CT>(out[r][1]), to_f<CT>(out[r][2]), 1.0f);
+        pp[r] = make_float4(__shfl_xor_sync(0xFFFFFFFFu, px[r].x, 1), __shfl_xor_sync(0xFFFFFFFFu, px[r].y, 1),
+                            __shfl_xor_sync(0xFFFFFFFFu, px[r].z, 1), 1.0f);
+    }
+    const bool odd = lane & 1;
+    // level 1: rows 0-1 (A) and 2-3 (B) of this column pair, children in (row, column) order
+    const float4 A = odd ? mean4(pp[0], px[0], pp[1], px[1]) : mean4(px[0], pp[0], px[1], pp[1]);
+    const float4 B = odd ? mean4(pp[2], px[2], pp[3], px[3]) : mean4(px[2], pp[2], px[3], pp[3]);
+    const float4 Ap = make_float4(__shfl_xor_sync(0xFFFFFFFFu, A.x, 2), __shfl_xor_sync(0xFFFFFFFFu, A.y, 2),
+                                  __shfl_xor_sync(0xFFFFFFFFu, A.z, 2), 1.0f);
+    const float4 Bp = make_float4(__shfl_xor_sync(0xFFFFFFFFu, B.x, 2), __shfl_xor_sync(0xFFFFFFFFu, B.y, 2),
+                                  __shfl_xor_sync(0xFFFFFFFFu, B.z, 2), 1.0f);
+    const bool right = lane & 2;
+    const float4 n2 = right ? mean4(Ap, A, Bp, B) : mean4(A, Ap, B, Bp);
+    float4 *l2 = s.l2[g][buf];
+    if ((lane & 3) == 0) l2[w * 8 + (lane >> 2)] = n2;
+    if (w != 0) {
+        asm volatile("bar.arrive %0, %1;" ::"r"(2 + g), "r"(kGroupThreads) : "memory");
+        return;
+    }
+    bar_sync(2 + g, kGroupThreads);
+    float4 l3, l4, l5;
+    upper_levels(l2, l3, l4, l5);
+    if (lane == 0) publish_node(p, l5, kk, tile);
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Consumers
+// ------------------------------------------------------------------------------------------------------------
+template <typename CT, int WX, int WY, bool FILL>
+__device__ void engine_consumer(EngineSmem<CT, WX, WY> &s, const TileParams &p, bool vec) {
+    const int tid = threadIdx.x;  // 0 .. 767
+    const int g = tid >> 8, tg = tid & (kGroupThreads - 1);
+    const int bx = tg & 15, by = tg >> 4;
+    const bool active = g < p.nfrac;
+    const GlobalAcc<CT> ga{(const CT *)p.color, p.depth, p.mv, p.W, (size_t)p.W * p.H};
+    bool aborted = false;
+    uint32_t ndone = 0;  // (tile, fraction) items this group finished
+    for (uint32_t i = 0;; ++i) {
+        const int b = (int)(i & 1u);
+        const bool ok = mbar_wait_or_abort(&s.full[b], (i >> 1) & 1u, &s.abort);
+        const TileSlot &sl = s.slot[b];
+        const int mode = ok ? sl.plan.mode : kModeEnd;
+        Window<CT, WX, WY> &win = s.win[b];
+        if (ok && mode == 0)
+            build_source_words(win, sl.plan.wx0, sl.plan.wy0, sl.N, __uint_as_float(sl.plan.umx),
+                               __uint_as_float(sl.plan.umy), tid);
+        if (ok && mode >= 1 && mode <= 3 && active)
+            for (int r = tg; r < kRegionN; r += kGroupThreads) s.key[g][r] = kKeyEmpty;
+        if (bar_red_or(kBarConsumers, kConsumerThreads, !ok)) {
+            if (tid == 0) {
+                atomicExch(p.status, (uint32_t)EXW_ERR_TIMEOUT);
+                *(volatile int *)&s.abort = 1;
+            }
+            aborted = true;
+            break;
+        }
+        if (mode == kModeEnd) break;
+        const int tile = sl.tile, X0 = sl.X0, Y0 = sl.Y0;
+        const int RX0 = X0 - 1, RY0 = Y0 - 1;
+        const int wx0 = sl.plan.wx0, wy0 = sl.plan.wy0;
+        if (mode == 1) {
+            const WinAcc<CT, WX, WY> wa{&win, wx0, wy0};
+            engine_splat_window(s.key, p, wa, plan_union(sl.plan, p.nfrac), RX0, RY0, tid);
+            bar_sync(kBarConsumers, kConsumerThreads);
+        } else if (mode == 2 || mode == 3) {
+            engine_splat_global(s, p, RX0, RY0, tid);
+        }
+        if (active) {
+            const int kk = g, k = p.k0 + kk;
+            const int TX = X0 + 2 * bx, TY = Y0 + 2 * by;
+            float4 c[4];
+            uint8_t m[4];
+            if (mode == 5) {
+                CT out[4][3];
+                smooth_column<CT, WX, WY>(win, wx0, wy0, sl.u[kk], X0, Y0, out);
+                store_column<CT>(p, kk, X0, Y0, out);
+                if (FILL) {
+                    smooth_publish(s, p, g, kk, tile, (int)(i & 1u), out);
+                    ++ndone;
+                }
+            } else if (mode == 0) {
+                const UniformFrac &u = sl.u[kk];
+                if (u.flags & kInterior) uniform_block_any<CT, WX, WY, false>(win, wx0, wy0, p, u, TX, TY, c, m);
+                else uniform_block_any<CT, WX, WY, true>(win, wx0, wy0, p, u, TX, TY, c, m);
+            } else if (mode == 1) {
+                const WinAcc<CT, WX, WY> wa{&win, wx0, wy0};
+                gather_block<CT>(s.key[kk], wa, p, k, TX, TY, bx, by, c, m);
+            } else if (mode == 2 || mode == 3) {
+                gather_block<CT>(s.key[kk], ga, p, k, TX, TY, bx, by, c, m);
+            } else {  // 4: nothing lands
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    c[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    m[t] = (TX + (t & 1) < p.W && TY + (t >> 1) < p.H) ? (uint8_t)EXW_MASK_EMPTY : (uint8_t)0;
+                }
+            }
+            if (mode == 5) {
+                // stored above
+            } else if (FILL) {
+                fill_store_block(s, p, g, kk, tile, (int)(i & 1u), TX, TY, c, m, vec);
+                ++ndone;
+            } else {
+                const bool all[4] = {true, true, true, true};
+                store_block<CT>(p, kk, TX, TY, c, m, all, vec);
+                if (mode >= 1 && mode <= 3)
+                    bar_sync(2 + g, kGroupThreads);  // every key read of the group is done before the next init
+            }
+        }
+        if (mode == 0) fence_proxy_async_smem();  // generic writes to the window before the next TMA into it
+        __syncwarp();
+        if ((tid & 31) == 0) mbar_arrive(&s.empty[b]);
+    }
+    if (FILL && active && !aborted) {
+        // Count this group's items after a fence over its level-5 nodes; the group that completes the frame's
+        // count builds the coarse levels.
+        if (tg == 0) {
+            __threadfence();
+            const uint32_t total = (uint32_t)(p.n5x * p.n5y) * (uint32_t)p.nfrac;
+            s.last[g] = ndone > 0u && atomicAdd(&p.fh->done, ndone) + ndone == total;
+        }
+        bar_sync(2 + g, kGroupThreads);
+        if (s.last[g]) {
+            __threadfence();
+            engine_coarse_pass(p, g);
+        }
+    }
+}
+
+}  // namespace exw

@@ -1,19 +1,6 @@
-// exw_fwd.cu -- forward kernels: fused splat+gather+fill (persistent TMA and plain), tile plans, staged gather,
-// staged fill, coarse fix-up.
-//
-// The persistent TMA kernel runs 2 CTAs of 512 threads per SM (about 100 KB of shared memory each).  Each CTA takes
-// 32 x 32 target tiles from a queue; the plan kernel has already chosen, per tile, how to stage its sources: the
-// source depth, motion and colour of the rectangle that can land in the tile (plus its one-pixel ring), grown by one
-// pixel for the bilinear taps, comes into shared memory with three TMA loads (cp.async.bulk.tensor, mbarrier
-// completion):
-//   uniform: every candidate source tile carries one and the same motion, so each fraction is a pure translation
-//            and the winners are read off the window directly -- no splat, no atomics;
-//   mode 1:  one window covers the rectangles of all fractions -> one load, splat all fractions, gather each;
-//   mode 2:  per fraction, a window for that fraction's rectangle;
-//   mode 3:  a rectangle too large for a window -> the tile is processed from global memory.
-// While one CTA of an SM waits for its TMA load, the other computes.  Tiles without a valid pixel after the fill
-// are finished from the coarse pyramid levels, which the CTA finishing the frame's last tile builds (a done
-// counter in the workspace; no grid-wide barrier and no spin on other CTAs).
+// exw_fwd.cu -- forward kernels besides the persistent engine (exw_engine.cu): the plain fused kernel (one tile
+// per CTA, sources from global memory, for frames whose rows cannot be TMA-staged), tile plans, the staged gather
+// (exw_warp), the staged fill (exw_fill_holes) and the coarse fix-up.
 #include "exw_items.cuh"
 
 namespace exw {
@@ -30,29 +17,6 @@ template <typename CT, int WX, int WY>
 __global__ void __launch_bounds__(kThreads) plan_kernel(TileParams p) {
     const int tile = blockIdx.x * kWarps + (threadIdx.x >> 5);
     if (tile < p.n5x * p.n5y) plan_tile<CT, WX, WY>(p, tile);
-}
-
-// Persistent fused kernel with TMA-staged source windows.
-template <typename CT, int WX, int WY, bool FILL>
-__global__ void __launch_bounds__(kThreads, 2)
-    fused_tma_kernel(TileParams p, const __grid_constant__ CUtensorMap tcol, const __grid_constant__ CUtensorMap tdep,
-                     const __grid_constant__ CUtensorMap tmv) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    TmaSmem<CT, WX, WY> &s = *reinterpret_cast<TmaSmem<CT, WX, WY> *>(smem_raw);
-    if (threadIdx.x == 0) {
-        mbar_init(&s.t.mbar, 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    uint32_t phase = 0;
-    const int ntiles = p.n5x * p.n5y;
-    for (;;) {
-        if (threadIdx.x == 0) s.t.tile = (int)atomicAdd(&p.fh->queue, 1u);
-        __syncthreads();
-        const int tile = s.t.tile;
-        if (tile >= ntiles) break;
-        if (!tma_tile<CT, WX, WY, FILL>(s, p, tcol, tdep, tmv, tile, phase)) return;
-    }
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -138,35 +102,6 @@ cudaError_t launch_fused(const TileParams &p, exw_dtype cdt, bool fill, cudaStre
     count_launch();
     timing_end("exw_fused", s);
     return cudaGetLastError();
-}
-
-template <typename CT, int WX, int WY, bool FILL>
-static cudaError_t launch_tma_t(const TileParams &p, const TmaMaps &m, int grid, cudaStream_t s) {
-    constexpr size_t kSmem = sizeof(TmaSmem<CT, WX, WY>);
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(fused_tma_kernel<CT, WX, WY, FILL>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    fused_tma_kernel<CT, WX, WY, FILL><<<grid, kThreads, kSmem, s>>>(p, m.col, m.depth, m.mv);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_fused_tma(const TileParams &p, const TmaMaps &m, exw_dtype cdt, bool fill, int grid,
-                             cudaStream_t s) {
-    timing_begin("exw_fused_tma", s);
-    cudaError_t e;
-    if (cdt == EXW_F32)
-        e = fill ? launch_tma_t<float, kWinXF32, kWinYF32, true>(p, m, grid, s)
-                 : launch_tma_t<float, kWinXF32, kWinYF32, false>(p, m, grid, s);
-    else
-        e = fill ? launch_tma_t<__half, kWinXF16, kWinYF16, true>(p, m, grid, s)
-                 : launch_tma_t<__half, kWinXF16, kWinYF16, false>(p, m, grid, s);
-    count_launch();
-    timing_end("exw_fused_tma", s);
-    return e;
 }
 
 cudaError_t launch_plan(const TileParams &p, exw_dtype cdt, cudaStream_t s) {

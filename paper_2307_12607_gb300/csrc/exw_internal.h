@@ -21,15 +21,17 @@ struct FrameHeader {
     uint32_t ninvalid[3];  // fill tiles without any valid pixel, per fraction
     uint32_t cready;       // batched path: the coarse values of this frame are written
     uint32_t queue;        // next tile of the persistent kernel
-    uint32_t nmode[4];     // tiles done as uniform / one window / one window per fraction / from global memory
+    uint32_t nmode[6];     // tiles done per plan mode (TilePlan::mode)
     uint32_t bdone;        // batched path: bounds regions finished
     uint32_t pdone;        // batched path: plan groups finished
+    uint32_t pad[14];
 };
-static_assert(sizeof(FrameHeader) == 64, "FrameHeader is 64 bytes");
+static_assert(sizeof(FrameHeader) == 128, "FrameHeader is 128 bytes");
 
 // Per target tile, how the fused pass stages its sources (written by the plan kernel).
 struct TilePlan {
-    int mode;          // 0 uniform motion, 1 one window, 2 one window per fraction, 3 global memory, 4 nothing lands
+    int mode;          // 0 uniform motion, 1 one window, 2 one window per fraction, 3 global memory, 4 nothing
+                       // lands, 5 uniform motion over smooth valid sources (every pixel a winner, every tap agrees)
     int wx0, wy0;      // window origin (modes 0 and 1)
     int pad0;
     int rect[3][4];    // per fraction, landing rectangle x0, x1, y0, y1 (source pixels; empty if x1 < x0)
@@ -40,7 +42,7 @@ static_assert(sizeof(TilePlan) == 80, "TilePlan is 80 bytes");
 
 // Byte offsets of the workspace sections for nframes frames of W x H with nfrac fractions.
 struct WsLayout {
-    size_t headers, tile_bounds, plans, nodes, list, fillval, coarse, keys, total;
+    size_t headers, tile_bounds, tile_depth, region_bounds, plans, nodes, list, fillval, coarse, keys, total;
     int nbx, nby;       // motion-bounds tiles
     int n5x, n5y;       // fill tiles (level-5 nodes of the pyramid)
     int ncoarse;        // pyramid nodes above level 5, per fraction
@@ -69,6 +71,10 @@ inline WsLayout ws_layout(int W, int H, int nframes, int nfrac, bool with_keys) 
     off += align_up((size_t)nframes * sizeof(FrameHeader));
     l.tile_bounds = off;
     off += align_up((size_t)l.nbx * l.nby * 16);
+    l.tile_depth = off;
+    off += align_up((size_t)l.nbx * l.nby * 8);
+    l.region_bounds = off;
+    off += align_up(n5 * 16);
     l.plans = off;
     off += align_up(n5 * sizeof(TilePlan));
     l.nodes = off;
@@ -96,6 +102,8 @@ struct TileParams {
     void *out_color[3];
     uint8_t *out_mask[3];
     const float4 *tile_bounds;
+    const float2 *tile_depth;   // per 8 x 8 tile: depth range of its pixels, (-1, -1) if one cannot land
+    const float4 *region_bounds;  // per 32 x 32 region (fill tile): motion bounds of its 8 x 8 tiles
     TilePlan *plans;            // [n5] staging plan per target tile (persistent TMA kernel)
     int nbx, nby;
     FrameHeader *fh;
@@ -121,13 +129,13 @@ cudaError_t launch_clear_keys(uint64_t *keys, size_t n, cudaStream_t s);
 cudaError_t launch_zero(void *p, size_t bytes, cudaStream_t s);
 cudaError_t launch_splat_global(const float *depth, const float *mv, int W, int H, int k, int L, uint64_t *keys,
                                 cudaStream_t s);
-cudaError_t launch_bounds(const float *depth, const float *mv, int W, int H, float4 *tile_bounds, FrameHeader *fh,
-                          cudaStream_t s);
+cudaError_t launch_bounds(const float *depth, const float *mv, int W, int H, float4 *tile_bounds, float2 *tile_depth,
+                          float4 *region_bounds, FrameHeader *fh, cudaStream_t s);
 cudaError_t launch_bounds_finalize(const FrameHeader *fh, float *frame_bounds, cudaStream_t s);
 cudaError_t launch_fused(const TileParams &p, exw_dtype cdt, bool fill, cudaStream_t s);
-cudaError_t launch_fused_tma(const TileParams &p, const TmaMaps &m, exw_dtype cdt, bool fill, int grid,
-                             cudaStream_t s);
 cudaError_t launch_plan(const TileParams &p, exw_dtype cdt, cudaStream_t s);
+cudaError_t launch_engine(const TileParams &p, const TmaMaps &m, exw_dtype cdt, bool fill, int grid, bool vec,
+                          cudaStream_t s);
 cudaError_t launch_warp_tiles(const TileParams &p, exw_dtype cdt, cudaStream_t s);
 cudaError_t launch_fill_tiles(const TileParams &p, exw_dtype cdt, cudaStream_t s);
 cudaError_t launch_fixup(const TileParams &p, exw_dtype cdt, cudaStream_t s);

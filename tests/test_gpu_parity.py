@@ -197,12 +197,42 @@ def test_tma_staging_modes_cover_all_tiles(b):
     ws = b.workspace(b.exw_workspace_bytes(b.OP_EXTRAPOLATE, 320, 192, b.F32, 1, 3), c.device)
     out, mask = b.exw_extrapolate(c, d, m, ws=ws)
     st = b.frame_stats(ws)
-    assert st["tiles_uniform"] + st["tiles_window_all"] + st["tiles_window_each"] + st["tiles_global"] == 10 * 6
+    assert sum(v for k, v in st.items() if k.startswith("tiles_") and k != "tiles_without_valid_pixel") == 10 * 6
     assert st["tiles_window_all"] > 0 and st["tiles_global"] + st["tiles_window_each"] > 0
     ref = oracle.extrapolate(color.astype(np.float64), depth, mv, 3)
     for j, (wo, wm, _) in enumerate(ref):
         np.testing.assert_array_equal(mask[j].cpu().numpy(), wm)
         np.testing.assert_allclose(out[j].cpu().numpy(), wo, rtol=0, atol=2e-6)
+
+
+@pytest.mark.parametrize("pan", [(1.3, -0.7), (-2.6, 0.0), (0.0, 1.9), (0.5, 0.5), (4.0, -8.0), (0.0, 0.0),
+                                 (-0.25, -3.75)])
+@pytest.mark.parametrize("dtype", [np.float32, np.float16])
+def test_smooth_tiles_every_residual_sign(b, pan, dtype):
+    # a slanted but smooth surface (depth within 1/32 over each tile's sources) under one motion: interior tiles are
+    # pure bilinear resamplings; the pans give every combination of residual signs, including none
+    W, H = 288, 160
+    rng = np.random.default_rng(11)
+    color = rng.uniform(size=(3, H, W)).astype(np.float32).astype(dtype)
+    yy, xx = np.mgrid[0:H, 0:W]
+    depth = (40.0 + 0.002 * xx + 0.003 * yy).astype(np.float32)
+    mv = np.empty((2, H, W), np.float32)
+    mv[0], mv[1] = pan
+    c, d, m = dev(color), dev(depth), dev(mv)
+    ws = b.workspace(b.exw_workspace_bytes(b.OP_EXTRAPOLATE, W, H, b.F16 if dtype == np.float16 else b.F32, 1, 3),
+                     c.device)
+    for fill in (True, False):
+        out, mask = b.exw_extrapolate(c, d, m, fill=fill, ws=ws)
+        assert b.frame_stats(ws)["tiles_smooth"] > 0
+        out2, mask2 = b.exw_extrapolate(c, d, m, fill=fill, tma=False)
+        assert torch.equal(mask, mask2)
+        iv = torch.int16 if dtype == np.float16 else torch.int32
+        assert torch.equal(out.view(iv), out2.view(iv))
+        ref = oracle.extrapolate(color.astype(np.float64), depth, mv, 3, fill=fill, storage=dtype)
+        tol = 1e-3 if dtype == np.float16 else 2e-6
+        for j, (wo, wm, _) in enumerate(ref):
+            np.testing.assert_array_equal(mask[j].cpu().numpy(), wm)
+            np.testing.assert_allclose(out[j].cpu().numpy().astype(np.float64), wo, rtol=0, atol=tol)
 
 
 def test_uniform_tiles_with_foreign_motion_inside_their_source(b):
@@ -223,7 +253,8 @@ def test_uniform_tiles_with_foreign_motion_inside_their_source(b):
     ws = b.workspace(b.exw_workspace_bytes(b.OP_EXTRAPOLATE, W, H, b.F32, 1, 3), c.device)
     for fill in (True, False):
         out, mask = b.exw_extrapolate(c, d, m, fill=fill, ws=ws)
-        assert b.frame_stats(ws)["tiles_uniform"] > 0
+        st = b.frame_stats(ws)
+        assert st["tiles_uniform"] > 0 and st["tiles_smooth"] > 0
         ref = oracle.extrapolate(color.astype(np.float64), depth, mv, 3, fill=fill)
         for j, (wo, wm, _) in enumerate(ref):
             np.testing.assert_array_equal(mask[j].cpu().numpy(), wm)
@@ -411,8 +442,8 @@ def test_timing_and_launch_count(b):
     b.exw_timing_enable(True)
     b.exw_extrapolate(dev(color), dev(depth), dev(mv))
     torch.cuda.synchronize()
-    assert "exw_fused_tma" in b.exw_timing_names()
-    ms, n = b.exw_timing_query("exw_fused_tma")
+    assert "exw_engine" in b.exw_timing_names()
+    ms, n = b.exw_timing_query("exw_engine")
     assert n == 1 and ms > 0
     b.exw_timing_enable(False)
     assert b.exw_launch_count() - n0 == 5   # zero, bounds, plan, fused, fixup
