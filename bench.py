@@ -63,7 +63,10 @@ def dist_env():
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a kernel from one ncu capture, with the
 # hash of the kernel sources it was taken on: reported only while the sources are unchanged, else null.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    ("exw_engine", "sequence_1080p_fp32"): (67.92e6, "c95faedd639a23c4"),
+    ("exw_engine", "warp_4k_fp16"): (233.14e6, "c95faedd639a23c4"),
+}
 
 
 def csrc_hash() -> str:
@@ -90,6 +93,29 @@ def peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def replica_seed(rank: int) -> int:
+    """Scene seed of rank ``rank``'s replica: rank 0 extrapolates the configured sequence, every other rank its own
+    independent sequence of the same recipe (weak scaling over independent problems)."""
+    from paper_2307_12607_gb300 import scenes
+    return scenes.workload_seed(1, rank)
+
+
+def max_over_ranks(x: float, device) -> float:
+    """The maximum of x over all ranks (the step time of a replicated run); x itself on a single process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: int, seconds: float) -> float:
+    """Units all ranks processed per second (millions), from the max-over-ranks time."""
+    return world * units_per_rank / seconds / 1e6
 
 
 def render_sequence(nframes, seed_scene=None):
@@ -377,7 +403,7 @@ def run_exw(args):
     build.build()
 
     F = args.frames
-    seq = render_sequence(F)
+    seq = render_sequence(F, replica_seed(rank))
     s, col, dep, mv = seq
     W, H = s.W, s.H
     c = torch.from_numpy(col).to(devc)
@@ -413,13 +439,9 @@ def run_exw(args):
         torch.cuda.synchronize()
         barrier()
     launches = b.exw_launch_count() - launches0
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=devc)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, devc)
     out_px = F * NFRAC * W * H
-    value = world * out_px / (ms / 1e3) / 1e6
+    value = whole_job_rate(world, out_px, ms / 1e3)
 
     # per-kernel event timing over a second timed region (same steps), on the launching stream
     b.exw_timing_enable(True)
@@ -471,12 +493,8 @@ def run_exw(args):
     for _ in range(args.e2e_steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device=devc)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-        barrier()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, devc)
+    barrier()
     h2d = (hc.numel() * 4 + hd.numel() * 4 + hm.numel() * 4)
     d2h = ho.numel() * 4 + hmask.numel()
 
@@ -498,7 +516,7 @@ def run_exw(args):
                 "clocks": clocks.summary(),
                 "roofline": roofline,
                 "cpu_baseline": cpu,
-                "e2e": {"value": world * out_px / e2e_s / 1e6, "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
+                "e2e": {"value": whole_job_rate(world, out_px, e2e_s), "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
                 "extras": extras}
         print(json.dumps(line), flush=True)
