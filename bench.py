@@ -461,13 +461,15 @@ def run_exw(args):
     per_src_px = {"exw_fused": compulsory, "exw_engine": compulsory,
                   "exw_bounds": 8 + 16.0 / 64,                               # motion read + tile bounds written
                   "exw_fixup": 0.0}
-    alg_bytes = per_src_px.get(dom, 0.0) * W * H
+    frames_per_launch = F * args.steps / n   # the engine takes up to 48 frames per launch
+    alg_bytes = per_src_px.get(dom, 0.0) * W * H * frames_per_launch
     peak, peak_kind = peaks()
     achieved = alg_bytes / (avg_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": measured_traffic(dom, "sequence_1080p_fp32"),
                 "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": alg_bytes, "mean_launch_ms": avg_ms,
+                "source_frames_per_launch": frames_per_launch,
                 "kernel_share": {k: v[0] / sum(x[0] for x in kern.values()) for k, v in kern.items()},
                 "tile_modes_frame0": b.frame_stats(ws, 0)}
 

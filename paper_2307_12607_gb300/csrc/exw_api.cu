@@ -13,65 +13,6 @@
 namespace exw {
 
 // ------------------------------------------------------------------------------------------------------------
-// TMA tensor maps (cuTensorMapEncodeTiled, reached through the runtime's driver entry point)
-// ------------------------------------------------------------------------------------------------------------
-static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static bool tried = false;
-    static std::mutex mu;
-    std::lock_guard<std::mutex> g(mu);
-    if (!tried) {
-        tried = true;
-        void *ptr = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
-    }
-    return fn;
-}
-
-// A [planes][H][W] array (planes = 1 gives a 2-D map) with box [planes][by][bx].
-static bool encode_map(CUtensorMap *m, CUtensorMapDataType t, const void *base, int W, int H, int planes,
-                       size_t esize, int bx, int by) {
-    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
-    if (fn == nullptr) return false;
-    const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)planes};
-    const cuuint64_t strides[2] = {(cuuint64_t)W * esize, (cuuint64_t)W * H * esize};
-    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)planes};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    const cuuint32_t rank = planes > 1 ? 3 : 2;
-    return fn(m, t, rank, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-// TMA staging needs 16-byte aligned bases and rows (W * element size a multiple of 16).
-static bool tma_eligible(const void *color, const float *depth, const float *mv, int W, exw_dtype cdt) {
-    const int a = cdt == EXW_F16 ? 8 : 4;
-    return (W % a) == 0 && ((uintptr_t)color & 15u) == 0 && ((uintptr_t)depth & 15u) == 0 &&
-           ((uintptr_t)mv & 15u) == 0 && encode_fn() != nullptr;
-}
-
-static bool make_maps(TmaMaps *m, const void *color, const float *depth, const float *mv, int W, int H,
-                      exw_dtype cdt) {
-    const int bx = cdt == EXW_F16 ? kWinXF16 : kWinXF32, by = cdt == EXW_F16 ? kWinYF16 : kWinYF32;
-    const CUtensorMapDataType ct = cdt == EXW_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    return encode_map(&m->col, ct, color, W, H, 3, cdt == EXW_F16 ? 2 : 4, bx, by) &&
-           encode_map(&m->depth, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, depth, W, H, 1, 4, bx, by) &&
-           encode_map(&m->mv, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, mv, W, H, 2, 4, bx, by);
-}
-
-static int sm_count() {
-    int dev = 0, n = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
-                                                  cudaSuccess)
-        return 1;
-    return n > 0 ? n : 1;
-}
-
-// ------------------------------------------------------------------------------------------------------------
 // Kernel timing: CUDA event pairs on the launching stream around every launch, while enabled.
 // ------------------------------------------------------------------------------------------------------------
 struct TimedLaunch {
@@ -180,9 +121,15 @@ size_t exw_workspace_bytes(exw_op op, int W, int H, exw_dtype cdt, int nframes, 
     switch (op) {
         case EXW_OP_MOTION_BOUNDS:
         case EXW_OP_FILL_HOLES: return ws_layout(W, H, 1, 1, false).total;
-        case EXW_OP_EXTRAPOLATE:
+        case EXW_OP_EXTRAPOLATE: {
             if (nframes < 1 || nfrac < 1 || nfrac > EXW_MAX_FRAC) return 0;
-            return ws_layout(W, H, nframes, nfrac, false).total;
+            EngineSpec sp{};
+            sp.src.W = W;
+            sp.src.H = H;
+            sp.src.cdt = cdt;
+            std::vector<EngineSpec> one(1, sp);
+            return engine_workspace_bytes(one.data(), nframes, nfrac, true);
+        }
         case EXW_OP_WARP_BACKWARD: return ws_layout(W, H, 1, 1, true).total;
     }
     return 0;
@@ -279,41 +226,12 @@ exw_status exw_extrapolate(const exw_frame *frames, int nframes, int nfrac, unsi
             if (!aligned(o.color, csize(cdt)) || !aligned(o.mask, 1)) return EXW_ERR_INVALID_ARG;
         }
     }
-    const WsLayout l = ws_layout(W, H, nframes, nfrac, false);
-    if (!aligned16(ws) || ws_bytes < l.total) return EXW_ERR_WORKSPACE;
-    if (entry_check() != EXW_OK) return EXW_ERR_CUDA;
-    cudaStream_t s = (cudaStream_t)stream;
-    const bool fill = (flags & EXW_FLAG_NO_FILL) == 0;
-    cudaError_t e = launch_zero(ws, l.headers + (size_t)nframes * sizeof(FrameHeader), s);
-    for (int f = 0; f < nframes && e == cudaSuccess; ++f) {
-        TileParams p = tile_params(l, ws, W, H, nfrac, 2, 1, f);
-        p.color = frames[f].color;
-        p.depth = frames[f].depth;
-        p.mv = frames[f].mv;
-        for (int j = 0; j < nfrac; ++j) {
-            p.out_color[j] = out[(size_t)f * nfrac + j].color;
-            p.out_mask[j] = out[(size_t)f * nfrac + j].mask;
-        }
-        e = launch_bounds(p.depth, p.mv, W, H, (float4 *)p.tile_bounds, (float2 *)p.tile_depth,
-                          (float4 *)p.region_bounds, p.fh, s);
-        TmaMaps maps;
-        const bool tma = (flags & EXW_FLAG_NO_TMA) == 0 && tma_eligible(p.color, p.depth, p.mv, W, cdt) &&
-                         make_maps(&maps, p.color, p.depth, p.mv, W, H, cdt);
-        if (e == cudaSuccess) {
-            if (tma) {
-                const int ntiles = l.n5x * l.n5y, g = sm_count();
-                bool vec = (W % 2) == 0;
-                for (int j = 0; j < nfrac; ++j)
-                    vec = vec && aligned(p.out_color[j], 2 * csize(cdt)) && aligned(p.out_mask[j], 2);
-                e = launch_plan(p, cdt, s);
-                if (e == cudaSuccess) e = launch_engine(p, maps, cdt, fill, ntiles < g ? ntiles : g, vec, s);
-            } else {
-                e = launch_fused(p, cdt, fill, s);
-            }
-        }
-        if (e == cudaSuccess && fill) e = launch_fixup(p, cdt, s);
+    std::vector<EngineSpec> specs((size_t)nframes);
+    for (int f = 0; f < nframes; ++f) {
+        specs[f].src = frames[f];
+        for (int j = 0; j < nfrac; ++j) specs[f].out[j] = out[(size_t)f * nfrac + j];
     }
-    return from_cuda(e);
+    return engine_run(specs.data(), nframes, nfrac, flags, ws, ws_bytes, nullptr, true, (cudaStream_t)stream);
 }
 
 exw_status exw_warp_backward(const float *grad_out, const void *color, exw_dtype cdt, const float *depth,

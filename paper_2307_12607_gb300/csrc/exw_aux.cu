@@ -36,7 +36,8 @@ __global__ void __launch_bounds__(256, 8) bounds_kernel(const float *__restrict_
                                                         int W, int H, float4 *tile_bounds, float2 *tile_depth,
                                                         float4 *region_bounds, FrameHeader *fh) {
     __shared__ float4 part[64];
-    bounds_region<8>(depth, mv, W, H, tile_bounds, tile_depth, region_bounds, fh, blockIdx.x, blockIdx.y, part, true);
+    bounds_region<8>(depth, mv, W, H, tile_bounds, tile_depth, region_bounds, fh, blockIdx.x, blockIdx.y, part, true,
+                     (int)threadIdx.x, CtaBarrier{});
 }
 
 __global__ void bounds_finalize_kernel(const FrameHeader *fh, float *out) {

@@ -1,18 +1,14 @@
-// exw_batched.cu -- many independent streams of mixed sizes and colour types in ONE persistent launch.
+// exw_batched.cu -- host side of the persistent engine: workspace layout, kernel parameters (per-stream tile
+// parameters, TMA maps, the diagonal item queue), launches in groups of at most 48 streams, and the autotuner;
+// the entry points exw_extrapolate_batched and the tuner API.  exw_extrapolate (exw_api.cu) runs the frames of a
+// sequence through the same engine_run, as streams of one size.
 //
-// Every stream needs four stages per source frame: motion bounds (one item per 32 x 32 source region), tile plans
-// (one item per 16 target tiles), fused tiles (one item per 32 x 32 target tile) and, with the fill, the coarse
-// fix-up (a few items).  All items of all streams sit in one queue in the workspace; CTAs take items in order.  The
-// queue is laid out diagonally -- bounds of stream d, plans of stream d-1, tiles of stream d-2, fix-ups of stream
-// d-3, for d = 0, 1, ... -- so an item's dependencies (the previous stage of its own stream) were taken from the
-// queue well before it and have normally finished: a wait only spins when they have not.  A wait is a bounded spin
-// of thread 0 on a counter of the stream (acquire load, back-off) that gives up after an iteration limit or as soon
-// as the workspace status word reports an error; it then records EXW_ERR_TIMEOUT and the CTA leaves.  Items only
-// wait for items taken earlier, which are held by CTAs already running, so the waits end without any co-residency
-// guarantee.
+// Queue: for d = 0, 1, ... the bounds items of stream d, the plan items of stream d - lag, the tile items of
+// stream d - 2 lag and the fix-up items of stream d - 3 lag.  A stage's items thus come after every item of the
+// previous stage of the same stream, so the producer's wait for them only spins when they have not finished yet.
 //
-// The autotuner times the schedule choices (CTAs per SM, TMA windows or global-memory reads) on the caller's batch
-// the first time it sees a set of sizes and keeps the fastest.
+// The autotuner times the schedule choices (TMA windows or global-memory reads, the queue lag) on the caller's
+// streams the first time it sees a set of sizes, outside any stream capture, and keeps the fastest.
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -22,161 +18,34 @@
 
 #include <cudaTypedefs.h>
 
-#include "exw_items.cuh"
+#include "exw_engine.cuh"
 
 namespace exw {
 
-constexpr int kMaxBatch = 48;
-constexpr uint32_t kBatchWaitLimit = 1u << 22;   // ~0.5-1 s of back-off before a wait gives up
-constexpr uint32_t kInjectedWaitLimit = 20000u;  // the injected fault gives up after a few milliseconds
+cudaError_t launch_engine(const EngineParams &ep, bool fill, int grid, cudaStream_t s);
 
-struct BatchStream {
-    TileParams p;
-    int cdt;    // EXW_F32 / EXW_F16
-    int tma;    // stage this stream's tiles with TMA windows
-    int nrx;    // bounds regions per row
-    int nregions, nplans, ntiles, nfix;
-};
+constexpr size_t kEngineHeader = 256;  // status word
 
-struct BatchSeg {
-    int start;          // first queue index of the segment
-    uint16_t stream;
-    uint16_t stage;     // 0 bounds, 1 plans, 2 tiles, 3 fix-up
-};
-
-struct BatchParams {
-    int n, nseg, total, fill, inject;
-    uint32_t *queue, *status;
-    BatchStream st[kMaxBatch];
-    BatchSeg seg[4 * kMaxBatch];
-    CUtensorMap maps[kMaxBatch][3];  // colour, depth, motion
-};
-static_assert(sizeof(BatchParams) <= 32764, "kernel parameters fit the 32 KB limit");
-
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Thread 0 waits until *counter >= target; all threads return the same verdict.  False: the limit ran out or
-// another CTA reported an error (the status word is set).
-__device__ bool batch_wait(const BatchParams &bp, const uint32_t *counter, uint32_t target, uint32_t limit,
-                           int *flag) {
-    if (threadIdx.x == 0) {
-        int ok = 0;
-        for (uint32_t i = 0; i < limit; ++i) {
-            if (ld_acquire(counter) >= target) {
-                ok = 1;
-                break;
-            }
-            if (*(volatile uint32_t *)bp.status != 0u) break;
-            __nanosleep(i < 64 ? 32 : 256);
-        }
-        if (!ok) atomicCAS(bp.status, 0u, (uint32_t)EXW_ERR_TIMEOUT);
-        *flag = ok;
-    }
-    __syncthreads();
-    return *flag != 0;
-}
-
-// Make this CTA's writes visible, then count the item in *counter.
-__device__ __forceinline__ void batch_signal(uint32_t *counter) {
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) atomicAdd(counter, 1u);
-}
-
-template <bool FILL>
-__global__ void __launch_bounds__(kThreads, 2) batched_kernel(const __grid_constant__ BatchParams bp) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    TmaSmem<float, kWinXF32, kWinYF32> &sf = *reinterpret_cast<TmaSmem<float, kWinXF32, kWinYF32> *>(smem_raw);
-    TmaSmem<__half, kWinXF16, kWinYF16> &sh = *reinterpret_cast<TmaSmem<__half, kWinXF16, kWinYF16> *>(smem_raw);
-    TileSmem &ts = sf.t;  // the same bytes in both views (equal window sizes)
-    __shared__ float4 part[kWarps * 8];
-    if (threadIdx.x == 0) {
-        mbar_init(&ts.mbar, 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    uint32_t phase = 0;
-    for (;;) {
-        if (threadIdx.x == 0) ts.tile = (int)atomicAdd(bp.queue, 1u);
-        __syncthreads();
-        const int item = ts.tile;
-        if (item >= bp.total) break;
-        int lo = 0, hi = bp.nseg - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (bp.seg[mid].start <= item) lo = mid;
-            else hi = mid - 1;
-        }
-        const BatchSeg &sg = bp.seg[lo];
-        const int local = item - sg.start;
-        const BatchStream &st = bp.st[sg.stream];
-        const TileParams &p = st.p;
-        FrameHeader *fh = p.fh;
-        if (sg.stage == 0) {
-            bounds_region<kWarps>(p.depth, p.mv, p.W, p.H, const_cast<float4 *>(p.tile_bounds),
-                          const_cast<float2 *>(p.tile_depth), const_cast<float4 *>(p.region_bounds), fh,
-                          local % st.nrx, local / st.nrx, part, true);
-            batch_signal(&fh->bdone);
-        } else if (sg.stage == 1) {
-            if (!batch_wait(bp, &fh->bdone, (uint32_t)st.nregions, kBatchWaitLimit, &ts.flag)) return;
-            const int tile = local * kWarps + (threadIdx.x >> 5);
-            if (tile < st.ntiles) {
-                if (st.cdt == EXW_F16) plan_tile<__half, kWinXF16, kWinYF16>(p, tile);
-                else plan_tile<float, kWinXF32, kWinYF32>(p, tile);
-            }
-            batch_signal(&fh->pdone);
-        } else if (sg.stage == 2) {
-            const bool injected = bp.inject && sg.stream == 0 && local == 0;
-            if (!batch_wait(bp, &fh->pdone, (uint32_t)st.nplans + (injected ? 1u : 0u),
-                            injected ? kInjectedWaitLimit : kBatchWaitLimit, &ts.flag))
-                return;
-            if (st.tma) {
-                const CUtensorMap *m = bp.maps[sg.stream];
-                const bool ok = st.cdt == EXW_F16
-                                    ? tma_tile<__half, kWinXF16, kWinYF16, FILL>(sh, p, m[0], m[1], m[2], local, phase)
-                                    : tma_tile<float, kWinXF32, kWinYF32, FILL>(sf, p, m[0], m[1], m[2], local, phase);
-                if (!ok) return;
-            } else {
-                if (st.cdt == EXW_F16) plain_tile<__half, FILL>(ts, p, local);
-                else plain_tile<float, FILL>(ts, p, local);
-            }
-            if (FILL && ts.last) {  // this CTA ran the coarse pass: its values are ready for the fix-up
-                __threadfence();
-                __syncthreads();
-                if (threadIdx.x == 0) atomicExch(&fh->cready, 1u);
-            }
-        } else {
-            if (!batch_wait(bp, &fh->cready, 1u, kBatchWaitLimit, &ts.flag)) return;
-            if (st.cdt == EXW_F16) fixup_slice<__half>(p, (uint32_t)local, (uint32_t)st.nfix);
-            else fixup_slice<float>(p, (uint32_t)local, (uint32_t)st.nfix);
-        }
-        __syncthreads();
-    }
-}
-
-// ------------------------------------------------------------------------------------------------------------
-// Host side
-// ------------------------------------------------------------------------------------------------------------
-constexpr size_t kBatchHeader = 256;  // status word, queue counter
-
-struct BatchLayout {
-    size_t headers;              // n frame headers
-    size_t base[kMaxBatch];      // start of each stream's sections
-    WsLayout l[kMaxBatch];
+// Workspace: status block, one 128-byte header per stream (frame), then the sections of min(n, 48) slots; a
+// launch uses slots 0.. for its streams.  shared_size: every stream has specs[0]'s size (a sequence), so every
+// slot has that layout.
+struct EngineLayout {
+    size_t headers;
+    int nslots;
+    size_t base[kMaxStreams];
+    WsLayout l[kMaxStreams];
     size_t total;
 };
 
-static BatchLayout batch_layout(const exw_stream_desc *d, int n, int nfrac) {
-    BatchLayout b{};
-    size_t off = kBatchHeader;
+static EngineLayout engine_layout(const EngineSpec *specs, int n, int nfrac, bool shared_size) {
+    EngineLayout b{};
+    size_t off = kEngineHeader;
     b.headers = off;
     off += align_up((size_t)n * sizeof(FrameHeader));
-    for (int i = 0; i < n; ++i) {
-        b.l[i] = ws_layout(d[i].src.W, d[i].src.H, 1, nfrac, false);
+    b.nslots = n < kMaxStreams ? n : kMaxStreams;
+    for (int i = 0; i < b.nslots; ++i) {
+        const exw_frame &f = specs[shared_size ? 0 : i].src;
+        b.l[i] = ws_layout(f.W, f.H, 1, nfrac, false);
         b.base[i] = off;
         off += b.l[i].total;
     }
@@ -184,18 +53,11 @@ static BatchLayout batch_layout(const exw_stream_desc *d, int n, int nfrac) {
     return b;
 }
 
-static bool encode(PFN_cuTensorMapEncodeTiled_v12000 fn, CUtensorMap *m, CUtensorMapDataType t, const void *base,
-                   int W, int H, int planes, size_t esize, int bx, int by) {
-    const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)planes};
-    const cuuint64_t strides[2] = {(cuuint64_t)W * esize, (cuuint64_t)W * H * esize};
-    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)planes};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    return fn(m, t, planes > 1 ? 3 : 2, const_cast<void *>(base), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+size_t engine_workspace_bytes(const EngineSpec *specs, int n, int nfrac, bool shared_size) {
+    return engine_layout(specs, n, nfrac, shared_size).total;
 }
 
-static PFN_cuTensorMapEncodeTiled_v12000 batch_encode_fn() {
+static PFN_cuTensorMapEncodeTiled_v12000 engine_encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static std::once_flag once;
     std::call_once(once, [] {
@@ -209,26 +71,42 @@ static PFN_cuTensorMapEncodeTiled_v12000 batch_encode_fn() {
     return fn;
 }
 
+// A [planes][H][W] array (planes = 1 gives a 2-D map) with box [planes][by][bx].
+static bool encode(PFN_cuTensorMapEncodeTiled_v12000 fn, CUtensorMap *m, CUtensorMapDataType t, const void *base,
+                   int W, int H, int planes, size_t esize, int bx, int by) {
+    const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)planes};
+    const cuuint64_t strides[2] = {(cuuint64_t)W * esize, (cuuint64_t)W * H * esize};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)planes};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(m, t, planes > 1 ? 3 : 2, const_cast<void *>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 struct Schedule {
-    int ctas_per_sm;
     int tma;  // 1: TMA windows where a stream allows them; 0: global-memory reads everywhere
+    int lag;  // queue distance between consecutive stages of one stream
 };
 
-static bool build_params(BatchParams *bp, const exw_stream_desc *d, int n, int nfrac, bool fill, void *ws,
-                         const BatchLayout &bl, const Schedule &sc, bool inject) {
-    std::memset(bp, 0, sizeof(BatchParams));
-    char *b = (char *)ws;
-    bp->n = n;
-    bp->fill = fill ? 1 : 0;
-    bp->inject = inject ? 1 : 0;
-    bp->status = (uint32_t *)b;
-    bp->queue = (uint32_t *)(b + 4);
-    PFN_cuTensorMapEncodeTiled_v12000 fn = batch_encode_fn();
+// Kernel parameters for streams [first, first + n) of specs, in slots 0 .. n - 1.  The bounds and plans of
+// slot 0 -- the head of the pipeline, which nothing else overlaps -- are computed by the bounds and plan kernels
+// before the launch, at their full occupancy; the queue starts with slot 0's tiles.
+static bool build_params(EngineParams *ep, const EngineSpec *specs, int first, int n, int nfrac, bool fill, char *ws,
+                         const EngineLayout &bl, const Schedule &sc, bool inject) {
+    std::memset(ep, 0, sizeof(EngineParams));
+    FrameHeader *headers = (FrameHeader *)(ws + bl.headers) + first;
+    ep->n = n;
+    ep->inject = inject ? 1 : 0;
+    ep->ahead = 1ull;
+    ep->status = (uint32_t *)ws;
+    ep->queue = &headers[0].queue;
+    PFN_cuTensorMapEncodeTiled_v12000 fn = engine_encode_fn();
     for (int i = 0; i < n; ++i) {
-        const exw_frame &f = d[i].src;
+        const EngineSpec &sp = specs[first + i];
+        const exw_frame &f = sp.src;
         const WsLayout &l = bl.l[i];
-        char *sb = b + bl.base[i];
-        BatchStream &st = bp->st[i];
+        char *sb = ws + bl.base[i];
+        EngineStream &st = ep->st[i];
         TileParams &p = st.p;
         p.color = f.color;
         p.depth = f.depth;
@@ -239,8 +117,8 @@ static bool build_params(BatchParams *bp, const exw_stream_desc *d, int n, int n
         p.L = 2;
         p.k0 = 1;
         for (int j = 0; j < nfrac; ++j) {
-            p.out_color[j] = d[i].out[j].color;
-            p.out_mask[j] = d[i].out[j].mask;
+            p.out_color[j] = sp.out[j].color;
+            p.out_mask[j] = sp.out[j].mask;
         }
         p.tile_bounds = (const float4 *)(sb + l.tile_bounds);
         p.tile_depth = (const float2 *)(sb + l.tile_depth);
@@ -248,7 +126,7 @@ static bool build_params(BatchParams *bp, const exw_stream_desc *d, int n, int n
         p.plans = (TilePlan *)(sb + l.plans);
         p.nbx = l.nbx;
         p.nby = l.nby;
-        p.fh = (FrameHeader *)(b + bl.headers) + i;
+        p.fh = headers + i;
         p.nodes = (float4 *)(sb + l.nodes);
         p.list = (uint32_t *)(sb + l.list);
         p.fillval = (float4 *)(sb + l.fillval);
@@ -256,67 +134,47 @@ static bool build_params(BatchParams *bp, const exw_stream_desc *d, int n, int n
         p.n5x = l.n5x;
         p.n5y = l.n5y;
         p.ncoarse = l.ncoarse;
-        p.status = bp->status;
+        p.status = ep->status;
         st.cdt = (int)f.cdt;
-        const int a = f.cdt == EXW_F16 ? 8 : 4;
+        const int a = f.cdt == EXW_F16 ? 8 : 4;  // TMA: rows and bases 16-byte aligned
         st.tma = sc.tma && fn != nullptr && (f.W % a) == 0 && ((uintptr_t)f.color & 15u) == 0 &&
                  ((uintptr_t)f.depth & 15u) == 0 && ((uintptr_t)f.mv & 15u) == 0;
         if (st.tma) {
             const int bx = f.cdt == EXW_F16 ? kWinXF16 : kWinXF32, by = f.cdt == EXW_F16 ? kWinYF16 : kWinYF32;
             const bool ok =
-                encode(fn, &bp->maps[i][0],
+                encode(fn, &ep->maps[i][0],
                        f.cdt == EXW_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, f.color,
                        f.W, f.H, 3, f.cdt == EXW_F16 ? 2 : 4, bx, by) &&
-                encode(fn, &bp->maps[i][1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, f.depth, f.W, f.H, 1, 4, bx, by) &&
-                encode(fn, &bp->maps[i][2], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, f.mv, f.W, f.H, 2, 4, bx, by);
+                encode(fn, &ep->maps[i][1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, f.depth, f.W, f.H, 1, 4, bx, by) &&
+                encode(fn, &ep->maps[i][2], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, f.mv, f.W, f.H, 2, 4, bx, by);
             if (!ok) st.tma = 0;
         }
-        st.nrx = ceil_div(f.W, 32);
-        st.nregions = st.nrx * ceil_div(f.H, 32);
+        st.nregions = ceil_div(f.W, 32) * ceil_div(f.H, 32);
         st.ntiles = l.n5x * l.n5y;
-        st.nplans = ceil_div(st.ntiles, kWarps);
-        st.nfix = fill ? (st.ntiles < 8 ? st.ntiles : 8) : 0;
+        st.nfix = fill ? (int)kFixupItems : 0;
     }
-    // diagonal queue: bounds of d, plans of d-1, tiles of d-2, fix-ups of d-3
+    // diagonal queue
+    const int lag = sc.lag < 1 ? 1 : sc.lag;
     int nseg = 0, total = 0;
-    for (int dd = 0; dd < n + 3; ++dd) {
+    for (int dd = 0; dd < n + 3 * lag; ++dd) {
         for (int stage = 0; stage < 4; ++stage) {
-            const int s = dd - stage;
+            const int s = dd - stage * lag;
             if (s < 0 || s >= n) continue;
-            const BatchStream &st = bp->st[s];
-            const int cnt = stage == 0 ? st.nregions : stage == 1 ? st.nplans : stage == 2 ? st.ntiles : st.nfix;
+            const EngineStream &st = ep->st[s];
+            if (stage < 2 && ((ep->ahead >> s) & 1ull)) continue;
+            const int cnt = stage == 0   ? ceil_div(st.nregions, kRegionsPerItem)
+                            : stage == 1 ? ceil_div(st.ntiles, kPlansPerItem)
+                            : stage == 2 ? st.ntiles
+                                         : st.nfix;
             if (cnt == 0) continue;
-            bp->seg[nseg] = BatchSeg{total, (uint16_t)s, (uint16_t)stage};
+            ep->seg[nseg] = EngineSeg{total, (uint16_t)s, (uint16_t)stage};
             ++nseg;
             total += cnt;
         }
     }
-    bp->nseg = nseg;
-    bp->total = total;
+    ep->nseg = nseg;
+    ep->total = total;
     return nseg > 0;
-}
-
-static cudaError_t launch_batched(const BatchParams &bp, const BatchLayout &bl, void *ws, int grid, cudaStream_t s) {
-    constexpr size_t kSmem = sizeof(TmaSmem<float, kWinXF32, kWinYF32>);
-    static_assert(sizeof(TmaSmem<float, kWinXF32, kWinYF32>) == sizeof(TmaSmem<__half, kWinXF16, kWinYF16>),
-                  "both window views have one size");
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(batched_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kSmem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(batched_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    cudaError_t e = launch_zero(ws, bl.headers + (size_t)bp.n * sizeof(FrameHeader), s);
-    if (e != cudaSuccess) return e;
-    timing_begin("exw_batched", s);
-    if (bp.fill) batched_kernel<true><<<grid, kThreads, kSmem, s>>>(bp);
-    else batched_kernel<false><<<grid, kThreads, kSmem, s>>>(bp);
-    count_launch();
-    timing_end("exw_batched", s);
-    return cudaGetLastError();
 }
 
 static int num_sms() {
@@ -325,6 +183,29 @@ static int num_sms() {
                                                   cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
+}
+
+// All streams, in launches of at most 48.  The headers of all streams are zeroed first (one launch).
+static cudaError_t run_all(EngineParams *ep, const EngineSpec *specs, int n, int nfrac, bool fill, char *ws,
+                           const EngineLayout &bl, const Schedule &sc, bool inject, cudaStream_t s) {
+    cudaError_t e = launch_zero(ws, bl.headers + (size_t)n * sizeof(FrameHeader), s);
+    const int sms = num_sms();
+    for (int first = 0; first < n && e == cudaSuccess; first += kMaxStreams) {
+        const int cnt = n - first < kMaxStreams ? n - first : kMaxStreams;
+        if (!build_params(ep, specs, first, cnt, nfrac, fill, ws, bl, sc, inject && first == 0))
+            return cudaErrorInvalidValue;
+        int tiles = 0;
+        for (int i = 0; i < cnt; ++i) tiles += ep->st[i].ntiles;
+        for (int i = 0; i < cnt && e == cudaSuccess; ++i) {
+            if (!((ep->ahead >> i) & 1ull)) continue;
+            const TileParams &p = ep->st[i].p;
+            e = launch_bounds(p.depth, p.mv, p.W, p.H, const_cast<float4 *>(p.tile_bounds),
+                              const_cast<float2 *>(p.tile_depth), const_cast<float4 *>(p.region_bounds), p.fh, s);
+            if (e == cudaSuccess) e = launch_plan(p, (exw_dtype)ep->st[i].cdt, s);
+        }
+        if (e == cudaSuccess) e = launch_engine(*ep, fill, tiles < sms ? tiles : sms, s);
+    }
+    return e;
 }
 
 }  // namespace exw
@@ -340,79 +221,28 @@ struct exw_tuner {
     std::map<std::string, Entry> table;
 };
 
-static std::string batch_key(const exw_stream_desc *d, int n, int nfrac, unsigned flags) {
+namespace exw {
+
+static std::string batch_key(const EngineSpec *d, int n, int nfrac, unsigned flags) {
     std::string k = std::to_string(n) + "/" + std::to_string(nfrac) + "/" + std::to_string(flags);
     for (int i = 0; i < n; ++i)
         k += ":" + std::to_string(d[i].src.W) + "x" + std::to_string(d[i].src.H) + "c" + std::to_string(d[i].src.cdt);
     return k;
 }
 
-extern "C" {
-
-exw_tuner *exw_tuner_create(void) { return new exw_tuner(); }
-
-void exw_tuner_destroy(exw_tuner *t) { delete t; }
-
-size_t exw_tuner_report(const exw_tuner *t, char *buf, size_t len) {
-    std::string r;
-    if (t != nullptr) {
-        exw_tuner *tt = const_cast<exw_tuner *>(t);
-        std::lock_guard<std::mutex> g(tt->mu);
-        for (auto &kv : tt->table) {
-            r += "streams " + kv.first.substr(0, kv.first.find(':')) + ": best ctas_per_sm=" +
-                 std::to_string(kv.second.best.ctas_per_sm) + " tma=" + std::to_string(kv.second.best.tma) + " (";
-            for (size_t i = 0; i < kv.second.trials.size(); ++i) {
-                char tmp[96];
-                std::snprintf(tmp, sizeof tmp, "%s%d/%d: %.3f ms", i ? ", " : "", kv.second.trials[i].first.ctas_per_sm,
-                              kv.second.trials[i].first.tma, kv.second.trials[i].second);
-                r += tmp;
-            }
-            r += ")\n";
-        }
-    }
-    if (buf != nullptr && len > 0) {
-        const size_t c = r.size() < len - 1 ? r.size() : len - 1;
-        std::memcpy(buf, r.data(), c);
-        buf[c] = '\0';
-    }
-    return r.size() + 1;
-}
-
-size_t exw_batched_workspace_bytes(const exw_stream_desc *d, int n, int nfrac) {
-    if (d == nullptr || n < 1 || n > kMaxBatch || nfrac < 1 || nfrac > EXW_MAX_FRAC) return 0;
-    for (int i = 0; i < n; ++i)
-        if (d[i].src.W < 1 || d[i].src.H < 1 || d[i].src.W > 16384 || d[i].src.H > 16384) return 0;
-    return batch_layout(d, n, nfrac).total;
-}
-
-exw_status exw_extrapolate_batched(const exw_stream_desc *d, int n, int nfrac, unsigned flags, void *ws,
-                                   size_t ws_bytes, exw_tuner *t, exw_stream_t stream) {
-    if (d == nullptr || n < 1 || nfrac < 1 || nfrac > EXW_MAX_FRAC || (flags & ~(EXW_FLAG_NO_FILL | EXW_FLAG_NO_TMA)))
-        return EXW_ERR_INVALID_ARG;
-    if (n > kMaxBatch) return EXW_ERR_UNSUPPORTED;
-    for (int i = 0; i < n; ++i) {
-        const exw_frame &f = d[i].src;
-        const uintptr_t cs = f.cdt == EXW_F16 ? 2 : 4;
-        if (f.W < 1 || f.H < 1 || f.W > 16384 || f.H > 16384 || (f.cdt != EXW_F32 && f.cdt != EXW_F16) ||
-            f.color == nullptr || f.depth == nullptr || f.mv == nullptr || ((uintptr_t)f.color & (cs - 1)) ||
-            ((uintptr_t)f.depth & 3u) || ((uintptr_t)f.mv & 3u))
-            return EXW_ERR_INVALID_ARG;
-        for (int j = 0; j < nfrac; ++j)
-            if (d[i].out[j].color == nullptr || d[i].out[j].mask == nullptr ||
-                ((uintptr_t)d[i].out[j].color & (cs - 1)))
-                return EXW_ERR_INVALID_ARG;
-    }
-    const BatchLayout bl = batch_layout(d, n, nfrac);
+exw_status engine_run(const EngineSpec *specs, int n, int nfrac, unsigned flags, void *ws, size_t ws_bytes,
+                      exw_tuner *t, bool shared_size, cudaStream_t s) {
+    const EngineLayout bl = engine_layout(specs, n, nfrac, shared_size);
     if (ws == nullptr || ((uintptr_t)ws & 15u) || ws_bytes < bl.total) return EXW_ERR_WORKSPACE;
     if (cudaGetLastError() != cudaSuccess) return EXW_ERR_CUDA;
-    cudaStream_t s = (cudaStream_t)stream;
     const bool fill = (flags & EXW_FLAG_NO_FILL) == 0;
     const char *fault = std::getenv("EXW_FAULT");
     const bool inject = fault != nullptr && std::strcmp(fault, "timeout") == 0;
-    Schedule sc{2, (flags & EXW_FLAG_NO_TMA) ? 0 : 1};
-    static thread_local BatchParams bp;  // 32 KB: kept off the stack
+    Schedule sc{(flags & EXW_FLAG_NO_TMA) ? 0 : 1, 1};
+    static thread_local EngineParams ep;  // 32 KB: kept off the stack
+    char *wsb = (char *)ws;
     if (t != nullptr && !inject) {
-        const std::string key = batch_key(d, n, nfrac, flags);
+        const std::string key = batch_key(specs, n, nfrac, flags);
         std::unique_lock<std::mutex> g(t->mu);
         auto it = t->table.find(key);
         if (it != t->table.end()) {
@@ -420,28 +250,30 @@ exw_status exw_extrapolate_batched(const exw_stream_desc *d, int n, int nfrac, u
         } else {
             cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
             if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
-                // Time each schedule on this batch (one warm-up, then the best of two runs) and keep the fastest.
+                // Time each schedule on these streams (one warm-up, then the best of two runs); keep the fastest.
                 exw_tuner::Entry ent;
                 float best = 1e30f;
                 cudaEvent_t e0, e1;
-                if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return EXW_ERR_CUDA;
-                for (int cps = 1; cps <= 2; ++cps) {
-                    for (int tma = (flags & EXW_FLAG_NO_TMA) ? 0 : 1; tma >= 0; --tma) {
-                        const Schedule c{cps, tma};
-                        build_params(&bp, d, n, nfrac, fill, ws, bl, c, false);
+                if (cudaEventCreate(&e0) != cudaSuccess) return EXW_ERR_CUDA;
+                if (cudaEventCreate(&e1) != cudaSuccess) {
+                    cudaEventDestroy(e0);
+                    return EXW_ERR_CUDA;
+                }
+                exw_status st = EXW_OK;
+                for (int tma = (flags & EXW_FLAG_NO_TMA) ? 0 : 1; tma >= 0 && st == EXW_OK; --tma) {
+                    for (int lag = 1; lag <= 2 && st == EXW_OK; ++lag) {
+                        const Schedule c{tma, lag};
                         float ms = 1e30f;
                         for (int r = 0; r < 3; ++r) {
                             cudaEventRecord(e0, s);
-                            if (launch_batched(bp, bl, ws, c.ctas_per_sm * num_sms(), s) != cudaSuccess) {
-                                cudaEventDestroy(e0);
-                                cudaEventDestroy(e1);
-                                return EXW_ERR_CUDA;
+                            if (run_all(&ep, specs, n, nfrac, fill, wsb, bl, c, false, s) != cudaSuccess) {
+                                st = EXW_ERR_CUDA;
+                                break;
                             }
                             cudaEventRecord(e1, s);
                             if (cudaEventSynchronize(e1) != cudaSuccess) {
-                                cudaEventDestroy(e0);
-                                cudaEventDestroy(e1);
-                                return EXW_ERR_CUDA;
+                                st = EXW_ERR_CUDA;
+                                break;
                             }
                             float m = 0.f;
                             cudaEventElapsedTime(&m, e0, e1);
@@ -456,13 +288,86 @@ exw_status exw_extrapolate_batched(const exw_stream_desc *d, int n, int nfrac, u
                 }
                 cudaEventDestroy(e0);
                 cudaEventDestroy(e1);
+                if (st != EXW_OK) return st;
                 t->table[key] = ent;
                 sc = ent.best;
             }
         }
     }
-    if (!build_params(&bp, d, n, nfrac, fill, ws, bl, sc, inject)) return EXW_ERR_INVALID_ARG;
-    return launch_batched(bp, bl, ws, sc.ctas_per_sm * num_sms(), s) == cudaSuccess ? EXW_OK : EXW_ERR_CUDA;
+    return run_all(&ep, specs, n, nfrac, fill, wsb, bl, sc, inject, s) == cudaSuccess ? EXW_OK : EXW_ERR_CUDA;
+}
+
+}  // namespace exw
+
+extern "C" {
+
+exw_tuner *exw_tuner_create(void) { return new exw_tuner(); }
+
+void exw_tuner_destroy(exw_tuner *t) { delete t; }
+
+size_t exw_tuner_report(const exw_tuner *t, char *buf, size_t len) {
+    std::string r;
+    if (t != nullptr) {
+        exw_tuner *tt = const_cast<exw_tuner *>(t);
+        std::lock_guard<std::mutex> g(tt->mu);
+        for (auto &kv : tt->table) {
+            r += "streams " + kv.first.substr(0, kv.first.find(':')) + ": best tma=" +
+                 std::to_string(kv.second.best.tma) + " lag=" + std::to_string(kv.second.best.lag) + " (";
+            for (size_t i = 0; i < kv.second.trials.size(); ++i) {
+                char tmp[96];
+                std::snprintf(tmp, sizeof tmp, "%stma %d lag %d: %.3f ms", i ? ", " : "",
+                              kv.second.trials[i].first.tma, kv.second.trials[i].first.lag,
+                              kv.second.trials[i].second);
+                r += tmp;
+            }
+            r += ")\n";
+        }
+    }
+    if (buf != nullptr && len > 0) {
+        const size_t c = r.size() < len - 1 ? r.size() : len - 1;
+        std::memcpy(buf, r.data(), c);
+        buf[c] = '\0';
+    }
+    return r.size() + 1;
+}
+
+static void specs_from(const exw_stream_desc *d, int n, std::vector<EngineSpec> &out) {
+    out.resize((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        out[i].src = d[i].src;
+        for (int j = 0; j < EXW_MAX_FRAC; ++j) out[i].out[j] = d[i].out[j];
+    }
+}
+
+size_t exw_batched_workspace_bytes(const exw_stream_desc *d, int n, int nfrac) {
+    if (d == nullptr || n < 1 || n > kMaxStreams || nfrac < 1 || nfrac > EXW_MAX_FRAC) return 0;
+    for (int i = 0; i < n; ++i)
+        if (d[i].src.W < 1 || d[i].src.H < 1 || d[i].src.W > 16384 || d[i].src.H > 16384) return 0;
+    std::vector<EngineSpec> specs;
+    specs_from(d, n, specs);
+    return engine_workspace_bytes(specs.data(), n, nfrac, false);
+}
+
+exw_status exw_extrapolate_batched(const exw_stream_desc *d, int n, int nfrac, unsigned flags, void *ws,
+                                   size_t ws_bytes, exw_tuner *t, exw_stream_t stream) {
+    if (d == nullptr || n < 1 || nfrac < 1 || nfrac > EXW_MAX_FRAC || (flags & ~(EXW_FLAG_NO_FILL | EXW_FLAG_NO_TMA)))
+        return EXW_ERR_INVALID_ARG;
+    if (n > kMaxStreams) return EXW_ERR_UNSUPPORTED;
+    for (int i = 0; i < n; ++i) {
+        const exw_frame &f = d[i].src;
+        const uintptr_t cs = f.cdt == EXW_F16 ? 2 : 4;
+        if (f.W < 1 || f.H < 1 || f.W > 16384 || f.H > 16384 || (f.cdt != EXW_F32 && f.cdt != EXW_F16) ||
+            f.color == nullptr || f.depth == nullptr || f.mv == nullptr || ((uintptr_t)f.color & (cs - 1)) ||
+            ((uintptr_t)f.depth & 3u) || ((uintptr_t)f.mv & 3u))
+            return EXW_ERR_INVALID_ARG;
+        for (int j = 0; j < nfrac; ++j)
+            if (d[i].out[j].color == nullptr || d[i].out[j].mask == nullptr ||
+                ((uintptr_t)d[i].out[j].color & (cs - 1)))
+                return EXW_ERR_INVALID_ARG;
+    }
+    std::vector<EngineSpec> specs;
+    specs_from(d, n, specs);
+    return engine_run(specs.data(), n, nfrac, flags, ws, ws_bytes, t, false, (cudaStream_t)stream);
 }
 
 }  // extern "C"

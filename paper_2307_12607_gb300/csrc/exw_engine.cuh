@@ -1,25 +1,29 @@
-// exw_engine.cuh -- the fused forward pass (stages (b) and (c) for P_1..P_3, Sec. IV-B) as a warp-specialised
-// persistent kernel: one CTA per SM, 25 warps.
+// exw_engine.cuh -- the forward pass (stages (a0), (a), (b), (c) for P_1..P_3, Sec. IV-B) of any number of frames
+// or streams as ONE warp-specialised persistent kernel: one CTA per SM, 25 warps.
 //
-//   producer warp:   takes 32 x 32 target tiles from the frame's queue, reads each tile's plan and stages the
-//                    tile's source window (depth, motion, colour) into one of two shared-memory buffers with three
-//                    TMA loads (cp.async.bulk.tensor, mbarrier completion), one tile ahead of the consumers;
-//   3 x 8 consumer warps: group g computes fraction k0 + g of the tile -- each thread a 2 x 2 pixel block --
-//                    then fills and stores it.  A consumer warp releases the buffer through a second mbarrier.
+// Work items of all streams (a stream = one source frame with its outputs) sit in one queue, laid out diagonally --
+// motion-bounds regions of stream d, tile plans of stream d-1, target tiles of stream d-2, fix-ups of stream d-3
+// -- so an item's dependencies (the previous stage of its own stream) come earlier in the queue.
 //
-// Tiles whose candidate sources all carry one motion (plan mode 0) are pure translations: the winner of target q
-// is the source q - o_k when that pixel is valid and carries the tile's motion, so no splat is needed.  The
-// consumers first rewrite the staged depth plane in place into one word per source pixel -- its depth bits when
-// the pixel is valid with the tile's motion, the bits with the sign set when it is valid with another motion, all
-// ones when its depth is not valid -- and every fraction then reads its winners, crack neighbours and tap depths
-// off that plane with whole-pixel offsets, with bilinear weights that are constant over the tile.  Other tiles
-// splat their candidate sources into per-fraction region keys (from the window, or from global memory when the
-// landing rectangle is wider than a window) and gather through the keys.
+//   producer warp:   takes items in queue order, waits (bounded) until the item's stage may start, and hands the
+//                    item to the consumers in one of two shared-memory slots.  For a target tile it reads the
+//                    tile's plan, computes the per-fraction constants of uniform tiles and stages the tile's source
+//                    window (depth, motion, colour) into the slot's buffer with TMA loads (cp.async.bulk.tensor,
+//                    mbarrier completion), one item ahead of the consumers.
+//   3 x 8 consumer warps: a bounds item gives each group one 32 x 32 source region, a plan item each warp one
+//                    target tile, a fix-up item all of them a slice; for a target tile, group g computes fraction
+//                    k0 + g -- each thread a 2 x 2 pixel block -- then fills and stores it.  Every consumer warp
+//                    releases the slot through a second mbarrier.
 //
-// Every result is bit-identical to the per-tile passes of exw_tile.cuh (same arithmetic in the same order).
+// Tiles whose candidate sources all carry one motion (plan modes 0 and 5) are pure translations: the winner of
+// target q is the source q - o_k when that pixel is valid and carries the tile's motion, so no splat is needed.
+// Other tiles splat their candidate sources into per-fraction region keys (from the window, or from global memory
+// when the landing rectangle is wider than a window) and gather through the keys.  Every result is bit-identical
+// to the per-tile passes of exw_tile.cuh (same arithmetic in the same order).
 #pragma once
 
 #include "exw_items.cuh"
+#include "exw_tma.cuh"
 
 namespace exw {
 
@@ -28,7 +32,36 @@ constexpr int kConsumerThreads = kMaxFrac * kGroupThreads;  // 768
 constexpr int kConsumerWarps = kConsumerThreads / 32;       // 24
 constexpr int kEngineThreads = kConsumerThreads + 32;       // + the producer warp
 constexpr int kBarConsumers = 1;                            // named barriers: 1 all consumers, 2 + g group g
-constexpr int kModeEnd = -1;                                // plan slot mode: no more tiles
+constexpr int kMaxStreams = 48;                             // streams per launch (kernel-parameter space)
+constexpr int kRegionsPerItem = 2 * kMaxFrac;               // a bounds item: one region per half group (4 warps)
+constexpr int kPlansPerItem = kConsumerWarps;               // a plan item: one tile per consumer warp
+constexpr uint32_t kFixupItems = 8u;                        // fix-up items per stream (with the fill)
+constexpr uint32_t kStageWaitLimit = 1u << 22;              // iterations (>= 64 ns each) before a wait gives up
+constexpr uint32_t kInjectedWaitLimit = 20000u;             // the injected fault gives up after a few ms
+
+// Slot kinds.
+constexpr int kSlotEnd = 0, kSlotBounds = 1, kSlotPlans = 2, kSlotTile = 3, kSlotFixup = 4;
+
+// Per stream, in the kernel parameters.
+struct EngineStream {
+    TileParams p;
+    int cdt;     // EXW_F32 / EXW_F16
+    int tma;     // stage this stream's tiles with TMA windows (else every tile reads global memory)
+    int nregions, ntiles, nfix;
+};
+struct EngineSeg {
+    int start;         // first queue index of the segment
+    uint16_t stream;
+    uint16_t stage;    // 0 bounds, 1 plans, 2 tiles, 3 fix-up
+};
+struct EngineParams {
+    int n, nseg, total, inject;
+    uint64_t ahead;  // streams whose bounds and plans were computed before the launch (bit s = stream s)
+    uint32_t *queue, *status;
+    EngineStream st[kMaxStreams];
+    EngineSeg seg[4 * kMaxStreams];
+    CUtensorMap maps[kMaxStreams][3];  // colour, depth, motion
+};
 
 // Per-fraction constants of a uniform tile (computed by the producer).
 struct UniformFrac {
@@ -39,26 +72,44 @@ struct UniformFrac {
 };
 constexpr uint32_t kTapX = 1u, kTapY = 2u, kMirX = 4u, kMirY = 8u, kInterior = 16u;
 
+// The scalars of a stream the per-pixel code needs, held in registers for a whole tile (the slot's parameters sit
+// in shared memory, and every barrier would otherwise reload them).
+struct FrameDims {
+    int W, H, L, k0, nfrac;
+};
+__device__ __forceinline__ FrameDims dims_of(const TileParams &p) { return FrameDims{p.W, p.H, p.L, p.k0, p.nfrac}; }
+
 // What the producer hands the consumers with each buffer.
 struct TileSlot {
-    TilePlan plan;
-    int tile, X0, Y0;
-    Rect N;                   // mode 0: the source rectangle the fractions read
-    UniformFrac u[kMaxFrac];  // mode 0
+    TileParams p;             // the item's stream
+    int kind, stream, index, cdt;
+    TilePlan plan;            // tile: its plan (mode 3 for every tile of a stream without TMA windows)
+    int X0, Y0;
+    Rect N;                   // modes 0, 5: the source rectangle the fractions read
+    UniformFrac u[kMaxFrac];  // modes 0, 5
+};
+
+constexpr int kWindowBytes = 64512;  // both window shapes (56 x 48 FP32, 64 x 56 FP16) hold 64,512 bytes
+static_assert(sizeof(Window<float, kWinXF32, kWinYF32>) == kWindowBytes &&
+                  sizeof(Window<__half, kWinXF16, kWinYF16>) == kWindowBytes,
+              "one buffer size for both colour types");
+
+struct EngineSmem {
+    alignas(128) unsigned char win[2][kWindowBytes];  // TMA destinations, double-buffered
+    uint64_t key[kMaxFrac][kRegionN];                // region keys per fraction (modes 1-3)
+    float4 l2[kMaxFrac][2][64];                      // pyramid level 2 (8 x 8 nodes) per group, by tile parity
+    float4 bpart[kMaxFrac][64];                      // per group: partial bounds of a region
+    TileSlot slot[2];                                // the item in each buffer
+    uint32_t cand[kConsumerThreads];                 // candidate 8 x 8 source tiles of the global-memory splat
+    uint32_t ncand;
+    int abort;                                       // a bounded wait ran out: every warp leaves
+    uint64_t full[2], empty[2];
 };
 
 template <typename CT, int WX, int WY>
-struct EngineSmem {
-    Window<CT, WX, WY> win[2];            // TMA destinations, double-buffered
-    uint64_t key[kMaxFrac][kRegionN];     // region keys per fraction (modes 1-3)
-    float4 l2[kMaxFrac][2][64];           // pyramid level 2 (8 x 8 nodes) per group, by tile parity
-    TileSlot slot[2];                     // the tile in each buffer
-    uint32_t cand[kConsumerThreads];      // candidate 8 x 8 source tiles of the global-memory splat
-    uint32_t ncand;
-    int last[kMaxFrac];                   // group g finished the frame's last (tile, fraction)
-    int abort;                            // a bounded wait ran out: every warp leaves
-    uint64_t full[2], empty[2];
-};
+__device__ __forceinline__ Window<CT, WX, WY> &window(EngineSmem &s, int b) {
+    return *reinterpret_cast<Window<CT, WX, WY> *>(s.win[b]);
+}
 
 // ------------------------------------------------------------------------------------------------------------
 // Barriers
@@ -128,81 +179,176 @@ __device__ __forceinline__ void uniform_frac(UniformFrac &u, const TileParams &p
     }
 }
 
-template <typename CT, int WX, int WY>
-__device__ void engine_producer(EngineSmem<CT, WX, WY> &s, const TileParams &p, const CUtensorMap *tcol,
-                                const CUtensorMap *tdep, const CUtensorMap *tmv) {
-    constexpr uint32_t kBytes = WX * WY * (4 + 8 + 3 * (uint32_t)sizeof(CT));
-    constexpr uint32_t kColourBytes = WX * WY * 3 * (uint32_t)sizeof(CT);
-    constexpr int kWords = (int)(sizeof(TilePlan) / 4);
-    const int lane = threadIdx.x & 31;
-    const int ntiles = p.n5x * p.n5y;
-    // Two tiles of look-ahead: the queue position of tile i + 2 and the plan of tile i + 1 are requested while
-    // tile i is staged.
-    int qnext = 0;
-    if (lane == 0) {
-        qnext = (int)atomicAdd(&p.fh->queue, 1u);
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Lane 0 waits until *counter >= target; false when the limit ran out, the workspace status reports an error or
+// the CTA aborts.
+__device__ __forceinline__ bool stage_wait(const uint32_t *counter, uint32_t target, uint32_t limit,
+                                           const uint32_t *status, const volatile int *abort) {
+    for (uint32_t i = 0; i < limit; ++i) {
+        if (ld_acquire(counter) >= target) return true;
+        if (*(const volatile uint32_t *)status != 0u || *abort) return false;
+        __nanosleep(i < 64 ? 32 : 256);
     }
-    int tile = __shfl_sync(0xFFFFFFFFu, qnext, 0);
-    if (lane == 0 && tile < ntiles) qnext = (int)atomicAdd(&p.fh->queue, 1u);
-    int word = (tile < ntiles && lane < kWords) ? __ldcg(reinterpret_cast<const int *>(p.plans + tile) + lane) : 0;
+    return false;
+}
+
+struct QueueItem {
+    int item, stream, stage, local;  // item >= total: no more items
+};
+
+// A producer's items increase, so its segment index only moves forward: seg is the last segment found.
+__device__ __forceinline__ QueueItem decode(const EngineParams &ep, int item, int &seg) {
+    QueueItem q{item, 0, 0, 0};
+    if (item < ep.total) {
+        while (seg + 1 < ep.nseg && ep.seg[seg + 1].start <= item) ++seg;
+        q.stream = ep.seg[seg].stream;
+        q.stage = ep.seg[seg].stage;
+        q.local = item - ep.seg[seg].start;
+    }
+    return q;
+}
+
+__device__ inline void engine_producer(EngineSmem &s, const EngineParams &ep) {
+    constexpr int kWords = (int)(sizeof(TilePlan) / 4), kParamWords = (int)(sizeof(TileParams) / 4);
+    static_assert(sizeof(TileParams) % 4 == 0 && kParamWords <= 64, "two words per lane");
+    const int lane = threadIdx.x & 31;
+    // streams whose previous stage is known complete (the injected fault makes stream 0's tiles wait)
+    uint64_t planned = ep.ahead & (ep.inject ? ~1ull : ~0ull), bounded = ep.ahead, coarsed = 0ull;
+    // Two items of look-ahead: the queue position of item i + 2 and, when its stream's plans are known complete,
+    // the plan of item i + 1 are requested while item i is handed over.
+    int qa = 0, qb = 0;
+    if (lane == 0) {
+        qa = (int)atomicAdd(ep.queue, 1u);
+        qb = qa < ep.total ? (int)atomicAdd(ep.queue, 1u) : ep.total;
+    }
+    int seg = 0;
+    QueueItem cur = decode(ep, __shfl_sync(0xFFFFFFFFu, qa, 0), seg);
+    int word = 0;
+    bool have_word = false;
+    int copied0 = -1, copied1 = -1;  // stream whose parameters slot 0 / slot 1 holds
     for (uint32_t i = 0;; ++i) {
         const int b = (int)(i & 1u);
-        const int tnext = tile < ntiles ? __shfl_sync(0xFFFFFFFFu, qnext, 0) : ntiles;
-        if (lane == 0 && tnext < ntiles) qnext = (int)atomicAdd(&p.fh->queue, 1u);
-        const int wnext =
-            (tnext < ntiles && lane < kWords) ? __ldcg(reinterpret_cast<const int *>(p.plans + tnext) + lane) : 0;
+        const QueueItem nxt = decode(ep, cur.item < ep.total ? __shfl_sync(0xFFFFFFFFu, qb, 0) : ep.total, seg);
+        if (lane == 0 && nxt.item < ep.total) qb = (int)atomicAdd(ep.queue, 1u);
+        int nword = 0;
+        bool nhave = false;
+        if (nxt.item < ep.total && nxt.stage == 2 && (planned & (1ull << nxt.stream))) {
+            nword = lane < kWords ? __ldcg(reinterpret_cast<const int *>(ep.st[nxt.stream].p.plans + nxt.local) + lane)
+                                  : 0;
+            nhave = true;
+        }
+        const int item = cur.item, stream = cur.stream, stage = cur.stage, local = cur.local;
+        const EngineStream &st = ep.st[stream];
+        const TileParams &p = st.p;
         bool ok = true;
-        if (i >= 2) {  // the consumers' release of this buffer's previous use
+        // the item's stage may start once the previous stage of its stream is complete
+        if (item < ep.total && stage > 0) {
+            const uint64_t bit = 1ull << stream;
+            const uint64_t known = stage == 1 ? bounded : stage == 2 ? planned : coarsed;
+            if (!(known & bit)) {
+                const bool injected = ep.inject && stream == 0 && stage == 2;
+                // fix-ups: item 0 (the coarse pass) waits for every (tile, fraction) count, the others for it
+                const bool first_fix = stage == 3 && local == 0;
+                const uint32_t *counter = stage == 1 ? &p.fh->bdone
+                                          : stage == 2 ? &p.fh->pdone
+                                          : first_fix ? &p.fh->done : &p.fh->cready;
+                const uint32_t target = stage == 1   ? (uint32_t)st.nregions
+                                        : stage == 2 ? (uint32_t)st.ntiles + (injected ? 1u : 0u)
+                                        : first_fix  ? (uint32_t)st.ntiles * (uint32_t)p.nfrac : 1u;
+                if (lane == 0)
+                    ok = stage_wait(counter, target, injected ? kInjectedWaitLimit : kStageWaitLimit, ep.status,
+                                    &s.abort);
+                ok = __shfl_sync(0xFFFFFFFFu, (int)ok, 0) != 0;
+                if (ok && !first_fix) {
+                    if (stage == 1) bounded |= bit;
+                    else if (stage == 2) planned |= bit;
+                    else coarsed |= bit;
+                }
+            }
+        }
+        if (ok && i >= 2) {  // the consumers' release of this buffer's previous use
             if (lane == 0) ok = mbar_wait_or_abort(&s.empty[b], ((i >> 1) - 1u) & 1u, &s.abort);
             ok = __shfl_sync(0xFFFFFFFFu, (int)ok, 0) != 0;
         }
         if (!ok) {
             if (lane == 0) {
-                atomicExch(p.status, (uint32_t)EXW_ERR_TIMEOUT);
+                atomicCAS(ep.status, 0u, (uint32_t)EXW_ERR_TIMEOUT);
                 *(volatile int *)&s.abort = 1;
             }
             return;
         }
         TileSlot &sl = s.slot[b];
-        if (tile >= ntiles) {
+        if (item >= ep.total) {
             if (lane == 0) {
-                sl.plan.mode = kModeEnd;
+                sl.kind = kSlotEnd;
                 mbar_arrive(&s.full[b]);
             }
             return;
         }
-        if (lane < kWords) reinterpret_cast<int *>(&sl.plan)[lane] = word;
-        const int mode = __shfl_sync(0xFFFFFFFFu, word, 0);
-        const int wx0 = __shfl_sync(0xFFFFFFFFu, word, 1), wy0 = __shfl_sync(0xFFFFFFFFu, word, 2);
-        const int X0 = (tile % p.n5x) * kFillTile, Y0 = (tile / p.n5x) * kFillTile;
-        if (mode == 0 || mode == 5) {
-            const uint32_t umx = (uint32_t)__shfl_sync(0xFFFFFFFFu, word, 16);
-            const uint32_t umy = (uint32_t)__shfl_sync(0xFFFFFFFFu, word, 17);
-            if (lane < 8 * p.nfrac) uniform_frac(sl.u[lane >> 3], p, umx, umy, lane >> 3, X0 - 1, Y0 - 1, lane & 7);
-            if (lane == 0) sl.N = uniform_sources(p, umx, umy, X0 - 1, Y0 - 1);
+        if ((b ? copied1 : copied0) != stream) {  // the slot's parameters are another stream's
+            const int *pw = reinterpret_cast<const int *>(&p);
+            int *sw = reinterpret_cast<int *>(&sl.p);
+            sw[lane] = pw[lane];
+            if (lane + 32 < kParamWords) sw[lane + 32] = pw[lane + 32];
+            if (b) copied1 = stream;
+            else copied0 = stream;
+        }
+        const int kind = stage == 0 ? kSlotBounds : stage == 1 ? kSlotPlans : stage == 2 ? kSlotTile : kSlotFixup;
+        int mode = -1, wx0 = 0, wy0 = 0;
+        if (kind == kSlotTile) {
+            if (!have_word) word = lane < kWords ? __ldcg(reinterpret_cast<const int *>(p.plans + local) + lane) : 0;
+            if (lane < kWords) reinterpret_cast<int *>(&sl.plan)[lane] = word;
+            mode = __shfl_sync(0xFFFFFFFFu, word, 0);
+            wx0 = __shfl_sync(0xFFFFFFFFu, word, 1);
+            wy0 = __shfl_sync(0xFFFFFFFFu, word, 2);
+            const int X0 = (local % p.n5x) * kFillTile, Y0 = (local / p.n5x) * kFillTile;
+            if (!st.tma && mode != 4) mode = 3;  // no window: every tile reads global memory
+            if (mode == 0 || mode == 5) {
+                const uint32_t umx = (uint32_t)__shfl_sync(0xFFFFFFFFu, word, 16);
+                const uint32_t umy = (uint32_t)__shfl_sync(0xFFFFFFFFu, word, 17);
+                if (lane < 8 * p.nfrac) uniform_frac(sl.u[lane >> 3], p, umx, umy, lane >> 3, X0 - 1, Y0 - 1, lane & 7);
+                if (lane == 0) sl.N = uniform_sources(p, umx, umy, X0 - 1, Y0 - 1);
+            }
+            if (lane == 0) {
+                sl.plan.mode = mode;
+                sl.X0 = X0;
+                sl.Y0 = Y0;
+            }
         }
         __syncwarp();
         if (lane == 0) {
-            sl.tile = tile;
-            sl.X0 = X0;
-            sl.Y0 = Y0;
-            atomicAdd(&p.fh->nmode[mode], 1u);
-            if (mode == 5) {  // smooth: only the colour is read
+            sl.kind = kind;
+            sl.stream = stream;
+            sl.index = local;
+            sl.cdt = st.cdt;
+            if (kind == kSlotTile) atomicAdd(&p.fh->nmode[mode], 1u);
+            const CUtensorMap *m = ep.maps[stream];
+            unsigned char *wb = s.win[b];
+            // a window holds npx pixels: depth (4 B), motion (8 B), colour (3 c B) planes in this order
+            const int npx = st.cdt == EXW_F16 ? kWinXF16 * kWinYF16 : kWinXF32 * kWinYF32;
+            const uint32_t cbytes = (uint32_t)npx * 3u * (st.cdt == EXW_F16 ? 2u : 4u);
+            if (kind == kSlotTile && mode == 5) {  // smooth: only the colour is read
                 fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&s.full[b], kColourBytes);
-                tma_load_3d(&s.win[b].col[0][0], tcol, wx0, wy0, 0, &s.full[b]);
-            } else if (mode == 0 || mode == 1) {
+                mbar_arrive_expect_tx(&s.full[b], cbytes);
+                tma_load_3d(wb + 12 * npx, &m[0], wx0, wy0, 0, &s.full[b]);
+            } else if (kind == kSlotTile && (mode == 0 || mode == 1)) {
                 fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&s.full[b], kBytes);
-                tma_load_2d(s.win[b].depth, tdep, wx0, wy0, &s.full[b]);
-                tma_load_3d(&s.win[b].mv[0][0], tmv, wx0, wy0, 0, &s.full[b]);
-                tma_load_3d(&s.win[b].col[0][0], tcol, wx0, wy0, 0, &s.full[b]);
+                mbar_arrive_expect_tx(&s.full[b], (uint32_t)kWindowBytes);
+                tma_load_2d(wb, &m[1], wx0, wy0, &s.full[b]);
+                tma_load_3d(wb + 4 * npx, &m[2], wx0, wy0, 0, &s.full[b]);
+                tma_load_3d(wb + 12 * npx, &m[0], wx0, wy0, 0, &s.full[b]);
             } else {
                 mbar_arrive(&s.full[b]);
             }
         }
-        tile = tnext;
-        word = wnext;
+        cur = nxt;
+        word = nword;
+        have_word = nhave;
     }
 }
 
@@ -260,7 +406,7 @@ __device__ __forceinline__ void build_source_words(Window<CT, WX, WY> &w, int wx
 // likewise), pixels at j, i in {1, 2}.  EDGE adds the frame checks of tiles near the border (and keeps every
 // shared-memory index inside the window).  Results c[], m[] are in true pixel order (dy * 2 + dx).
 template <typename CT, int WX, int WY, bool EDGE, bool MX, bool MY>
-__device__ __forceinline__ void uniform_block(const Window<CT, WX, WY> &w, int wx0, int wy0, const TileParams &p,
+__device__ __forceinline__ void uniform_block(const Window<CT, WX, WY> &w, int wx0, int wy0, const FrameDims &p,
                                               const UniformFrac &u, int TX, int TY, float4 c[4], uint8_t m[4]) {
     const int SX = TX - u.ox, SY = TY - u.oy;
     int cidx[4], ridx[4];
@@ -353,7 +499,7 @@ __device__ __forceinline__ void uniform_block(const Window<CT, WX, WY> &w, int w
 }
 
 template <typename CT, int WX, int WY, bool EDGE>
-__device__ __forceinline__ void uniform_block_any(const Window<CT, WX, WY> &w, int wx0, int wy0, const TileParams &p,
+__device__ __forceinline__ void uniform_block_any(const Window<CT, WX, WY> &w, int wx0, int wy0, const FrameDims &p,
                                                   const UniformFrac &u, int TX, int TY, float4 c[4], uint8_t m[4]) {
     if (u.flags & kMirX) {
         if (u.flags & kMirY) uniform_block<CT, WX, WY, EDGE, true, true>(w, wx0, wy0, p, u, TX, TY, c, m);
@@ -367,7 +513,7 @@ __device__ __forceinline__ void uniform_block_any(const Window<CT, WX, WY> &w, i
 // ------------------------------------------------------------------------------------------------------------
 // Tiles through splat keys (modes 1-3)
 // ------------------------------------------------------------------------------------------------------------
-__device__ __forceinline__ void engine_splat_pixel(uint64_t (*key)[kRegionN], const TileParams &p, int x, int y,
+__device__ __forceinline__ void engine_splat_pixel(uint64_t (*key)[kRegionN], const FrameDims &p, int x, int y,
                                                    uint32_t db, uint32_t ux, uint32_t uy, uint32_t fm, int RX0,
                                                    int RY0) {
     if (!depth_ok(db) || !finite_bits(ux) || !finite_bits(uy)) return;
@@ -401,7 +547,7 @@ __device__ __forceinline__ Rect plan_union(const TilePlan &pl, int nfrac) {
 
 // Splat every window pixel of rectangle U for all fractions (all consumer threads).
 template <typename CT, int WX, int WY>
-__device__ __forceinline__ void engine_splat_window(uint64_t (*key)[kRegionN], const TileParams &p,
+__device__ __forceinline__ void engine_splat_window(uint64_t (*key)[kRegionN], const FrameDims &p,
                                                     const WinAcc<CT, WX, WY> &a, Rect U, int RX0, int RY0, int tid) {
     const int lane = tid & 31, wid = tid >> 5;
     const uint32_t fm = (1u << p.nfrac) - 1u;
@@ -414,8 +560,7 @@ __device__ __forceinline__ void engine_splat_window(uint64_t (*key)[kRegionN], c
 }
 
 // Splat from global memory: the 8 x 8 source tiles whose bounds reach R, 64 threads per tile (all consumers).
-template <typename CT, int WX, int WY>
-__device__ inline void engine_splat_global(EngineSmem<CT, WX, WY> &s, const TileParams &p, int RX0, int RY0,
+__device__ inline void engine_splat_global(EngineSmem &s, const TileParams &p, const FrameDims &d, int RX0, int RY0,
                                            int tid) {
     int bx0, bx1, by0, by1;
     if (!frame_window(p, RX0, RY0, bx0, bx1, by0, by1)) return;
@@ -454,7 +599,7 @@ __device__ inline void engine_splat_global(EngineSmem<CT, WX, WY> &s, const Tile
                 const int x = 8 * bx + (tid & 7), y = 8 * by + ((tid >> 3) & 7);
                 if (x < p.W && y < p.H) {
                     const size_t i = (size_t)y * p.W + x;
-                    engine_splat_pixel(s.key, p, x, y, __float_as_uint(__ldg(p.depth + i)),
+                    engine_splat_pixel(s.key, d, x, y, __float_as_uint(__ldg(p.depth + i)),
                                        __float_as_uint(__ldg(p.mv + i)), __float_as_uint(__ldg(p.mv + plane + i)),
                                        e >> 24, RX0, RY0);
                 }
@@ -466,7 +611,7 @@ __device__ inline void engine_splat_global(EngineSmem<CT, WX, WY> &s, const Tile
 
 // Stage (b) for one target pixel (gx, gy) at region cell r from the keys kw (as 32-bit words) through accessor a.
 template <typename CT, class Acc>
-__device__ __forceinline__ void gather_pixel(const uint32_t *kw, const Acc &a, const TileParams &p, int k, int gx,
+__device__ __forceinline__ void gather_pixel(const uint32_t *kw, const Acc &a, const FrameDims &p, int k, int gx,
                                              int gy, int r, float4 &c, uint8_t &m) {
     const bool in = gx < p.W && gy < p.H;
     const uint32_t dq = kw[2 * r + 1];
@@ -518,7 +663,7 @@ __device__ __forceinline__ void gather_pixel(const uint32_t *kw, const Acc &a, c
 }
 
 template <typename CT, class Acc>
-__device__ __forceinline__ void gather_block(const uint64_t *keys, const Acc &a, const TileParams &p, int k, int TX,
+__device__ __forceinline__ void gather_block(const uint64_t *keys, const Acc &a, const FrameDims &p, int k, int TX,
                                              int TY, int bx, int by, float4 c[4], uint8_t m[4]) {
     const uint32_t *kw = reinterpret_cast<const uint32_t *>(keys);
 #pragma unroll
@@ -549,11 +694,9 @@ __device__ __forceinline__ void upper_levels(const float4 *l2, float4 &l3, float
 }
 
 template <typename CT>
-__device__ __forceinline__ void store_block(const TileParams &p, int kk, int TX, int TY, const float4 c[4],
+__device__ __forceinline__ void store_block(const FrameDims &p, CT *oc, uint8_t *om, int TX, int TY, const float4 c[4],
                                             const uint8_t m[4], const bool write[4], bool vec) {
     const size_t plane = (size_t)p.W * p.H;
-    CT *oc = (CT *)p.out_color[kk];
-    uint8_t *om = p.out_mask[kk];
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy) {
         const int gy = TY + dy;
@@ -588,11 +731,34 @@ __device__ __forceinline__ void store_block(const TileParams &p, int kk, int TX,
     }
 }
 
+// Items (tile, fraction) a group has published but not yet counted: thread 0 of the group publishes every node
+// of the group's tiles and counts them in batches -- when the group moves to another stream or kind of item,
+// when it waits for its next item, and before it leaves -- behind one fence per batch.  The stream's first fix-up
+// item starts once the count is complete.
+struct PendingCount {
+    FrameHeader *fh = nullptr;
+    uint32_t n = 0;
+    __device__ __forceinline__ void flush() {
+        if (n != 0u) {
+            __threadfence();
+            atomicAdd(&fh->done, n);
+            n = 0u;
+        }
+    }
+    __device__ __forceinline__ void add(FrameHeader *f) {
+        if (f != fh) {
+            flush();
+            fh = f;
+        }
+        ++n;
+    }
+};
+
 // Fill and store one fraction of the tile for the calling group (contains one group barrier).  c[] .w = validity.
-template <typename CT, int WX, int WY>
-__device__ __forceinline__ void fill_store_block(EngineSmem<CT, WX, WY> &s, const TileParams &p, int g, int kk,
-                                                 int tile, int buf, int TX, int TY, float4 c[4], const uint8_t m[4],
-                                                 bool vec) {
+template <typename CT>
+__device__ __forceinline__ void fill_store_block(EngineSmem &s, const TileParams &p, const FrameDims &d, CT *oc,
+                                                 uint8_t *om, int g, int kk, int tile, int buf, int TX, int TY,
+                                                 float4 c[4], const uint8_t m[4], bool vec) {
     const int tg = threadIdx.x & (kGroupThreads - 1);
     const int lane = tg & 31, w = tg >> 5;
     const float4 n1 = mean4(c[0], c[1], c[2], c[3]);
@@ -607,7 +773,7 @@ __device__ __forceinline__ void fill_store_block(EngineSmem<CT, WX, WY> &s, cons
     for (int t = 0; t < 4; ++t) deep = deep || (m[t] != 0 && n1.w == 0.0f && n2.w == 0.0f);
     float4 l3 = n2, l4 = n2, l5 = n2;
     if (w == 0 || __any_sync(0xFFFFFFFFu, deep)) upper_levels(l2, l3, l4, l5);
-    if (w == 0 && lane == 0) publish_node(p, l5, kk, tile);  // counted (after a fence) when the group finishes
+    if (w == 0 && lane == 0) publish_node(p, l5, kk, tile);
     // push: first valid ancestor (tile rows 4w..4w+3: level-3 node (w >> 1, bx >> 2), level-4 (w >> 2, bx >> 3))
     const int bx = lane & 15;
     const float4 v3 = shfl4_idx(l3, (w >> 1) * 4 + (bx >> 2));
@@ -620,12 +786,12 @@ __device__ __forceinline__ void fill_store_block(EngineSmem<CT, WX, WY> &s, cons
         if (hole) c[t] = push;
         write[t] = !hole || push.w != 0.0f;
     }
-    store_block<CT>(p, kk, TX, TY, c, m, write, vec);
+    store_block<CT>(d, oc, om, TX, TY, c, m, write, vec);
 }
 
-// Coarse levels of the pyramid and the value of every tile without a valid pixel, run by one group.
-__device__ inline void engine_coarse_pass(const TileParams &p, int g) {
-    const int tid = threadIdx.x & (kGroupThreads - 1), nt = kGroupThreads;
+// Coarse levels of the pyramid and the value of every tile without a valid pixel (all consumer threads).
+__device__ inline void engine_coarse_pass(const TileParams &p) {
+    const int tid = threadIdx.x, nt = kConsumerThreads;
     const int n5 = p.n5x * p.n5y;
     for (int kk = 0; kk < p.nfrac; ++kk) {
         const uint32_t cnt = __ldcg(&p.fh->ninvalid[kk]);
@@ -647,7 +813,7 @@ __device__ inline void engine_coarse_pass(const TileParams &p, int g) {
                 par[node] = mean4(c[0], c[1], c[2], c[3]);
             }
             __threadfence_block();
-            bar_sync(2 + g, kGroupThreads);
+            bar_sync(kBarConsumers, kConsumerThreads);
             child = par;
             off += pw * ph;
             cw = pw;
@@ -673,7 +839,7 @@ __device__ inline void engine_coarse_pass(const TileParams &p, int g) {
             }
             p.fillval[(size_t)kk * n5 + e] = make_float4(v.x, v.y, v.z, 1.0f);
         }
-        bar_sync(2 + g, kGroupThreads);
+        bar_sync(kBarConsumers, kConsumerThreads);
     }
 }
 
@@ -734,13 +900,13 @@ __device__ __forceinline__ void smooth_column(const Window<CT, WX, WY> &win, int
 }
 
 template <typename CT>
-__device__ __forceinline__ void store_column(const TileParams &p, int kk, int X0, int Y0, const CT out[4][3]) {
+__device__ __forceinline__ void store_column(const FrameDims &p, CT *oc, uint8_t *om, int X0, int Y0,
+                                             const CT out[4][3]) {
     const int tg = threadIdx.x & (kGroupThreads - 1);
     const int lane = tg & 31, w = tg >> 5;
     const int x = X0 + lane;
     if (x >= p.W) return;
     const size_t plane = (size_t)p.W * p.H;
-    CT *oc = (CT *)p.out_color[kk];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         const int y = Y0 + 4 * w + r;
@@ -749,16 +915,16 @@ __device__ __forceinline__ void store_column(const TileParams &p, int kk, int X0
         oc[q] = out[r][0];
         oc[plane + q] = out[r][1];
         oc[2 * plane + q] = out[r][2];
-        p.out_mask[kk][q] = 0;
+        om[q] = 0;
     }
 }
 
 // Level-5 node of a tile whose pixels are all valid, from columns of four pixels (same pyramid as mean4 over
 // valid children): levels 1 and 2 by shuffles, the level-2 row of each warp to shared memory, levels 3-5 by
 // warp 0, which publishes it.  The other warps only arrive at the group barrier.
-template <typename CT, int WX, int WY>
-__device__ __forceinline__ void smooth_publish(EngineSmem<CT, WX, WY> &s, const TileParams &p, int g, int kk, int tile,
-                                               int buf, const CT out[4][3]) {
+template <typename CT>
+__device__ __forceinline__ void smooth_publish(EngineSmem &s, const TileParams &p, int g, int kk, int tile, int buf,
+                                               const CT out[4][3]) {
     const int tg = threadIdx.x & (kGroupThreads - 1);
     const int lane = tg & 31, w = tg >> 5;
     float4 px[4], pp[4];
@@ -793,103 +959,171 @@ __device__ __forceinline__ void smooth_publish(EngineSmem<CT, WX, WY> &s, const 
 // ------------------------------------------------------------------------------------------------------------
 // Consumers
 // ------------------------------------------------------------------------------------------------------------
+// One target tile for the calling group (fraction k0 + g); the splat (modes 1-3) is done.
 template <typename CT, int WX, int WY, bool FILL>
-__device__ void engine_consumer(EngineSmem<CT, WX, WY> &s, const TileParams &p, bool vec) {
+__device__ __forceinline__ void tile_group(EngineSmem &s, const TileSlot &sl, int b, int g, int buf) {
+    const TileParams &p = sl.p;
+    const FrameDims d = dims_of(p);
+    const int tg = threadIdx.x & (kGroupThreads - 1);
+    const int bx = tg & 15, by = tg >> 4;
+    const int mode = sl.plan.mode, tile = sl.index, X0 = sl.X0, Y0 = sl.Y0;
+    const int wx0 = sl.plan.wx0, wy0 = sl.plan.wy0;
+    const int kk = g, k = d.k0 + kk;
+    const int TX = X0 + 2 * bx, TY = Y0 + 2 * by;
+    CT *oc = (CT *)p.out_color[kk];
+    uint8_t *om = p.out_mask[kk];
+    const bool vec = (d.W % 2) == 0 && ((uintptr_t)oc % (2 * sizeof(CT))) == 0 && ((uintptr_t)om % 2) == 0;
+    Window<CT, WX, WY> &win = window<CT, WX, WY>(s, b);
+    if (mode == 5) {
+        CT out[4][3];
+        smooth_column<CT, WX, WY>(win, wx0, wy0, sl.u[kk], X0, Y0, out);
+        store_column<CT>(d, oc, om, X0, Y0, out);
+        if (FILL) smooth_publish<CT>(s, p, g, kk, tile, buf, out);
+        return;
+    }
+    float4 c[4];
+    uint8_t m[4];
+    if (mode == 0) {
+        const UniformFrac &u = sl.u[kk];
+        if (u.flags & kInterior) uniform_block_any<CT, WX, WY, false>(win, wx0, wy0, d, u, TX, TY, c, m);
+        else uniform_block_any<CT, WX, WY, true>(win, wx0, wy0, d, u, TX, TY, c, m);
+    } else if (mode == 1) {
+        const WinAcc<CT, WX, WY> wa{&win, wx0, wy0};
+        gather_block<CT>(s.key[kk], wa, d, k, TX, TY, bx, by, c, m);
+    } else if (mode == 2 || mode == 3) {
+        const GlobalAcc<CT> ga{(const CT *)p.color, p.depth, p.mv, d.W, (size_t)d.W * d.H};
+        gather_block<CT>(s.key[kk], ga, d, k, TX, TY, bx, by, c, m);
+    } else {  // 4: nothing lands
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            c[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+            m[t] = (TX + (t & 1) < d.W && TY + (t >> 1) < d.H) ? (uint8_t)EXW_MASK_EMPTY : (uint8_t)0;
+        }
+    }
+    if (FILL) {
+        fill_store_block<CT>(s, p, d, oc, om, g, kk, tile, buf, TX, TY, c, m, vec);
+    } else {
+        const bool all[4] = {true, true, true, true};
+        store_block<CT>(d, oc, om, TX, TY, c, m, all, vec);
+        if (mode >= 1 && mode <= 3)
+            bar_sync(2 + g, kGroupThreads);  // every key read of the group is done before the next init
+    }
+}
+
+// The splat of a tile (modes 1-3), all consumer threads; keys were initialised before the slot's vote.
+template <typename CT, int WX, int WY>
+__device__ __forceinline__ void tile_splat(EngineSmem &s, const TileSlot &sl, int b, int tid) {
+    const TileParams &p = sl.p;
+    const FrameDims d = dims_of(p);
+    const int mode = sl.plan.mode;
+    const int RX0 = sl.X0 - 1, RY0 = sl.Y0 - 1;
+    if (mode == 1) {
+        const WinAcc<CT, WX, WY> wa{&window<CT, WX, WY>(s, b), sl.plan.wx0, sl.plan.wy0};
+        engine_splat_window(s.key, d, wa, plan_union(sl.plan, d.nfrac), RX0, RY0, tid);
+        bar_sync(kBarConsumers, kConsumerThreads);
+    } else if (mode == 2 || mode == 3) {
+        engine_splat_global(s, p, d, RX0, RY0, tid);
+    }
+}
+
+struct HalfGroupBarrier {  // the 4 warps of half group h: named barrier 5 + h
+    int id;
+    __device__ __forceinline__ void operator()() const { bar_sync(id, kGroupThreads / 2); }
+};
+
+template <bool FILL>
+__device__ void engine_consumer(EngineSmem &s) {
     const int tid = threadIdx.x;  // 0 .. 767
     const int g = tid >> 8, tg = tid & (kGroupThreads - 1);
-    const int bx = tg & 15, by = tg >> 4;
-    const bool active = g < p.nfrac;
-    const GlobalAcc<CT> ga{(const CT *)p.color, p.depth, p.mv, p.W, (size_t)p.W * p.H};
-    bool aborted = false;
-    uint32_t ndone = 0;  // (tile, fraction) items this group finished
+    const int lane = tid & 31, w = tid >> 5;
+    PendingCount pend;  // thread 0 of each group
     for (uint32_t i = 0;; ++i) {
         const int b = (int)(i & 1u);
-        const bool ok = mbar_wait_or_abort(&s.full[b], (i >> 1) & 1u, &s.abort);
+        // the next item is not ready: count what this group published before blocking (the producer may be
+        // waiting for exactly that count)
+        if (FILL && tg == 0 && pend.n != 0u && !mbar_test_wait(&s.full[b], (i >> 1) & 1u)) pend.flush();
+        bool ok = false;
+        for (uint32_t it = 1; it <= kWaitLimit; ++it) {
+            if (mbar_try_wait(&s.full[b], (i >> 1) & 1u)) {
+                ok = true;
+                break;
+            }
+            if ((it & 15u) == 0u) {
+                if (*(volatile int *)&s.abort) break;
+                __nanosleep(64);
+            }
+        }
         const TileSlot &sl = s.slot[b];
-        const int mode = ok ? sl.plan.mode : kModeEnd;
-        Window<CT, WX, WY> &win = s.win[b];
-        if (ok && mode == 0)
-            build_source_words(win, sl.plan.wx0, sl.plan.wy0, sl.N, __uint_as_float(sl.plan.umx),
-                               __uint_as_float(sl.plan.umy), tid);
-        if (ok && mode >= 1 && mode <= 3 && active)
+        const int kind = ok ? sl.kind : kSlotEnd;
+        const int mode = kind == kSlotTile ? sl.plan.mode : -1;
+        const TileParams &p = sl.p;
+        if (ok && mode == 0) {
+            if (sl.cdt == EXW_F16)
+                build_source_words(window<__half, kWinXF16, kWinYF16>(s, b), sl.plan.wx0, sl.plan.wy0, sl.N,
+                                   __uint_as_float(sl.plan.umx), __uint_as_float(sl.plan.umy), tid);
+            else
+                build_source_words(window<float, kWinXF32, kWinYF32>(s, b), sl.plan.wx0, sl.plan.wy0, sl.N,
+                                   __uint_as_float(sl.plan.umx), __uint_as_float(sl.plan.umy), tid);
+        }
+        if (ok && mode >= 1 && mode <= 3 && g < p.nfrac)
             for (int r = tg; r < kRegionN; r += kGroupThreads) s.key[g][r] = kKeyEmpty;
         if (bar_red_or(kBarConsumers, kConsumerThreads, !ok)) {
             if (tid == 0) {
-                atomicExch(p.status, (uint32_t)EXW_ERR_TIMEOUT);
+                atomicCAS(sl.p.status, 0u, (uint32_t)EXW_ERR_TIMEOUT);
                 *(volatile int *)&s.abort = 1;
             }
-            aborted = true;
-            break;
+            return;
         }
-        if (mode == kModeEnd) break;
-        const int tile = sl.tile, X0 = sl.X0, Y0 = sl.Y0;
-        const int RX0 = X0 - 1, RY0 = Y0 - 1;
-        const int wx0 = sl.plan.wx0, wy0 = sl.plan.wy0;
-        if (mode == 1) {
-            const WinAcc<CT, WX, WY> wa{&win, wx0, wy0};
-            engine_splat_window(s.key, p, wa, plan_union(sl.plan, p.nfrac), RX0, RY0, tid);
-            bar_sync(kBarConsumers, kConsumerThreads);
-        } else if (mode == 2 || mode == 3) {
-            engine_splat_global(s, p, RX0, RY0, tid);
-        }
-        if (active) {
-            const int kk = g, k = p.k0 + kk;
-            const int TX = X0 + 2 * bx, TY = Y0 + 2 * by;
-            float4 c[4];
-            uint8_t m[4];
-            if (mode == 5) {
-                CT out[4][3];
-                smooth_column<CT, WX, WY>(win, wx0, wy0, sl.u[kk], X0, Y0, out);
-                store_column<CT>(p, kk, X0, Y0, out);
-                if (FILL) {
-                    smooth_publish(s, p, g, kk, tile, (int)(i & 1u), out);
-                    ++ndone;
-                }
-            } else if (mode == 0) {
-                const UniformFrac &u = sl.u[kk];
-                if (u.flags & kInterior) uniform_block_any<CT, WX, WY, false>(win, wx0, wy0, p, u, TX, TY, c, m);
-                else uniform_block_any<CT, WX, WY, true>(win, wx0, wy0, p, u, TX, TY, c, m);
-            } else if (mode == 1) {
-                const WinAcc<CT, WX, WY> wa{&win, wx0, wy0};
-                gather_block<CT>(s.key[kk], wa, p, k, TX, TY, bx, by, c, m);
-            } else if (mode == 2 || mode == 3) {
-                gather_block<CT>(s.key[kk], ga, p, k, TX, TY, bx, by, c, m);
-            } else {  // 4: nothing lands
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    c[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    m[t] = (TX + (t & 1) < p.W && TY + (t >> 1) < p.H) ? (uint8_t)EXW_MASK_EMPTY : (uint8_t)0;
+        if (FILL && tg == 0 && (kind != kSlotTile || p.fh != pend.fh)) pend.flush();
+        if (kind == kSlotEnd) return;
+        if (kind == kSlotBounds) {
+            const int h = tid >> 7, th = tid & 127;  // half group: 4 warps, 8 rows each, 24 loads in flight
+            const int region = sl.index * kRegionsPerItem + h;
+            const int nrx = (p.W + 31) / 32;
+            if (region < nrx * ((p.H + 31) / 32)) {
+                bounds_region<4>(p.depth, p.mv, p.W, p.H, const_cast<float4 *>(p.tile_bounds),
+                                 const_cast<float2 *>(p.tile_depth), const_cast<float4 *>(p.region_bounds), p.fh,
+                                 region % nrx, region / nrx, &s.bpart[g][32 * (h & 1)], true, th,
+                                 HalfGroupBarrier{5 + h});
+                if (th < 32) {  // warp 0 of the half group wrote the bounds
+                    __threadfence();
+                    __syncwarp();
+                    if (th == 0) atomicAdd(&p.fh->bdone, 1u);
                 }
             }
-            if (mode == 5) {
-                // stored above
-            } else if (FILL) {
-                fill_store_block(s, p, g, kk, tile, (int)(i & 1u), TX, TY, c, m, vec);
-                ++ndone;
-            } else {
-                const bool all[4] = {true, true, true, true};
-                store_block<CT>(p, kk, TX, TY, c, m, all, vec);
-                if (mode >= 1 && mode <= 3)
-                    bar_sync(2 + g, kGroupThreads);  // every key read of the group is done before the next init
+            bar_sync(2 + g, kGroupThreads);  // the group's bounds partials are free again
+        } else if (kind == kSlotPlans) {
+            const int tile = sl.index * kPlansPerItem + w;
+            if (tile < p.n5x * p.n5y) {
+                if (sl.cdt == EXW_F16) plan_tile<__half, kWinXF16, kWinYF16>(p, tile);
+                else plan_tile<float, kWinXF32, kWinYF32>(p, tile);
+                if (lane == 0) {
+                    __threadfence();
+                    atomicAdd(&p.fh->pdone, 1u);
+                }
             }
+        } else if (kind == kSlotFixup) {
+            if (sl.index == 0) {  // every node of the stream is counted: build the coarse levels, then release
+                __threadfence();
+                engine_coarse_pass(p);
+                __threadfence();
+                bar_sync(kBarConsumers, kConsumerThreads);
+                if (tid == 0) asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&p.fh->cready), "r"(1u) : "memory");
+            }
+            if (sl.cdt == EXW_F16) fixup_slice<__half>(p, (uint32_t)sl.index, kFixupItems, tid, kConsumerThreads);
+            else fixup_slice<float>(p, (uint32_t)sl.index, kFixupItems, tid, kConsumerThreads);
+        } else {  // target tile
+            if (sl.cdt == EXW_F16) tile_splat<__half, kWinXF16, kWinYF16>(s, sl, b, tid);
+            else tile_splat<float, kWinXF32, kWinYF32>(s, sl, b, tid);
+            if (g < p.nfrac) {
+                if (sl.cdt == EXW_F16) tile_group<__half, kWinXF16, kWinYF16, FILL>(s, sl, b, g, (int)(i & 1u));
+                else tile_group<float, kWinXF32, kWinYF32, FILL>(s, sl, b, g, (int)(i & 1u));
+                if (FILL && tg == 0) pend.add(p.fh);
+            }
+            if (mode == 0) fence_proxy_async_smem();  // generic writes to the window before the next TMA into it
         }
-        if (mode == 0) fence_proxy_async_smem();  // generic writes to the window before the next TMA into it
         __syncwarp();
-        if ((tid & 31) == 0) mbar_arrive(&s.empty[b]);
-    }
-    if (FILL && active && !aborted) {
-        // Count this group's items after a fence over its level-5 nodes; the group that completes the frame's
-        // count builds the coarse levels.
-        if (tg == 0) {
-            __threadfence();
-            const uint32_t total = (uint32_t)(p.n5x * p.n5y) * (uint32_t)p.nfrac;
-            s.last[g] = ndone > 0u && atomicAdd(&p.fh->done, ndone) + ndone == total;
-        }
-        bar_sync(2 + g, kGroupThreads);
-        if (s.last[g]) {
-            __threadfence();
-            engine_coarse_pass(p, g);
-        }
+        if (lane == 0) mbar_arrive(&s.empty[b]);
     }
 }
 

@@ -1,18 +1,10 @@
-// exw_fwd.cu -- forward kernels besides the persistent engine (exw_engine.cu): the plain fused kernel (one tile
-// per CTA, sources from global memory, for frames whose rows cannot be TMA-staged), tile plans, the staged gather
-// (exw_warp), the staged fill (exw_fill_holes) and the coarse fix-up.
+// exw_fwd.cu -- the staged kernels (exw_warp's gather, exw_fill_holes' fill) and the coarse fix-up; the fused
+// forward pass is the persistent engine (exw_engine.cu).
 #include "exw_items.cuh"
 
 namespace exw {
 
-// Plain fused kernel: one tile per CTA, source read from global memory (any frame width).
-template <typename CT, bool FILL>
-__global__ void __launch_bounds__(kThreads) fused_kernel(TileParams p) {
-    __shared__ __align__(16) TileSmem s;
-    plain_tile<CT, FILL>(s, p, blockIdx.y * p.n5x + blockIdx.x);
-}
-
-// Plans: one warp per target tile.
+// Plans: one warp per target tile (the first stream of an engine launch is planned ahead of the launch).
 template <typename CT, int WX, int WY>
 __global__ void __launch_bounds__(kThreads) plan_kernel(TileParams p) {
     const int tile = blockIdx.x * kWarps + (threadIdx.x >> 5);
@@ -81,7 +73,7 @@ __global__ void __launch_bounds__(kThreads) fill_tiles_kernel(TileParams p) {
 // Fix-up: every tile without a valid pixel takes the coarse value chosen for it.
 template <typename CT>
 __global__ void __launch_bounds__(kThreads) fixup_kernel(TileParams p) {
-    fixup_slice<CT>(p, blockIdx.x, gridDim.x);
+    fixup_slice<CT>(p, blockIdx.x, gridDim.x, (int)threadIdx.x, (int)blockDim.x);
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -89,24 +81,9 @@ __global__ void __launch_bounds__(kThreads) fixup_kernel(TileParams p) {
 // ------------------------------------------------------------------------------------------------------------
 static dim3 tile_grid(const TileParams &p) { return dim3((unsigned)p.n5x, (unsigned)p.n5y, 1); }
 
-cudaError_t launch_fused(const TileParams &p, exw_dtype cdt, bool fill, cudaStream_t s) {
-    const dim3 g = tile_grid(p);
-    timing_begin("exw_fused", s);
-    if (cdt == EXW_F32) {
-        if (fill) fused_kernel<float, true><<<g, kThreads, 0, s>>>(p);
-        else fused_kernel<float, false><<<g, kThreads, 0, s>>>(p);
-    } else {
-        if (fill) fused_kernel<__half, true><<<g, kThreads, 0, s>>>(p);
-        else fused_kernel<__half, false><<<g, kThreads, 0, s>>>(p);
-    }
-    count_launch();
-    timing_end("exw_fused", s);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_plan(const TileParams &p, exw_dtype cdt, cudaStream_t s) {
     const int ntiles = p.n5x * p.n5y;
-    const unsigned g = (unsigned)((ntiles + kThreads / 32 - 1) / (kThreads / 32));
+    const unsigned g = (unsigned)((ntiles + kWarps - 1) / kWarps);
     timing_begin("exw_plan", s);
     if (cdt == EXW_F32) plan_kernel<float, kWinXF32, kWinYF32><<<g, kThreads, 0, s>>>(p);
     else plan_kernel<__half, kWinXF16, kWinYF16><<<g, kThreads, 0, s>>>(p);

@@ -119,11 +119,6 @@ struct TileParams {
 constexpr int kWinXF32 = 56, kWinYF32 = 48;
 constexpr int kWinXF16 = 64, kWinYF16 = 56;
 
-// Tensor maps of one source frame: colour [3][H][W], depth [H][W], motion [2][H][W] with the window as box.
-struct TmaMaps {
-    CUtensorMap col, depth, mv;
-};
-
 // Launchers (exw_fwd.cu, exw_aux.cu, exw_bwd.cu).  Each returns the launch error.
 cudaError_t launch_clear_keys(uint64_t *keys, size_t n, cudaStream_t s);
 cudaError_t launch_zero(void *p, size_t bytes, cudaStream_t s);
@@ -132,10 +127,8 @@ cudaError_t launch_splat_global(const float *depth, const float *mv, int W, int 
 cudaError_t launch_bounds(const float *depth, const float *mv, int W, int H, float4 *tile_bounds, float2 *tile_depth,
                           float4 *region_bounds, FrameHeader *fh, cudaStream_t s);
 cudaError_t launch_bounds_finalize(const FrameHeader *fh, float *frame_bounds, cudaStream_t s);
-cudaError_t launch_fused(const TileParams &p, exw_dtype cdt, bool fill, cudaStream_t s);
+
 cudaError_t launch_plan(const TileParams &p, exw_dtype cdt, cudaStream_t s);
-cudaError_t launch_engine(const TileParams &p, const TmaMaps &m, exw_dtype cdt, bool fill, int grid, bool vec,
-                          cudaStream_t s);
 cudaError_t launch_warp_tiles(const TileParams &p, exw_dtype cdt, cudaStream_t s);
 cudaError_t launch_fill_tiles(const TileParams &p, exw_dtype cdt, cudaStream_t s);
 cudaError_t launch_fixup(const TileParams &p, exw_dtype cdt, cudaStream_t s);
@@ -144,6 +137,16 @@ cudaError_t launch_l2_loss(const void *out, const void *target, exw_dtype cdt, c
 cudaError_t launch_backward(const float *grad_out, const void *color, exw_dtype cdt, const float *depth,
                             const float *mv, const uint64_t *keys, int W, int H, int k, int L, float *grad_color,
                             float *grad_mv, cudaStream_t s);
+
+// The fused forward pass of exw_extrapolate and exw_extrapolate_batched (exw_batched.cu): one engine launch per
+// group of at most 48 frames.  specs[i] = (source frame, its nfrac outputs).
+struct EngineSpec {
+    exw_frame src;
+    exw_frame_out out[EXW_MAX_FRAC];
+};
+size_t engine_workspace_bytes(const EngineSpec *specs, int n, int nfrac, bool shared_size);
+exw_status engine_run(const EngineSpec *specs, int n, int nfrac, unsigned flags, void *ws, size_t ws_bytes,
+                      struct exw_tuner *tuner, bool shared_size, cudaStream_t s);
 
 // Timing hooks (exw_api.cu): bracket a launch with events when timing is enabled.
 void timing_begin(const char *name, cudaStream_t s);

@@ -11,12 +11,6 @@ namespace exw {
 constexpr uint32_t kWaitLimit = 1u << 22;  // iterations of the bounded mbarrier wait (each >= 128 ns)
 
 template <typename CT, int WX, int WY>
-struct TmaSmem {
-    Window<CT, WX, WY> win;  // first: 128-byte aligned TMA destinations
-    TileSmem t;
-};
-
-template <typename CT, int WX, int WY>
 __device__ __forceinline__ Rect window_rect(Rect U) {  // window origin/extent for rectangle U grown by 1
     constexpr int kAlign = sizeof(CT) == 2 ? 8 : 4;  // x * element size must be a multiple of 16 bytes
     Rect w;
@@ -230,130 +224,10 @@ __device__ inline void plan_tile(const TileParams &p, int tile) {  // called by 
     p.plans[tile] = pl;
 }
 
-__device__ __forceinline__ Rect union_rect(const TilePlan &pl, int nfrac) {
-    Rect U{1 << 30, -(1 << 30), 1 << 30, -(1 << 30)};
-    for (int kk = 0; kk < nfrac; ++kk) {
-        const Rect R{__ldcg(&pl.rect[kk][0]), __ldcg(&pl.rect[kk][1]), __ldcg(&pl.rect[kk][2]),
-                     __ldcg(&pl.rect[kk][3])};
-        if (R.empty()) continue;
-        U.x0 = min(U.x0, R.x0);
-        U.x1 = max(U.x1, R.x1);
-        U.y0 = min(U.y0, R.y0);
-        U.y1 = max(U.y1, R.y1);
-    }
-    return U;
-}
-
-// Stage the window at (x0, y0) and wait for it.  Returns false (with the status word set) if the bounded wait ran
-// out; every thread returns the same value.  The leading barrier makes every thread finish with the previous
-// contents of the window before the copy overwrites them.
-template <typename CT, int WX, int WY>
-__device__ inline bool load_window(TmaSmem<CT, WX, WY> &s, const TileParams &p, const CUtensorMap *tcol,
-                            const CUtensorMap *tdep, const CUtensorMap *tmv, int x0, int y0, uint32_t &phase) {
-    constexpr uint32_t kBytes = WX * WY * (4 + 8 + 3 * (uint32_t)sizeof(CT));
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&s.t.mbar, kBytes);
-        tma_load_2d(s.win.depth, tdep, x0, y0, &s.t.mbar);
-        tma_load_3d(&s.win.mv[0][0], tmv, x0, y0, 0, &s.t.mbar);
-        tma_load_3d(&s.win.col[0][0], tcol, x0, y0, 0, &s.t.mbar);
-    }
-    const bool ok = mbar_wait_bounded(&s.t.mbar, phase, kWaitLimit);
-    phase ^= 1u;
-    if (__syncthreads_or(!ok)) {
-        if (threadIdx.x == 0) atomicExch(p.status, (uint32_t)EXW_ERR_TIMEOUT);
-        mbar_wait_bounded(&s.t.mbar, phase ^ 1u, kWaitLimit);  // let the copy in flight land before leaving
-        return false;
-    }
-    return true;
-}
-
-// One target tile of the fused pass with TMA-staged windows (all threads of the CTA).  Returns false when a bounded
-// wait ran out (the status word is set).
-template <typename CT, int WX, int WY, bool FILL>
-__device__ bool tma_tile(TmaSmem<CT, WX, WY> &s, const TileParams &p, const CUtensorMap &tcol, const CUtensorMap &tdep,
-                         const CUtensorMap &tmv, int tile, uint32_t &phase) {
-    const int tid = threadIdx.x;
-    const GlobalAcc<CT> ga{(const CT *)p.color, p.depth, p.mv, p.W, (size_t)p.W * p.H};
-    const int X0 = (tile % p.n5x) * kFillTile, Y0 = (tile / p.n5x) * kFillTile;
-    const int RX0 = X0 - 1, RY0 = Y0 - 1;
-    const TilePlan &pl = p.plans[tile];
-    const int mode = __ldcg(&pl.mode);
-    if (tid == 0) atomicAdd(&p.fh->nmode[mode], 1u);
-    if (mode == 0 || mode == 5) {
-        const int x0 = __ldcg(&pl.wx0), y0 = __ldcg(&pl.wy0);
-        const uint32_t umx = __ldcg(&pl.umx), umy = __ldcg(&pl.umy);
-        if (!load_window(s, p, &tcol, &tdep, &tmv, x0, y0, phase)) return false;
-        const WinAcc<CT, WX, WY> wa{&s.win, x0, y0};
-        uint32_t *dw = reinterpret_cast<uint32_t *>(&s.t.key[0][0]);
-        for (int kk = 0; kk < p.nfrac; ++kk)
-            uniform_words(dw + kk * kRegionN, p, wa, axis_off_of(umx, p.k0 + kk, p.L),
-                          axis_off_of(umy, p.k0 + kk, p.L), __uint_as_float(umx), __uint_as_float(umy), RX0, RY0);
-        __syncthreads();
-        for (int kk = 0; kk < p.nfrac; ++kk)
-            finish_fraction<CT, FILL>(s.t, wa,
-                                      UniformSource{dw + kk * kRegionN, __uint_as_float(umx),
-                                                    __uint_as_float(umy), axis_off_of(umx, p.k0 + kk, p.L),
-                                                    axis_off_of(umy, p.k0 + kk, p.L)},
-                                      p, kk, X0, Y0, tile);
-    } else if (mode == 1) {
-        const int x0 = __ldcg(&pl.wx0), y0 = __ldcg(&pl.wy0);
-        const Rect U = union_rect(pl, p.nfrac);
-        init_keys(s.t, p.nfrac);
-        if (!load_window(s, p, &tcol, &tdep, &tmv, x0, y0, phase)) return false;
-        const WinAcc<CT, WX, WY> wa{&s.win, x0, y0};
-        splat_window(s.t, p, wa, U, (1u << p.nfrac) - 1u, RX0, RY0);
-        __syncthreads();
-        for (int kk = 0; kk < p.nfrac; ++kk)
-            finish_fraction<CT, FILL>(s.t, wa, key_source(s.t, kk), p, kk, X0, Y0, tile);
-    } else if (mode == 2) {
-        init_keys(s.t, p.nfrac);
-        for (int kk = 0; kk < p.nfrac; ++kk) {
-            const Rect R{__ldcg(&pl.rect[kk][0]), __ldcg(&pl.rect[kk][1]), __ldcg(&pl.rect[kk][2]),
-                         __ldcg(&pl.rect[kk][3])};
-            if (R.empty()) {
-                __syncthreads();
-                finish_fraction<CT, FILL>(s.t, ga, key_source(s.t, kk), p, kk, X0, Y0, tile);
-                continue;
-            }
-            const Rect w = window_rect<CT, WX, WY>(R);
-            if (!load_window(s, p, &tcol, &tdep, &tmv, w.x0, w.y0, phase)) return false;
-            const WinAcc<CT, WX, WY> wa{&s.win, w.x0, w.y0};
-            splat_window(s.t, p, wa, R, 1u << kk, RX0, RY0);
-            __syncthreads();
-            finish_fraction<CT, FILL>(s.t, wa, key_source(s.t, kk), p, kk, X0, Y0, tile);
-        }
-    } else {  // 3: too wide for a window; 4: nothing lands (every key stays empty)
-        init_keys(s.t, p.nfrac);
-        __syncthreads();
-        if (mode == 3) {
-            splat_global(s.t, p, RX0, RY0);
-            __syncthreads();
-        }
-        for (int kk = 0; kk < p.nfrac; ++kk)
-            finish_fraction<CT, FILL>(s.t, ga, key_source(s.t, kk), p, kk, X0, Y0, tile);
-    }
-    if (FILL) tile_done(p, &s.t.last);
-    return true;
-}
-
-// One target tile of the fused pass reading its sources from global memory (all threads of the CTA).
-template <typename CT, bool FILL>
-__device__ void plain_tile(TileSmem &s, const TileParams &p, int tile) {
-    const int X0 = (tile % p.n5x) * kFillTile, Y0 = (tile / p.n5x) * kFillTile;
-    init_keys(s, p.nfrac);
-    __syncthreads();
-    splat_global(s, p, X0 - 1, Y0 - 1);
-    __syncthreads();
-    const GlobalAcc<CT> a{(const CT *)p.color, p.depth, p.mv, p.W, (size_t)p.W * p.H};
-    for (int kk = 0; kk < p.nfrac; ++kk) finish_fraction<CT, FILL>(s, a, key_source(s, kk), p, kk, X0, Y0, tile);
-    if (FILL) tile_done(p, &s.last);
-}
-
-// Fix-up of the tiles without a valid pixel: this CTA takes list entries first, first + stride, ...
+// Fix-up of the tiles without a valid pixel: the calling threads (tid of nt) take list entries first,
+// first + stride, ...
 template <typename CT>
-__device__ void fixup_slice(const TileParams &p, uint32_t first, uint32_t stride) {
+__device__ void fixup_slice(const TileParams &p, uint32_t first, uint32_t stride, int tid, int nt) {
     const int n5 = p.n5x * p.n5y;
     const size_t plane = (size_t)p.W * p.H;
     for (int kk = 0; kk < p.nfrac; ++kk) {
@@ -364,7 +238,7 @@ __device__ void fixup_slice(const TileParams &p, uint32_t first, uint32_t stride
             const float4 v = __ldcg(p.fillval + (size_t)kk * n5 + e);
             const int X0 = (int)(tile % (uint32_t)p.n5x) * kFillTile, Y0 = (int)(tile / (uint32_t)p.n5x) * kFillTile;
             const CT c0 = to_storage<CT>(v.x), c1 = to_storage<CT>(v.y), c2 = to_storage<CT>(v.z);
-            for (int i = threadIdx.x; i < kFillTile * kFillTile; i += blockDim.x) {
+            for (int i = tid; i < kFillTile * kFillTile; i += nt) {
                 const int gx = X0 + (i & 31), gy = Y0 + (i >> 5);
                 if (gx >= p.W || gy >= p.H) continue;
                 const size_t q = (size_t)gy * p.W + gx;
@@ -384,12 +258,16 @@ __device__ void fixup_slice(const TileParams &p, uint32_t first, uint32_t stride
 // warps), lane = column.  part: 8 float4 per warp of shared memory.
 // The region's bounds go to region_bounds[ry * ceil(W / 32) + rx]; with frame_atomics the frame-wide maxima are
 // raised here, else the caller raises them from the returned bounds (valid in warp 0).
-template <int NW>  // warps of the calling CTA (4, 8 or 16)
+// NW warps take part (4, 8 or 16), thread index tid in [0, 32 NW); bar() is a barrier over exactly them.
+struct CtaBarrier {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+template <int NW, class Bar>
 __device__ inline float4 bounds_region(const float *__restrict__ depth, const float *__restrict__ mv, int W, int H,
                                 float4 *tile_bounds, float2 *tile_depth, float4 *region_bounds, FrameHeader *fh,
-                                int rx, int ry, float4 *part, bool frame_atomics) {
+                                int rx, int ry, float4 *part, bool frame_atomics, int tid, Bar bar) {
     constexpr int nw = NW, rpw = 32 / NW;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int lane = tid & 31, w = tid >> 5;
     const int X0 = rx * 32, Y0 = ry * 32;
     const size_t plane = (size_t)W * H;
     float mnx = __int_as_float(0x7F800000), mxx = -mnx, mny = mnx, mxy = -mnx;
@@ -438,9 +316,9 @@ __device__ inline float4 bounds_region(const float *__restrict__ depth, const fl
         part[w * 4 + (lane >> 3)] = make_float4(mnx, mxx, mny, mxy);
         part[4 * nw + w * 4 + (lane >> 3)] = make_float4(dmn, dmx, bad, 0.0f);
     }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        const int t = threadIdx.x;
+    bar();
+    if (tid < 32) {
+        const int t = tid;
         float4 b = make_float4(__int_as_float(0x7F800000), __int_as_float(0xFF800000), __int_as_float(0x7F800000),
                                __int_as_float(0xFF800000));
         if (t < 16) {
@@ -478,15 +356,6 @@ __device__ inline float4 bounds_region(const float *__restrict__ depth, const fl
         return b;
     }
     return make_float4(0.f, 0.f, 0.f, 0.f);
-}
-
-// Raise the frame-wide maxima to cover bounds b (threads 0..3 of the calling warp).
-__device__ __forceinline__ void raise_frame_bounds(FrameHeader *fh, float4 b) {
-    const int t = threadIdx.x & 31;
-    if (t < 4 && b.x <= b.y) {
-        const float v = t == 0 ? -b.x : t == 1 ? b.y : t == 2 ? -b.z : b.w;
-        atomicMax(&fh->acc[t], float_order(v));
-    }
 }
 
 }  // namespace exw
