@@ -545,18 +545,85 @@ __device__ __forceinline__ Rect plan_union(const TilePlan &pl, int nfrac) {
     return U;
 }
 
-// Splat every window pixel of rectangle U for all fractions (all consumer threads).
-template <typename CT, int WX, int WY>
-__device__ __forceinline__ void engine_splat_window(uint64_t (*key)[kRegionN], const FrameDims &p,
-                                                    const WinAcc<CT, WX, WY> &a, Rect U, int RX0, int RY0, int tid) {
-    const int lane = tid & 31, wid = tid >> 5;
-    const uint32_t fm = (1u << p.nfrac) - 1u;
-    for (int y = U.y0 + wid; y <= U.y1; y += kConsumerWarps)
-        for (int x = U.x0 + lane; x <= U.x1; x += 32) {
-            const int i = a.at(x, y);
-            engine_splat_pixel(key, p, x, y, __float_as_uint(a.w->depth[i]), __float_as_uint(a.w->mv[0][i]),
-                               __float_as_uint(a.w->mv[1][i]), fm, RX0, RY0);
+// A candidate 8 x 8 source tile of a splat: the fractions whose landing rectangle meets R and, for a clean tile
+// (one exact motion, every pixel can land), its whole-pixel offsets per fraction.
+struct SplatTile {
+    uint16_t bx, by;
+    uint8_t fm, clean;
+    int8_t ox[kMaxFrac], oy[kMaxFrac];
+    int8_t pad[2];
+};
+static_assert(sizeof(SplatTile) == 14 || sizeof(SplatTile) == 16, "compact");
+constexpr int kMaxSplatTiles = (int)(sizeof(uint32_t) * kConsumerThreads / sizeof(SplatTile));
+
+// Describe the 8 x 8 source tiles overlapping rectangle U (all consumer threads, no barrier).  Returns the count.
+__device__ __forceinline__ int describe_tiles(SplatTile *out, const TileParams &p, const FrameDims &d, Rect U,
+                                              int RX0, int RY0, int tid) {
+    const int tx0 = U.x0 >> 3, ty0 = U.y0 >> 3, ntx = (U.x1 >> 3) - tx0 + 1;
+    const int nt = ntx * ((U.y1 >> 3) - ty0 + 1);
+    for (int t = tid; t < nt && t < kMaxSplatTiles; t += kConsumerThreads) {
+        const int bx = tx0 + t % ntx, by = ty0 + t / ntx;
+        SplatTile st{};
+        st.bx = (uint16_t)bx;
+        st.by = (uint16_t)by;
+        const float4 b = __ldcg(p.tile_bounds + (size_t)by * p.nbx + bx);
+        if (b.x <= b.y) {
+            const float2 dr = __ldcg(p.tile_depth + (size_t)by * p.nbx + bx);
+            const bool uni = b.x == b.y && b.z == b.w;
+            uint32_t fm = 0;
+            for (int kk = 0; kk < d.nfrac; ++kk) {
+                int ox0, ox1, oy0, oy1;
+                tile_offsets(b, d.k0 + kk, d.L, ox0, ox1, oy0, oy1);
+                if (8 * bx + 7 + ox1 >= RX0 && 8 * bx + ox0 < RX0 + kRegion && 8 * by + 7 + oy1 >= RY0 &&
+                    8 * by + oy0 < RY0 + kRegion)
+                    fm |= 1u << kk;
+                st.ox[kk] = (int8_t)max(-128, min(127, ox0));
+                st.oy[kk] = (int8_t)max(-128, min(127, oy0));
+            }
+            st.fm = (uint8_t)fm;
+            // offsets of a tile that reaches R lie within the window's span, far inside int8
+            st.clean = uni && dr.x > 0.0f ? 1 : 0;
         }
+        out[t] = st;
+    }
+    return nt < kMaxSplatTiles ? nt : kMaxSplatTiles;
+}
+
+// Splat the pixels of rectangle U from the staged window for all fractions (all consumer threads): candidate
+// 8 x 8 tiles only, a warp per tile (two pixels per lane); a clean tile splats with its precomputed offsets.
+template <typename CT, int WX, int WY>
+__device__ __forceinline__ void engine_splat_window(EngineSmem &s, const TileParams &p, const FrameDims &d,
+                                                    const WinAcc<CT, WX, WY> &a, Rect U, int RX0, int RY0, int tid) {
+    SplatTile *tiles = reinterpret_cast<SplatTile *>(s.cand);
+    const int nt = describe_tiles(tiles, p, d, U, RX0, RY0, tid);
+    bar_sync(kBarConsumers, kConsumerThreads);
+    const int lane = tid & 31, wid = tid >> 5;
+    for (int t = wid; t < nt; t += kConsumerWarps) {
+        const SplatTile st = tiles[t];
+        if (!st.fm) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int x = 8 * st.bx + (lane & 7), y = 8 * st.by + (lane >> 3) + 4 * h;
+            if (x < U.x0 || x > U.x1 || y < U.y0 || y > U.y1) continue;
+            const int i = a.at(x, y);
+            const uint32_t db = __float_as_uint(a.w->depth[i]);
+            if (st.clean) {
+                const uint64_t kv = pack_key_local(db, x, y);
+#pragma unroll
+                for (int kk = 0; kk < kMaxFrac; ++kk) {
+                    if (!(st.fm & (1u << kk))) continue;
+                    const int gx = x + st.ox[kk], gy = y + st.oy[kk];
+                    if ((unsigned)gx >= (unsigned)d.W || (unsigned)gy >= (unsigned)d.H) continue;
+                    const int rx = gx - RX0, ry = gy - RY0;
+                    if ((unsigned)rx < (unsigned)kRegion && (unsigned)ry < (unsigned)kRegion)
+                        atomicMin((unsigned long long *)&s.key[kk][ry * kRegion + rx], (unsigned long long)kv);
+                }
+            } else {
+                engine_splat_pixel(s.key, d, x, y, db, __float_as_uint(a.w->mv[0][i]),
+                                   __float_as_uint(a.w->mv[1][i]), st.fm, RX0, RY0);
+            }
+        }
+    }
 }
 
 // Splat from global memory: the 8 x 8 source tiles whose bounds reach R, 64 threads per tile (all consumers).
@@ -1019,7 +1086,7 @@ __device__ __forceinline__ void tile_splat(EngineSmem &s, const TileSlot &sl, in
     const int RX0 = sl.X0 - 1, RY0 = sl.Y0 - 1;
     if (mode == 1) {
         const WinAcc<CT, WX, WY> wa{&window<CT, WX, WY>(s, b), sl.plan.wx0, sl.plan.wy0};
-        engine_splat_window(s.key, d, wa, plan_union(sl.plan, d.nfrac), RX0, RY0, tid);
+        engine_splat_window(s, p, d, wa, plan_union(sl.plan, d.nfrac), RX0, RY0, tid);
         bar_sync(kBarConsumers, kConsumerThreads);
     } else if (mode == 2 || mode == 3) {
         engine_splat_global(s, p, d, RX0, RY0, tid);
