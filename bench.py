@@ -61,11 +61,12 @@ def dist_env():
     return rank, world, local
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a kernel from one ncu capture, with the
-# hash of the kernel sources it was taken on: reported only while the sources are unchanged, else null.
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of a kernel per SOURCE FRAME it processed, from one ncu
+# capture (a smaller launch; the engine's traffic grows in proportion to the frames of a launch), with the hash of
+# the kernel sources it was taken on: reported only while the sources are unchanged, else null.
 MEASURED_TRAFFIC = {
-    ("exw_engine", "sequence_1080p_fp32"): (67.92e6, "c95faedd639a23c4"),
-    ("exw_engine", "warp_4k_fp16"): (233.14e6, "c95faedd639a23c4"),
+    ("exw_engine", "sequence_1080p_fp32"): (515.30e6 / 4, "2d0fbefb985e262d"),
+    ("exw_engine", "warp_4k_fp16"): (235.63e6, "2d0fbefb985e262d"),
 }
 
 
@@ -466,7 +467,8 @@ def run_exw(args):
     peak, peak_kind = peaks()
     achieved = alg_bytes / (avg_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": measured_traffic(dom, "sequence_1080p_fp32"),
+                "frac": achieved / peak,
+                "traffic": (measured_traffic(dom, "sequence_1080p_fp32") or 0.0) * frames_per_launch or None,
                 "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": alg_bytes, "mean_launch_ms": avg_ms,
                 "source_frames_per_launch": frames_per_launch,
