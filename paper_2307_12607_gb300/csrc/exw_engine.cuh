@@ -821,11 +821,13 @@ struct PendingCount {
     }
 };
 
-// Fill and store one fraction of the tile for the calling group (contains one group barrier).  c[] .w = validity.
+// Fill and store one fraction of the tile for the calling group (contains one group barrier; a warp without holes
+// only arrives at it unless it is warp 0, which builds the upper levels, or the group read splat keys, whose next
+// initialisation the barrier orders after every read).  c[] .w = validity.
 template <typename CT>
 __device__ __forceinline__ void fill_store_block(EngineSmem &s, const TileParams &p, const FrameDims &d, CT *oc,
                                                  uint8_t *om, int g, int kk, int tile, int buf, int TX, int TY,
-                                                 float4 c[4], const uint8_t m[4], bool vec) {
+                                                 float4 c[4], const uint8_t m[4], bool vec, bool keys) {
     const int tg = threadIdx.x & (kGroupThreads - 1);
     const int lane = tg & 31, w = tg >> 5;
     const float4 n1 = mean4(c[0], c[1], c[2], c[3]);
@@ -833,8 +835,24 @@ __device__ __forceinline__ void fill_store_block(EngineSmem &s, const TileParams
     const float4 n2o = mean4(n1, a1, a16, a17);  // meaningful on lanes with even block x and even block y
     float4 *l2 = s.l2[g][buf];
     if ((lane & 17) == 0) l2[w * 8 + (lane >> 1)] = n2o;
-    const float4 n2 = shfl4_idx(n2o, lane & ~17);
+    const bool holes = __any_sync(0xFFFFFFFFu, (m[0] | m[1] | m[2] | m[3]) != 0);  // in the warp's rows
+    const bool all[4] = {true, true, true, true};
+    if (!holes && w != 0 && !keys) {  // needs no upper level; no other warp of the group still reads keys
+        asm volatile("bar.arrive %0, %1;" ::"r"(2 + g), "r"(kGroupThreads) : "memory");
+        store_block<CT>(d, oc, om, TX, TY, c, m, all, vec);
+        return;
+    }
     bar_sync(2 + g, kGroupThreads);
+    if (!holes) {
+        if (w == 0) {
+            float4 l3, l4, l5;
+            upper_levels(l2, l3, l4, l5);
+            if (lane == 0) publish_node(p, l5, kk, tile);
+        }
+        store_block<CT>(d, oc, om, TX, TY, c, m, all, vec);
+        return;
+    }
+    const float4 n2 = shfl4_idx(n2o, lane & ~17);
     bool deep = false;  // a hole whose level-1 and level-2 ancestors are both invalid
 #pragma unroll
     for (int t = 0; t < 4; ++t) deep = deep || (m[t] != 0 && n1.w == 0.0f && n2.w == 0.0f);
@@ -1068,7 +1086,7 @@ __device__ __forceinline__ void tile_group(EngineSmem &s, const TileSlot &sl, in
         }
     }
     if (FILL) {
-        fill_store_block<CT>(s, p, d, oc, om, g, kk, tile, buf, TX, TY, c, m, vec);
+        fill_store_block<CT>(s, p, d, oc, om, g, kk, tile, buf, TX, TY, c, m, vec, mode >= 1 && mode <= 3);
     } else {
         const bool all[4] = {true, true, true, true};
         store_block<CT>(d, oc, om, TX, TY, c, m, all, vec);

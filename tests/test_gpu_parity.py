@@ -205,6 +205,32 @@ def test_tma_staging_modes_cover_all_tiles(b):
         np.testing.assert_allclose(out[j].cpu().numpy(), wo, rtol=0, atol=2e-6)
 
 
+@pytest.mark.parametrize("dtype", [np.float32, np.float16])
+def test_fast_motion_mixed_staging(b, dtype):
+    # motion up to 16 pixels in every direction: the sources of most tiles overflow a staging window and are read
+    # from global memory; a slow band keeps ordinary windows, a fast block lands far from its sources
+    W, H = 264, 200
+    color, depth, mv = scenes.random_frame(W, H, 21, mv_scale=16.0)
+    mv[:, :40, :] *= 0.125
+    mv[:, 60:80, 40:72] = np.float32(70.0)
+    color = color.astype(dtype)
+    c, d, m = dev(color), dev(depth), dev(mv)
+    ws = b.workspace(b.exw_workspace_bytes(b.OP_EXTRAPOLATE, W, H, b.F16 if dtype == np.float16 else b.F32, 1, 3),
+                     c.device)
+    tol = 1e-3 if dtype == np.float16 else 2e-6
+    iv = torch.int16 if dtype == np.float16 else torch.int32
+    for fill in (True, False):
+        out, mask = b.exw_extrapolate(c, d, m, fill=fill, ws=ws)
+        st = b.frame_stats(ws)
+        assert st["tiles_window_all"] > 0 and st["tiles_global"] + st["tiles_window_each"] > 0
+        out2, mask2 = b.exw_extrapolate(c, d, m, fill=fill, tma=False)
+        assert torch.equal(mask, mask2) and torch.equal(out.view(iv), out2.view(iv))
+        ref = oracle.extrapolate(color.astype(np.float64), depth, mv, 3, fill=fill, storage=dtype)
+        for j, (wo, wm, _) in enumerate(ref):
+            np.testing.assert_array_equal(mask[j].cpu().numpy(), wm)
+            np.testing.assert_allclose(out[j].cpu().numpy().astype(np.float64), wo, rtol=0, atol=tol)
+
+
 @pytest.mark.parametrize("pan", [(1.3, -0.7), (-2.6, 0.0), (0.0, 1.9), (0.5, 0.5), (4.0, -8.0), (0.0, 0.0),
                                  (-0.25, -3.75)])
 @pytest.mark.parametrize("dtype", [np.float32, np.float16])
