@@ -18,7 +18,7 @@ __global__ void __launch_bounds__(kEngineThreads, 1) engine_kernel(const __grid_
     }
     __syncthreads();
     if (threadIdx.x >= kConsumerThreads) engine_producer(s, ep);
-    else engine_consumer<FILL>(s);
+    else engine_consumer<FILL>(s, ep.status);
 }
 
 cudaError_t launch_engine(const EngineParams &ep, bool fill, int grid, cudaStream_t s) {

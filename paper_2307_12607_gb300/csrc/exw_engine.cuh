@@ -279,6 +279,10 @@ __device__ inline void engine_producer(EngineSmem &s, const EngineParams &ep) {
             if (lane == 0) {
                 atomicCAS(ep.status, 0u, (uint32_t)EXW_ERR_TIMEOUT);
                 *(volatile int *)&s.abort = 1;
+                // the CTA must not end while a window it requested is still landing in its shared memory: wait
+                // (bounded) for the last two slots handed over, whose copies the consumers may not have waited for
+                for (uint32_t j = i >= 2u ? i - 2u : 0u; j < i; ++j)
+                    mbar_wait_bounded(&s.full[j & 1u], (j >> 1) & 1u, kWaitLimit);
             }
             return;
         }
@@ -547,13 +551,13 @@ __device__ __forceinline__ Rect plan_union(const TilePlan &pl, int nfrac) {
 
 // A candidate 8 x 8 source tile of a splat: the fractions whose landing rectangle meets R and, for a clean tile
 // (one exact motion, every pixel can land), its whole-pixel offsets per fraction.
-struct SplatTile {
+struct alignas(16) SplatTile {
     uint16_t bx, by;
     uint8_t fm, clean;
     int8_t ox[kMaxFrac], oy[kMaxFrac];
     int8_t pad[2];
 };
-static_assert(sizeof(SplatTile) == 14 || sizeof(SplatTile) == 16, "compact");
+static_assert(sizeof(SplatTile) == 16, "one load per descriptor");
 constexpr int kMaxSplatTiles = (int)(sizeof(uint32_t) * kConsumerThreads / sizeof(SplatTile));
 
 // Describe the 8 x 8 source tiles overlapping rectangle U (all consumer threads, no barrier).  Returns the count.
@@ -567,8 +571,8 @@ __device__ __forceinline__ int describe_tiles(SplatTile *out, const TileParams &
         st.bx = (uint16_t)bx;
         st.by = (uint16_t)by;
         const float4 b = __ldcg(p.tile_bounds + (size_t)by * p.nbx + bx);
+        const float2 dr = __ldcg(p.tile_depth + (size_t)by * p.nbx + bx);  // issued with the bounds
         if (b.x <= b.y) {
-            const float2 dr = __ldcg(p.tile_depth + (size_t)by * p.nbx + bx);
             const bool uni = b.x == b.y && b.z == b.w;
             uint32_t fm = 0;
             for (int kk = 0; kk < d.nfrac; ++kk) {
@@ -597,13 +601,12 @@ __device__ __forceinline__ void engine_splat_window(EngineSmem &s, const TilePar
     SplatTile *tiles = reinterpret_cast<SplatTile *>(s.cand);
     const int nt = describe_tiles(tiles, p, d, U, RX0, RY0, tid);
     bar_sync(kBarConsumers, kConsumerThreads);
-    const int lane = tid & 31, wid = tid >> 5;
-    for (int t = wid; t < nt; t += kConsumerWarps) {
-        const SplatTile st = tiles[t];
+    // half a source tile per warp and round (its descriptor is one broadcast load), all warps busy
+    for (int q = tid; q < 64 * nt; q += kConsumerThreads) {
+        const SplatTile st = tiles[q >> 6];
         if (!st.fm) continue;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int x = 8 * st.bx + (lane & 7), y = 8 * st.by + (lane >> 3) + 4 * h;
+        {
+            const int x = 8 * st.bx + (q & 7), y = 8 * st.by + ((q >> 3) & 7);
             if (x < U.x0 || x > U.x1 || y < U.y0 || y > U.y1) continue;
             const int i = a.at(x, y);
             const uint32_t db = __float_as_uint(a.w->depth[i]);
@@ -1117,7 +1120,7 @@ struct HalfGroupBarrier {  // the 4 warps of half group h: named barrier 5 + h
 };
 
 template <bool FILL>
-__device__ void engine_consumer(EngineSmem &s) {
+__device__ void engine_consumer(EngineSmem &s, uint32_t *status) {
     const int tid = threadIdx.x;  // 0 .. 767
     const int g = tid >> 8, tg = tid & (kGroupThreads - 1);
     const int lane = tid & 31, w = tid >> 5;
@@ -1153,8 +1156,8 @@ __device__ void engine_consumer(EngineSmem &s) {
         if (ok && mode >= 1 && mode <= 3 && g < p.nfrac)
             for (int r = tg; r < kRegionN; r += kGroupThreads) s.key[g][r] = kKeyEmpty;
         if (bar_red_or(kBarConsumers, kConsumerThreads, !ok)) {
-            if (tid == 0) {
-                atomicCAS(sl.p.status, 0u, (uint32_t)EXW_ERR_TIMEOUT);
+            if (tid == 0) {  // (the slot may never have been written: its parameters are not used here)
+                atomicCAS(status, 0u, (uint32_t)EXW_ERR_TIMEOUT);
                 *(volatile int *)&s.abort = 1;
             }
             return;
