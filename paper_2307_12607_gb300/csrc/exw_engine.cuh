@@ -64,7 +64,7 @@ struct EngineParams {
 };
 
 // Per-fraction constants of a uniform tile (computed by the producer).
-struct UniformFrac {
+struct alignas(16) UniformFrac {  // 16-byte aligned: its fields load as vectors
     int ox, oy;               // whole-pixel offset o_k
     uint32_t flags;           // kTapX, kTapY: a tap column / row exists; kMirX, kMirY: taps at -1; kInterior
     float W00, W10, W01, W11; // bilinear weights, constant over the tile
@@ -80,7 +80,7 @@ struct FrameDims {
 __device__ __forceinline__ FrameDims dims_of(const TileParams &p) { return FrameDims{p.W, p.H, p.L, p.k0, p.nfrac}; }
 
 // What the producer hands the consumers with each buffer.
-struct TileSlot {
+struct alignas(16) TileSlot {
     TileParams p;             // the item's stream
     int kind, stream, index, cdt;
     TilePlan plan;            // tile: its plan (mode 3 for every tile of a stream without TMA windows)

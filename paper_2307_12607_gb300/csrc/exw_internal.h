@@ -29,7 +29,7 @@ struct FrameHeader {
 static_assert(sizeof(FrameHeader) == 128, "FrameHeader is 128 bytes");
 
 // Per target tile, how the fused pass stages its sources (written by the plan kernel).
-struct TilePlan {
+struct alignas(16) TilePlan {
     int mode;          // 0 uniform motion, 1 one window, 2 one window per fraction, 3 global memory, 4 nothing
                        // lands, 5 uniform motion over smooth valid sources (every pixel a winner, every tap agrees)
     int wx0, wy0;      // window origin (modes 0 and 1)
@@ -92,7 +92,7 @@ inline WsLayout ws_layout(int W, int H, int nframes, int nfrac, bool with_keys) 
 }
 
 // Parameters of the per-tile passes (stage (b)+(c) on 32 x 32 tiles).
-struct TileParams {
+struct alignas(16) TileParams {
     const void *color;          // source colour (fused/warp) or in-out colour (fill)
     const float *depth;
     const float *mv;
