@@ -31,7 +31,8 @@ constexpr int kGroupThreads = 256;                          // one fraction: 16 
 constexpr int kConsumerThreads = kMaxFrac * kGroupThreads;  // 768
 constexpr int kConsumerWarps = kConsumerThreads / 32;       // 24
 constexpr int kEngineThreads = kConsumerThreads + 32;       // + the producer warp
-constexpr int kBarConsumers = 1;                            // named barriers: 1 all consumers, 2 + g group g
+constexpr int kBarConsumers = 1;                            // named barriers: 1 all consumers, 2 + g group g,
+constexpr int kBarPair = 11;                                // 11 + g group g on a paired smooth tile
 constexpr int kMaxStreams = 48;                             // streams per launch (kernel-parameter space)
 constexpr int kRegionsPerItem = 2 * kMaxFrac;               // a bounds item: one region per half group (4 warps)
 constexpr int kPlansPerItem = kConsumerWarps;               // a plan item: one tile per consumer warp
@@ -87,6 +88,10 @@ struct alignas(16) TileSlot {
     int X0, Y0;
     Rect N;                   // modes 0, 5: the source rectangle the fractions read
     UniformFrac u[kMaxFrac];  // modes 0, 5
+    // mode 5: a second smooth tile of the same stream, the next in the queue, shares the slot (its colour window
+    // follows the first one's in the buffer)
+    int pair, index2, X02, Y02, wx02, wy02;
+    UniformFrac u2[kMaxFrac];
 };
 
 constexpr int kWindowBytes = 64512;  // both window shapes (56 x 48 FP32, 64 x 56 FP16) hold 64,512 bytes
@@ -303,7 +308,8 @@ __device__ inline void engine_producer(EngineSmem &s, const EngineParams &ep) {
             else copied0 = stream;
         }
         const int kind = stage == 0 ? kSlotBounds : stage == 1 ? kSlotPlans : stage == 2 ? kSlotTile : kSlotFixup;
-        int mode = -1, wx0 = 0, wy0 = 0;
+        int mode = -1, wx0 = 0, wy0 = 0, wx02 = 0, wy02 = 0;
+        bool pair = false;
         if (kind == kSlotTile) {
             if (!have_word) word = lane < kWords ? __ldcg(reinterpret_cast<const int *>(p.plans + local) + lane) : 0;
             if (lane < kWords) reinterpret_cast<int *>(&sl.plan)[lane] = word;
@@ -318,10 +324,30 @@ __device__ inline void engine_producer(EngineSmem &s, const EngineParams &ep) {
                 if (lane < 8 * p.nfrac) uniform_frac(sl.u[lane >> 3], p, umx, umy, lane >> 3, X0 - 1, Y0 - 1, lane & 7);
                 if (lane == 0) sl.N = uniform_sources(p, umx, umy, X0 - 1, Y0 - 1);
             }
+            // two smooth tiles in a row (the second one's plan already read): one slot, one pass of the pipeline
+            pair = mode == 5 && nhave && nxt.stream == stream && nxt.stage == 2 &&
+                   __shfl_sync(0xFFFFFFFFu, nword, 0) == 5;
+            if (pair) {
+                const int X02 = (nxt.local % p.n5x) * kFillTile, Y02 = (nxt.local / p.n5x) * kFillTile;
+                const uint32_t umx = (uint32_t)__shfl_sync(0xFFFFFFFFu, nword, 16);
+                const uint32_t umy = (uint32_t)__shfl_sync(0xFFFFFFFFu, nword, 17);
+                wx02 = __shfl_sync(0xFFFFFFFFu, nword, 1);
+                wy02 = __shfl_sync(0xFFFFFFFFu, nword, 2);
+                if (lane < 8 * p.nfrac)
+                    uniform_frac(sl.u2[lane >> 3], p, umx, umy, lane >> 3, X02 - 1, Y02 - 1, lane & 7);
+                if (lane == 0) {
+                    sl.index2 = nxt.local;
+                    sl.X02 = X02;
+                    sl.Y02 = Y02;
+                    sl.wx02 = wx02;
+                    sl.wy02 = wy02;
+                }
+            }
             if (lane == 0) {
                 sl.plan.mode = mode;
                 sl.X0 = X0;
                 sl.Y0 = Y0;
+                sl.pair = pair ? 1 : 0;
             }
         }
         __syncwarp();
@@ -330,16 +356,17 @@ __device__ inline void engine_producer(EngineSmem &s, const EngineParams &ep) {
             sl.stream = stream;
             sl.index = local;
             sl.cdt = st.cdt;
-            if (kind == kSlotTile) atomicAdd(&p.fh->nmode[mode], 1u);
+            if (kind == kSlotTile) atomicAdd(&p.fh->nmode[mode], pair ? 2u : 1u);
             const CUtensorMap *m = ep.maps[stream];
             unsigned char *wb = s.win[b];
             // a window holds npx pixels: depth (4 B), motion (8 B), colour (3 c B) planes in this order
             const int npx = st.cdt == EXW_F16 ? kWinXF16 * kWinYF16 : kWinXF32 * kWinYF32;
             const uint32_t cbytes = (uint32_t)npx * 3u * (st.cdt == EXW_F16 ? 2u : 4u);
-            if (kind == kSlotTile && mode == 5) {  // smooth: only the colour is read
+            if (kind == kSlotTile && mode == 5) {  // smooth: only the colour is read, at the buffer's start
                 fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&s.full[b], cbytes);
-                tma_load_3d(wb + 12 * npx, &m[0], wx0, wy0, 0, &s.full[b]);
+                mbar_arrive_expect_tx(&s.full[b], pair ? 2u * cbytes : cbytes);
+                tma_load_3d(wb, &m[0], wx0, wy0, 0, &s.full[b]);
+                if (pair) tma_load_3d(wb + cbytes, &m[0], wx02, wy02, 0, &s.full[b]);
             } else if (kind == kSlotTile && (mode == 0 || mode == 1)) {
                 fence_proxy_async_smem();
                 mbar_arrive_expect_tx(&s.full[b], (uint32_t)kWindowBytes);
@@ -350,9 +377,15 @@ __device__ inline void engine_producer(EngineSmem &s, const EngineParams &ep) {
                 mbar_arrive(&s.full[b]);
             }
         }
-        cur = nxt;
-        word = nword;
-        have_word = nhave;
+        if (pair) {  // the second tile is taken: the item after it comes next
+            cur = decode(ep, __shfl_sync(0xFFFFFFFFu, qb, 0), seg);
+            if (lane == 0 && cur.item < ep.total) qb = (int)atomicAdd(ep.queue, 1u);
+            have_word = false;
+        } else {
+            cur = nxt;
+            word = nword;
+            have_word = nhave;
+        }
     }
 }
 
@@ -938,8 +971,8 @@ __device__ inline void engine_coarse_pass(const TileParams &p) {
 // One column of four pixels (tile rows 4w..4w+3 of column lane; w = warp in the group): out[r] = colour of row r.
 // Lanes are consecutive columns, so every shared-memory access of a warp is conflict-free.
 template <typename CT, int WX, int WY, bool MY, bool EX, bool EY>
-__device__ __forceinline__ void smooth_column_t(const Window<CT, WX, WY> &win, int wx0, int wy0, const UniformFrac &u,
-                                                int X0, int Y0, CT out[4][3]) {
+__device__ __forceinline__ void smooth_column_t(const CT *col, int wx0, int wy0, const UniformFrac &u, int X0, int Y0,
+                                                CT out[4][3]) {
     const int tg = threadIdx.x & (kGroupThreads - 1);
     const int lane = tg & 31, w = tg >> 5;
     const int sx = EX ? ((u.flags & kMirX) ? -1 : 1) : 0;
@@ -949,7 +982,7 @@ __device__ __forceinline__ void smooth_column_t(const Window<CT, WX, WY> &win, i
     const float W00 = u.W00, W10 = u.W10, W01 = u.W01, W11 = u.W11;
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
-        const CT *cp = win.col[ch] + ry * WX + cx;
+        const CT *cp = col + ch * (WX * WY) + ry * WX + cx;
         float C[5][2];
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
@@ -969,21 +1002,22 @@ __device__ __forceinline__ void smooth_column_t(const Window<CT, WX, WY> &win, i
     }
 }
 
+// col: plane 0 of the tile's colour window (WX x WY per plane, planes consecutive).
 template <typename CT, int WX, int WY>
-__device__ __forceinline__ void smooth_column(const Window<CT, WX, WY> &win, int wx0, int wy0, const UniformFrac &u,
-                                              int X0, int Y0, CT out[4][3]) {
+__device__ __forceinline__ void smooth_column(const CT *col, int wx0, int wy0, const UniformFrac &u, int X0, int Y0,
+                                              CT out[4][3]) {
     const bool my = (u.flags & kMirY) != 0;
     switch (u.flags & (kTapX | kTapY)) {
         case kTapX | kTapY:
-            if (my) smooth_column_t<CT, WX, WY, true, true, true>(win, wx0, wy0, u, X0, Y0, out);
-            else smooth_column_t<CT, WX, WY, false, true, true>(win, wx0, wy0, u, X0, Y0, out);
+            if (my) smooth_column_t<CT, WX, WY, true, true, true>(col, wx0, wy0, u, X0, Y0, out);
+            else smooth_column_t<CT, WX, WY, false, true, true>(col, wx0, wy0, u, X0, Y0, out);
             break;
-        case kTapX: smooth_column_t<CT, WX, WY, false, true, false>(win, wx0, wy0, u, X0, Y0, out); break;
+        case kTapX: smooth_column_t<CT, WX, WY, false, true, false>(col, wx0, wy0, u, X0, Y0, out); break;
         case kTapY:
-            if (my) smooth_column_t<CT, WX, WY, true, false, true>(win, wx0, wy0, u, X0, Y0, out);
-            else smooth_column_t<CT, WX, WY, false, false, true>(win, wx0, wy0, u, X0, Y0, out);
+            if (my) smooth_column_t<CT, WX, WY, true, false, true>(col, wx0, wy0, u, X0, Y0, out);
+            else smooth_column_t<CT, WX, WY, false, false, true>(col, wx0, wy0, u, X0, Y0, out);
             break;
-        default: smooth_column_t<CT, WX, WY, false, false, false>(win, wx0, wy0, u, X0, Y0, out); break;
+        default: smooth_column_t<CT, WX, WY, false, false, false>(col, wx0, wy0, u, X0, Y0, out); break;
     }
 }
 
@@ -1012,7 +1046,7 @@ __device__ __forceinline__ void store_column(const FrameDims &p, CT *oc, uint8_t
 // warp 0, which publishes it.  The other warps only arrive at the group barrier.
 template <typename CT>
 __device__ __forceinline__ void smooth_publish(EngineSmem &s, const TileParams &p, int g, int kk, int tile, int buf,
-                                               const CT out[4][3]) {
+                                               int bar, const CT out[4][3]) {
     const int tg = threadIdx.x & (kGroupThreads - 1);
     const int lane = tg & 31, w = tg >> 5;
     float4 px[4], pp[4];
@@ -1035,10 +1069,10 @@ __device__ __forceinline__ void smooth_publish(EngineSmem &s, const TileParams &
     float4 *l2 = s.l2[g][buf];
     if ((lane & 3) == 0) l2[w * 8 + (lane >> 2)] = n2;
     if (w != 0) {
-        asm volatile("bar.arrive %0, %1;" ::"r"(2 + g), "r"(kGroupThreads) : "memory");
+        asm volatile("bar.arrive %0, %1;" ::"r"(bar), "r"(kGroupThreads) : "memory");
         return;
     }
-    bar_sync(2 + g, kGroupThreads);
+    bar_sync(bar, kGroupThreads);
     float4 l3, l4, l5;
     upper_levels(l2, l3, l4, l5);
     if (lane == 0) publish_node(p, l5, kk, tile);
@@ -1062,11 +1096,18 @@ __device__ __forceinline__ void tile_group(EngineSmem &s, const TileSlot &sl, in
     uint8_t *om = p.out_mask[kk];
     const bool vec = (d.W % 2) == 0 && ((uintptr_t)oc % (2 * sizeof(CT))) == 0 && ((uintptr_t)om % 2) == 0;
     Window<CT, WX, WY> &win = window<CT, WX, WY>(s, b);
-    if (mode == 5) {
-        CT out[4][3];
-        smooth_column<CT, WX, WY>(win, wx0, wy0, sl.u[kk], X0, Y0, out);
-        store_column<CT>(d, oc, om, X0, Y0, out);
-        if (FILL) smooth_publish<CT>(s, p, g, kk, tile, buf, out);
+    if (mode == 5) {  // colour windows at the buffer's start: the slot's tile, then the paired one
+        const int n = sl.pair ? 2 : 1;
+#pragma unroll 1
+        for (int q = 0; q < n; ++q) {  // one copy of the code for both tiles
+            const CT *col = reinterpret_cast<const CT *>(s.win[b]) + q * 3 * WX * WY;
+            const int x0 = q ? sl.X02 : X0, y0 = q ? sl.Y02 : Y0;
+            CT out[4][3];
+            smooth_column<CT, WX, WY>(col, q ? sl.wx02 : wx0, q ? sl.wy02 : wy0, q ? sl.u2[kk] : sl.u[kk], x0, y0,
+                                      out);
+            store_column<CT>(d, oc, om, x0, y0, out);
+            if (FILL) smooth_publish<CT>(s, p, g, kk, q ? sl.index2 : tile, buf ^ q, q ? kBarPair + g : 2 + g, out);
+        }
         return;
     }
     float4 c[4];
@@ -1206,7 +1247,10 @@ __device__ void engine_consumer(EngineSmem &s, uint32_t *status) {
             if (g < p.nfrac) {
                 if (sl.cdt == EXW_F16) tile_group<__half, kWinXF16, kWinYF16, FILL>(s, sl, b, g, (int)(i & 1u));
                 else tile_group<float, kWinXF32, kWinYF32, FILL>(s, sl, b, g, (int)(i & 1u));
-                if (FILL && tg == 0) pend.add(p.fh);
+                if (FILL && tg == 0) {
+                    pend.add(p.fh);
+                    if (mode == 5 && sl.pair) pend.add(p.fh);
+                }
             }
             if (mode == 0) fence_proxy_async_smem();  // generic writes to the window before the next TMA into it
         }
