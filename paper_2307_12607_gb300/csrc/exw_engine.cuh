@@ -67,11 +67,11 @@ struct EngineParams {
 // Per-fraction constants of a uniform tile (computed by the producer).
 struct alignas(16) UniformFrac {  // 16-byte aligned: its fields load as vectors
     int ox, oy;               // whole-pixel offset o_k
-    uint32_t flags;           // kTapX, kTapY: a tap column / row exists; kMirX, kMirY: taps at -1; kInterior
+    uint32_t flags;           // kTapX, kTapY: a tap column / row exists; kMirX, kMirY: taps at -1
     float W00, W10, W01, W11; // bilinear weights, constant over the tile
     float inv[8];             // 1 / (sum of the weights of tap subset j), j = a10 | a01 << 1 | a11 << 2
 };
-constexpr uint32_t kTapX = 1u, kTapY = 2u, kMirX = 4u, kMirY = 8u, kInterior = 16u;
+constexpr uint32_t kTapX = 1u, kTapY = 2u, kMirX = 4u, kMirY = 8u;
 
 // The scalars of a stream the per-pixel code needs, held in registers for a whole tile (the slot's parameters sit
 // in shared memory, and every barrier would otherwise reload them).
@@ -160,7 +160,7 @@ __device__ __forceinline__ Rect uniform_sources(const TileParams &p, uint32_t um
 // Constants of fraction kk of a uniform tile, by the lanes 8 kk .. 8 kk + 7 of the producer warp (lane 8 kk + j
 // writes inv[j]).
 __device__ __forceinline__ void uniform_frac(UniformFrac &u, const TileParams &p, uint32_t umx, uint32_t umy, int kk,
-                                             int RX0, int RY0, int j) {
+                                             int j) {
     const int k = p.k0 + kk;
     const int ox = axis_off_of(umx, k, p.L), oy = axis_off_of(umy, k, p.L);
     int sx, sy;
@@ -171,12 +171,9 @@ __device__ __forceinline__ void uniform_frac(UniformFrac &u, const TileParams &p
     const float W00 = wx0 * wy0, W10 = wx1 * wy0, W01 = wx0 * wy1, W11 = wx1 * wy1;
     u.inv[j] = __frcp_rn(((W00 + ((j & 1) ? W10 : 0.0f)) + ((j & 2) ? W01 : 0.0f)) + ((j & 4) ? W11 : 0.0f));
     if (j == 0) {
-        const bool interior = RX0 >= 0 && RY0 >= 0 && RX0 + kRegion <= p.W && RY0 + kRegion <= p.H &&
-                              RX0 - ox >= 0 && RY0 - oy >= 0 && RX0 + kRegion - ox <= p.W && RY0 + kRegion - oy <= p.H;
         u.ox = ox;
         u.oy = oy;
-        u.flags = (sx != 0 ? kTapX : 0u) | (sy != 0 ? kTapY : 0u) | (sx < 0 ? kMirX : 0u) | (sy < 0 ? kMirY : 0u) |
-                  (interior ? kInterior : 0u);
+        u.flags = (sx != 0 ? kTapX : 0u) | (sy != 0 ? kTapY : 0u) | (sx < 0 ? kMirX : 0u) | (sy < 0 ? kMirY : 0u);
         u.W00 = W00;
         u.W10 = W10;
         u.W01 = W01;
@@ -321,7 +318,7 @@ __device__ inline void engine_producer(EngineSmem &s, const EngineParams &ep) {
             if (mode == 0 || mode == 5) {
                 const uint32_t umx = (uint32_t)__shfl_sync(0xFFFFFFFFu, word, 16);
                 const uint32_t umy = (uint32_t)__shfl_sync(0xFFFFFFFFu, word, 17);
-                if (lane < 8 * p.nfrac) uniform_frac(sl.u[lane >> 3], p, umx, umy, lane >> 3, X0 - 1, Y0 - 1, lane & 7);
+                if (lane < 8 * p.nfrac) uniform_frac(sl.u[lane >> 3], p, umx, umy, lane >> 3, lane & 7);
                 if (lane == 0) sl.N = uniform_sources(p, umx, umy, X0 - 1, Y0 - 1);
             }
             // two smooth tiles in a row (the second one's plan already read): one slot, one pass of the pipeline
@@ -334,7 +331,7 @@ __device__ inline void engine_producer(EngineSmem &s, const EngineParams &ep) {
                 wx02 = __shfl_sync(0xFFFFFFFFu, nword, 1);
                 wy02 = __shfl_sync(0xFFFFFFFFu, nword, 2);
                 if (lane < 8 * p.nfrac)
-                    uniform_frac(sl.u2[lane >> 3], p, umx, umy, lane >> 3, X02 - 1, Y02 - 1, lane & 7);
+                    uniform_frac(sl.u2[lane >> 3], p, umx, umy, lane >> 3, lane & 7);
                 if (lane == 0) {
                     sl.index2 = nxt.local;
                     sl.X02 = X02;
@@ -440,9 +437,10 @@ __device__ __forceinline__ void build_source_words(Window<CT, WX, WY> &w, int wx
 
 // One 2 x 2 block of a uniform tile for one fraction.  The block's cells are addressed in a frame mirrored so that
 // the taps lie at +1 in x and y: mirrored column j <-> source column SX + c(j), c(j) = MX ? 2 - j : j - 1 (rows
-// likewise), pixels at j, i in {1, 2}.  EDGE adds the frame checks of tiles near the border (and keeps every
-// shared-memory index inside the window).  Results c[], m[] are in true pixel order (dy * 2 + dx).
-template <typename CT, int WX, int WY, bool EDGE, bool MX, bool MY>
+// likewise), pixels at j, i in {1, 2}.  Frame checks for tiles near the border (one code path for every tile:
+// the kernel is sensitive to its instruction footprint); every shared-memory index stays inside the window.
+// Results c[], m[] are in true pixel order (dy * 2 + dx).
+template <typename CT, int WX, int WY, bool MX, bool MY>
 __device__ __forceinline__ void uniform_block(const Window<CT, WX, WY> &w, int wx0, int wy0, const FrameDims &p,
                                               const UniformFrac &u, int TX, int TY, float4 c[4], uint8_t m[4]) {
     const int SX = TX - u.ox, SY = TY - u.oy;
@@ -467,7 +465,7 @@ __device__ __forceinline__ void uniform_block(const Window<CT, WX, WY> &w, int w
     // validated word of a target cell: the source word if it is a winner, else all ones
     auto D = [&](uint32_t v, int i, int j) -> uint32_t {
         const uint32_t x = v | (uint32_t)((int32_t)v >> 31);
-        return (!EDGE || (fc[j] && fr[i])) ? x : 0xFFFFFFFFu;
+        return (fc[j] && fr[i]) ? x : 0xFFFFFFFFu;
     };
     const uint32_t v01 = V(0, 1), v02 = V(0, 2);
     const uint32_t v10 = V(1, 0), v11 = V(1, 1), v12 = V(1, 2), v13 = V(1, 3);
@@ -495,12 +493,12 @@ __device__ __forceinline__ void uniform_block(const Window<CT, WX, WY> &w, int w
         sel[q] = (a10 ? 1 : 0) | (a01 ? 2 : 0) | (a11 ? 4 : 0);
     };
     const bool tx = (u.flags & kTapX) != 0, ty = (u.flags & kTapY) != 0;
-    const bool ex2 = tx && (!EDGE || sc[2]), ex3 = tx && (!EDGE || sc[3]);
-    const bool ey2 = ty && (!EDGE || sr[2]), ey3 = ty && (!EDGE || sr[3]);
-    decide(0, d11, d10, d12, d01, d21, v12, v21, v22, !EDGE || (tc[1] && tr[1]), ex2, ey2);
-    decide(1, d12, d11, d13, d02, d22, v13, v22, v23, !EDGE || (tc[2] && tr[1]), ex3, ey2);
-    decide(2, d21, d20, d22, d11, d31, v22, v31, v32, !EDGE || (tc[1] && tr[2]), ex2, ey3);
-    decide(3, d22, d21, d23, d12, d32, v23, v32, v33, !EDGE || (tc[2] && tr[2]), ex3, ey3);
+    const bool ex2 = tx && sc[2], ex3 = tx && sc[3];
+    const bool ey2 = ty && sr[2], ey3 = ty && sr[3];
+    decide(0, d11, d10, d12, d01, d21, v12, v21, v22, tc[1] && tr[1], ex2, ey2);
+    decide(1, d12, d11, d13, d02, d22, v13, v22, v23, tc[2] && tr[1], ex3, ey2);
+    decide(2, d21, d20, d22, d11, d31, v22, v31, v32, tc[1] && tr[2], ex2, ey3);
+    decide(3, d22, d21, d23, d12, d32, v23, v32, v33, tc[2] && tr[2], ex3, ey3);
     float inv[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) inv[q] = u.inv[sel[q]];
@@ -535,15 +533,15 @@ __device__ __forceinline__ void uniform_block(const Window<CT, WX, WY> &w, int w
     }
 }
 
-template <typename CT, int WX, int WY, bool EDGE>
+template <typename CT, int WX, int WY>
 __device__ __forceinline__ void uniform_block_any(const Window<CT, WX, WY> &w, int wx0, int wy0, const FrameDims &p,
                                                   const UniformFrac &u, int TX, int TY, float4 c[4], uint8_t m[4]) {
     if (u.flags & kMirX) {
-        if (u.flags & kMirY) uniform_block<CT, WX, WY, EDGE, true, true>(w, wx0, wy0, p, u, TX, TY, c, m);
-        else uniform_block<CT, WX, WY, EDGE, true, false>(w, wx0, wy0, p, u, TX, TY, c, m);
+        if (u.flags & kMirY) uniform_block<CT, WX, WY, true, true>(w, wx0, wy0, p, u, TX, TY, c, m);
+        else uniform_block<CT, WX, WY, true, false>(w, wx0, wy0, p, u, TX, TY, c, m);
     } else {
-        if (u.flags & kMirY) uniform_block<CT, WX, WY, EDGE, false, true>(w, wx0, wy0, p, u, TX, TY, c, m);
-        else uniform_block<CT, WX, WY, EDGE, false, false>(w, wx0, wy0, p, u, TX, TY, c, m);
+        if (u.flags & kMirY) uniform_block<CT, WX, WY, false, true>(w, wx0, wy0, p, u, TX, TY, c, m);
+        else uniform_block<CT, WX, WY, false, false>(w, wx0, wy0, p, u, TX, TY, c, m);
     }
 }
 
@@ -911,7 +909,9 @@ __device__ __forceinline__ void fill_store_block(EngineSmem &s, const TileParams
 }
 
 // Coarse levels of the pyramid and the value of every tile without a valid pixel (all consumer threads).
-__device__ inline void engine_coarse_pass(const TileParams &p) {
+// (Not inlined, like the fix-up slice: the engine's throughput depends on how compact the code of its frequent
+// items stays in the instruction cache.)
+static __device__ __noinline__ void engine_coarse_pass(const TileParams &p) {
     const int tid = threadIdx.x, nt = kConsumerThreads;
     const int n5 = p.n5x * p.n5y;
     for (int kk = 0; kk < p.nfrac; ++kk) {
@@ -1114,8 +1114,7 @@ __device__ __forceinline__ void tile_group(EngineSmem &s, const TileSlot &sl, in
     uint8_t m[4];
     if (mode == 0) {
         const UniformFrac &u = sl.u[kk];
-        if (u.flags & kInterior) uniform_block_any<CT, WX, WY, false>(win, wx0, wy0, d, u, TX, TY, c, m);
-        else uniform_block_any<CT, WX, WY, true>(win, wx0, wy0, d, u, TX, TY, c, m);
+        uniform_block_any<CT, WX, WY>(win, wx0, wy0, d, u, TX, TY, c, m);
     } else if (mode == 1) {
         const WinAcc<CT, WX, WY> wa{&win, wx0, wy0};
         gather_block<CT>(s.key[kk], wa, d, k, TX, TY, bx, by, c, m);

@@ -227,7 +227,7 @@ __device__ inline void plan_tile(const TileParams &p, int tile) {  // called by 
 // Fix-up of the tiles without a valid pixel: the calling threads (tid of nt) take list entries first,
 // first + stride, ...
 template <typename CT>
-__device__ void fixup_slice(const TileParams &p, uint32_t first, uint32_t stride, int tid, int nt) {
+__device__ __noinline__ void fixup_slice(const TileParams &p, uint32_t first, uint32_t stride, int tid, int nt) {
     const int n5 = p.n5x * p.n5y;
     const size_t plane = (size_t)p.W * p.H;
     for (int kk = 0; kk < p.nfrac; ++kk) {
