@@ -437,12 +437,13 @@ __device__ __forceinline__ void build_source_words(Window<CT, WX, WY> &w, int wx
 
 // One 2 x 2 block of a uniform tile for one fraction.  The block's cells are addressed in a frame mirrored so that
 // the taps lie at +1 in x and y: mirrored column j <-> source column SX + c(j), c(j) = MX ? 2 - j : j - 1 (rows
-// likewise), pixels at j, i in {1, 2}.  Frame checks for tiles near the border (one code path for every tile:
+// likewise), pixels at j, i in {1, 2}; the mirror flags are runtime values (one code copy for the four cases).  Frame checks for tiles near the border (one code path for every tile:
 // the kernel is sensitive to its instruction footprint); every shared-memory index stays inside the window.
 // Results c[], m[] are in true pixel order (dy * 2 + dx).
-template <typename CT, int WX, int WY, bool MX, bool MY>
+template <typename CT, int WX, int WY>
 __device__ __forceinline__ void uniform_block(const Window<CT, WX, WY> &w, int wx0, int wy0, const FrameDims &p,
                                               const UniformFrac &u, int TX, int TY, float4 c[4], uint8_t m[4]) {
+    const bool MX = (u.flags & kMirX) != 0, MY = (u.flags & kMirY) != 0;
     const int SX = TX - u.ox, SY = TY - u.oy;
     int cidx[4], ridx[4];
     bool fc[4], fr[4], sc[4], sr[4], tc[4], tr[4];
@@ -523,26 +524,25 @@ __device__ __forceinline__ void uniform_block(const Window<CT, WX, WY> &w, int w
             out[q][ch] = ok[q] ? storage_round<CT>(n * inv[q]) : 0.0f;
         }
     }
-    // mirrored pixel q = (i, j) -> true pixel (MY ? 1 - i : i, MX ? 1 - j : j)
+    // true pixel t = (ti, tj) <- mirrored pixel (MY ? 1 - ti : ti, MX ? 1 - tj : tj), by selects
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int i = q >> 1, j = q & 1;
-        const int t = ((MY ? 1 - i : i) << 1) | (MX ? 1 - j : j);
-        c[t] = make_float4(out[q][0], out[q][1], out[q][2], ok[q] ? 1.0f : 0.0f);
-        m[t] = mk[q];
+    for (int t = 0; t < 4; ++t) {
+        const int ti = t >> 1, tj = t & 1;
+        const int qa = ((ti) << 1) | (tj), qx = ((ti) << 1) | (1 - tj), qy = ((1 - ti) << 1) | (tj),
+                  qxy = ((1 - ti) << 1) | (1 - tj);
+        auto pick = [&](auto v0, auto vx, auto vy, auto vxy) { return MY ? (MX ? vxy : vy) : (MX ? vx : v0); };
+        c[t] = make_float4(pick(out[qa][0], out[qx][0], out[qy][0], out[qxy][0]),
+                           pick(out[qa][1], out[qx][1], out[qy][1], out[qxy][1]),
+                           pick(out[qa][2], out[qx][2], out[qy][2], out[qxy][2]),
+                           pick(ok[qa], ok[qx], ok[qy], ok[qxy]) ? 1.0f : 0.0f);
+        m[t] = pick(mk[qa], mk[qx], mk[qy], mk[qxy]);
     }
 }
 
 template <typename CT, int WX, int WY>
 __device__ __forceinline__ void uniform_block_any(const Window<CT, WX, WY> &w, int wx0, int wy0, const FrameDims &p,
                                                   const UniformFrac &u, int TX, int TY, float4 c[4], uint8_t m[4]) {
-    if (u.flags & kMirX) {
-        if (u.flags & kMirY) uniform_block<CT, WX, WY, true, true>(w, wx0, wy0, p, u, TX, TY, c, m);
-        else uniform_block<CT, WX, WY, true, false>(w, wx0, wy0, p, u, TX, TY, c, m);
-    } else {
-        if (u.flags & kMirY) uniform_block<CT, WX, WY, false, true>(w, wx0, wy0, p, u, TX, TY, c, m);
-        else uniform_block<CT, WX, WY, false, false>(w, wx0, wy0, p, u, TX, TY, c, m);
-    }
+    uniform_block<CT, WX, WY>(w, wx0, wy0, p, u, TX, TY, c, m);
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -1041,12 +1041,16 @@ __device__ __forceinline__ void store_column(const FrameDims &p, CT *oc, uint8_t
     }
 }
 
+__device__ __forceinline__ void smooth_tail(EngineSmem &s, const TileParams &p, int g, int kk, int tile, int buf,
+                                            int bar);
+
 // Level-5 node of a tile whose pixels are all valid, from columns of four pixels (same pyramid as mean4 over
 // valid children): levels 1 and 2 by shuffles, the level-2 row of each warp to shared memory, levels 3-5 by
-// warp 0, which publishes it.  The other warps only arrive at the group barrier.
+// warp tw, which publishes it (defer: warp tw only arrives; it builds the levels later, by smooth_tail).  The
+// other warps only arrive at the group barrier.
 template <typename CT>
 __device__ __forceinline__ void smooth_publish(EngineSmem &s, const TileParams &p, int g, int kk, int tile, int buf,
-                                               int bar, const CT out[4][3]) {
+                                               int bar, int tw, bool defer, const CT out[4][3]) {
     const int tg = threadIdx.x & (kGroupThreads - 1);
     const int lane = tg & 31, w = tg >> 5;
     float4 px[4], pp[4];
@@ -1068,14 +1072,20 @@ __device__ __forceinline__ void smooth_publish(EngineSmem &s, const TileParams &
     const float4 n2 = right ? mean4(Ap, A, Bp, B) : mean4(A, Ap, B, Bp);
     float4 *l2 = s.l2[g][buf];
     if ((lane & 3) == 0) l2[w * 8 + (lane >> 2)] = n2;
-    if (w != 0) {
+    if (w != tw) {
         asm volatile("bar.arrive %0, %1;" ::"r"(bar), "r"(kGroupThreads) : "memory");
         return;
     }
+    if (!defer) smooth_tail(s, p, g, kk, tile, buf, bar);
+}
+
+// Levels 3-5 and the node of a smooth tile once every warp of the group has left its level-2 row (one warp).
+__device__ __forceinline__ void smooth_tail(EngineSmem &s, const TileParams &p, int g, int kk, int tile, int buf,
+                                            int bar) {
     bar_sync(bar, kGroupThreads);
     float4 l3, l4, l5;
-    upper_levels(l2, l3, l4, l5);
-    if (lane == 0) publish_node(p, l5, kk, tile);
+    upper_levels(s.l2[g][buf], l3, l4, l5);
+    if ((threadIdx.x & 31) == 0) publish_node(p, l5, kk, tile);
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -1106,8 +1116,13 @@ __device__ __forceinline__ void tile_group(EngineSmem &s, const TileSlot &sl, in
             smooth_column<CT, WX, WY>(col, q ? sl.wx02 : wx0, q ? sl.wy02 : wy0, q ? sl.u2[kk] : sl.u[kk], x0, y0,
                                       out);
             store_column<CT>(d, oc, om, x0, y0, out);
-            if (FILL) smooth_publish<CT>(s, p, g, kk, q ? sl.index2 : tile, buf ^ q, q ? kBarPair + g : 2 + g, out);
+            // a pair: warp 0 builds the first tile's levels after its part of the second, warp 7 the second's, so
+            // the two tails overlap
+            if (FILL)
+                smooth_publish<CT>(s, p, g, kk, q ? sl.index2 : tile, buf ^ q, q ? kBarPair + g : 2 + g,
+                                   q ? kGroupThreads / 32 - 1 : 0, n == 2 && q == 0, out);
         }
+        if (FILL && n == 2 && (threadIdx.x & (kGroupThreads - 1)) < 32) smooth_tail(s, p, g, kk, tile, buf, 2 + g);
         return;
     }
     float4 c[4];
