@@ -7,8 +7,9 @@ far larger than the 129 MB L2, so no flush is needed between steps.
 
 Reported (one JSON line on rank 0):
   value       whole-job output Mpixel/s with inputs resident in HBM (device-timed with CUDA events)
-  e2e         the same through the C ABI with host buffers: pinned host -> device copies of the step's inputs,
-              the extrapolation, device -> host copies of its outputs, all inside the timed region
+  e2e         the same through the C ABI with host buffers (exw_extrapolate_host): pinned host -> device copies
+              of the step's inputs, the extrapolation and device -> host copies of its outputs, overlapped chunk by
+              chunk on three streams, all inside the timed region
   roofline    the dominant kernel's algorithmic bytes per launch / its mean event-timed duration, against the
               measured HBM copy bandwidth
   cpu_baseline the CPU oracle (FP64, single thread) on a bounded sample of the same workload
@@ -46,6 +47,7 @@ def parse():
     ap.add_argument("--impl", choices=["exw", "reference"], default="exw")
     ap.add_argument("--frames", type=int, default=NFRAMES)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-chunk", type=int, default=2, help="frames per overlapped copy/compute chunk (e2e)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
@@ -482,13 +484,9 @@ def run_exw(args):
     ho = torch.empty(out.shape, dtype=out.dtype).pin_memory()
     hmask = torch.empty(mask.shape, dtype=mask.dtype).pin_memory()
 
-    def e2e_step():
-        c.copy_(hc, non_blocking=True)
-        d.copy_(hd, non_blocking=True)
-        m.copy_(hm, non_blocking=True)
-        step()
-        ho.copy_(out, non_blocking=True)
-        hmask.copy_(mask, non_blocking=True)
+    def e2e_step():  # exw_extrapolate_host: copies in, work and copies out overlap chunk by chunk inside the call
+        b.exw_extrapolate_host(hc, hd, hm, NFRAC, True, ho, hmask, dev_in=(c, d, m), dev_out=(out, mask), ws=ws,
+                               chunk=args.e2e_chunk)
 
     e2e_step()
     torch.cuda.synchronize()

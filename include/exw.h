@@ -176,6 +176,21 @@ EXW_API exw_status exw_fill_holes_static(void *color, exw_dtype cdt, const uint8
 EXW_API exw_status exw_extrapolate(const exw_frame *frames, int nframes, int nfrac, unsigned flags, exw_frame_out *out,
                            void *ws, size_t ws_bytes, exw_stream_t stream);
 
+/* exw_extrapolate for frames held in HOST memory (Sec. IV-B, all stages), with the host <-> device copies
+ * inside the call and overlapped with the work: the frames go in chunks of `chunk` frames (0: 8); chunk j's inputs
+ * are copied in on one internal stream while chunk j - 1 is extrapolated on `stream` and chunk j - 2's outputs are
+ * copied back on another.  frames_host [nframes] and out_host [nframes * nfrac] are HOST arrays of descriptors
+ * holding host pointers (page-locked memory for the copies to overlap; any host memory works), frames_dev and
+ * out_dev the same shapes in device memory, owned by the caller and written here (staging: every frame has its
+ * own device buffers, nothing is allocated).  Workspace: exw_workspace_bytes(EXW_OP_EXTRAPOLATE, W, H, cdt,
+ * min(chunk, nframes), nfrac).  The call returns once the work is queued; when `stream` completes, the outputs are
+ * in host memory.  The internal streams and events are created at the first call on a device; calls on one device
+ * are serialised by the caller.  Errors as exw_extrapolate. */
+EXW_API exw_status exw_extrapolate_host(const exw_frame *frames_host, const exw_frame *frames_dev, int nframes,
+                                        int nfrac, unsigned flags, const exw_frame_out *out_host,
+                                        const exw_frame_out *out_dev, int chunk, void *ws, size_t ws_bytes,
+                                        exw_stream_t stream);
+
 /* Adjoint of stage (b) for fraction k/denom with every integer decision held fixed (target, winner, taps, tap
  * participation, mask).  grad_out [3][H][W] float32 = dL/d out_color; accumulates (+=) into grad_color
  * [3][H][W] float32 (dL/d colour: w_t / sum w per participating tap) and grad_mv [2][H][W] float32 (dL/d motion

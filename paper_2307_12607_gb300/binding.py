@@ -196,6 +196,56 @@ def exw_extrapolate(color, depth, mv, nfrac: int = 3, fill: bool = True, out=Non
     return out, mask
 
 
+def exw_extrapolate_host(color, depth, mv, nfrac: int = 3, fill: bool = True, out=None, mask=None, dev_in=None,
+                         dev_out=None, ws=None, chunk: int = 8, stream=None, tma: bool = True):
+    """exw_extrapolate for a sequence in HOST memory ([F][3][H][W] colour, [F][H][W] depth, [F][2][H][W] motion;
+    page-locked for the copies to overlap): the copies in, the work and the copies out run chunk by chunk on
+    three streams inside the call.  Returns host (out [F][nfrac][3][H][W], mask [F][nfrac][H][W]) once the
+    caller's stream has been synchronised.  dev_in = (colour, depth, motion) and dev_out = (out, mask): device
+    staging tensors of the same shapes (allocated here when None)."""
+    F, _, H, W = (int(v) for v in color.shape)
+    cdt = _cdt(color)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if out is None:
+        out = torch.empty((F, nfrac, 3, H, W), dtype=color.dtype).pin_memory()
+    if mask is None:
+        mask = torch.empty((F, nfrac, H, W), dtype=torch.uint8).pin_memory()
+    for t, name in ((color, "color"), (depth, "depth"), (mv, "mv"), (out, "out"), (mask, "mask")):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name}: a contiguous host tensor is expected")
+    if dev_in is None:
+        dev_in = (torch.empty_like(color, device=dev), torch.empty_like(depth, device=dev),
+                  torch.empty_like(mv, device=dev))
+    if dev_out is None:
+        dev_out = (torch.empty_like(out, device=dev), torch.empty_like(mask, device=dev))
+    dc, dd, dm = dev_in
+    do, dk = dev_out
+    _dev(dc, "dev color", color.dtype, (F, 3, H, W))
+    _dev(dd, "dev depth", torch.float32, (F, H, W))
+    _dev(dm, "dev mv", torch.float32, (F, 2, H, W))
+    _dev(do, "dev out", color.dtype, (F, nfrac, 3, H, W))
+    _dev(dk, "dev mask", torch.uint8, (F, nfrac, H, W))
+    need = exw_workspace_bytes(OP_EXTRAPOLATE, W, H, cdt, min(chunk, F) if chunk > 0 else min(8, F), nfrac)
+    if ws is None:
+        ws = workspace(need, dev)
+    fh = (_lib.ExwFrame * F)()
+    fd = (_lib.ExwFrame * F)()
+    oh = (_lib.ExwFrameOut * (F * nfrac))()
+    od = (_lib.ExwFrameOut * (F * nfrac))()
+    for f in range(F):
+        fh[f] = _lib.ExwFrame(color[f].data_ptr(), depth[f].data_ptr(), mv[f].data_ptr(), W, H, cdt)
+        fd[f] = _lib.ExwFrame(dc[f].data_ptr(), dd[f].data_ptr(), dm[f].data_ptr(), W, H, cdt)
+        for j in range(nfrac):
+            oh[f * nfrac + j] = _lib.ExwFrameOut(out[f, j].data_ptr(), mask[f, j].data_ptr())
+            od[f * nfrac + j] = _lib.ExwFrameOut(do[f, j].data_ptr(), dk[f, j].data_ptr())
+    flags = (0 if fill else FLAG_NO_FILL) | (0 if tma else FLAG_NO_TMA)
+    _check(lib().exw_extrapolate_host(ctypes.cast(fh, ctypes.c_void_p), ctypes.cast(fd, ctypes.c_void_p), F,
+                                      int(nfrac), flags, ctypes.cast(oh, ctypes.c_void_p),
+                                      ctypes.cast(od, ctypes.c_void_p), int(chunk), ws.data_ptr(), ws.numel(),
+                                      _stream(stream, dev)))
+    return out, mask
+
+
 def exw_tuner_create() -> int:
     """Host-side autotuner handle for exw_extrapolate_batched (free it with exw_tuner_destroy)."""
     return int(lib().exw_tuner_create())

@@ -234,6 +234,119 @@ exw_status exw_extrapolate(const exw_frame *frames, int nframes, int nfrac, unsi
     return engine_run(specs.data(), nframes, nfrac, flags, ws, ws_bytes, nullptr, true, (cudaStream_t)stream);
 }
 
+// Host-memory variant: copies in on one stream, the work on the caller's, copies out on another, chunk by chunk.
+namespace {
+struct HostStreams {
+    cudaStream_t in = nullptr, out = nullptr;
+    cudaEvent_t start = nullptr, copied = nullptr, done = nullptr, back = nullptr;
+};
+std::mutex g_host_mu;
+HostStreams g_host[16];
+
+bool host_streams(HostStreams *&hs) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return false;
+    std::lock_guard<std::mutex> lock(g_host_mu);
+    HostStreams &h = g_host[dev];
+    if (h.in == nullptr) {
+        if (cudaStreamCreateWithFlags(&h.in, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&h.out, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h.start, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h.copied, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h.done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h.back, cudaEventDisableTiming) != cudaSuccess) {
+            h = HostStreams{};
+            return false;
+        }
+    }
+    hs = &h;
+    return true;
+}
+
+// One copy per run of consecutive items whose source and destination both follow the previous item's.
+struct Run {
+    char *dst = nullptr;
+    const char *src = nullptr;
+    size_t bytes = 0;
+};
+cudaError_t copy_run(Run &r, void *dst, const void *src, size_t bytes, cudaMemcpyKind kind, cudaStream_t s,
+                     bool flush) {
+    cudaError_t e = cudaSuccess;
+    if (r.bytes != 0 && (flush || (char *)dst != r.dst + r.bytes || (const char *)src != r.src + r.bytes)) {
+        e = cudaMemcpyAsync(r.dst, r.src, r.bytes, kind, s);
+        r = Run{};
+    }
+    if (flush || e != cudaSuccess) return e;
+    if (r.bytes == 0) r = Run{(char *)dst, (const char *)src, 0};
+    r.bytes += bytes;
+    return cudaSuccess;
+}
+}  // namespace
+
+exw_status exw_extrapolate_host(const exw_frame *frames_host, const exw_frame *frames_dev, int nframes, int nfrac,
+                                unsigned flags, const exw_frame_out *out_host, const exw_frame_out *out_dev, int chunk,
+                                void *ws, size_t ws_bytes, exw_stream_t stream) {
+    if (frames_host == nullptr || frames_dev == nullptr || out_host == nullptr || out_dev == nullptr ||
+        nframes < 1 || nfrac < 1 || nfrac > EXW_MAX_FRAC || chunk < 0)
+        return EXW_ERR_INVALID_ARG;
+    if (chunk == 0) chunk = 8;
+    const int W = frames_dev[0].W, H = frames_dev[0].H;
+    const exw_dtype cdt = frames_dev[0].cdt;
+    if (!size_ok(W, H) || !dtype_ok(cdt)) return EXW_ERR_INVALID_ARG;
+    for (int f = 0; f < nframes; ++f) {
+        const exw_frame &h = frames_host[f];
+        if (h.W != W || h.H != H || h.cdt != cdt || h.color == nullptr || h.depth == nullptr || h.mv == nullptr)
+            return EXW_ERR_INVALID_ARG;
+        for (int j = 0; j < nfrac; ++j)
+            if (out_host[(size_t)f * nfrac + j].color == nullptr || out_host[(size_t)f * nfrac + j].mask == nullptr)
+                return EXW_ERR_INVALID_ARG;
+    }
+    if (entry_check() != EXW_OK) return EXW_ERR_CUDA;
+    HostStreams *hs = nullptr;
+    if (!host_streams(hs)) return EXW_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t px = (size_t)W * H, cb = px * 3 * csize(cdt);
+    // the copies in start after the work already queued on the caller's stream
+    cudaError_t e = cudaEventRecord(hs->start, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hs->in, hs->start, 0);
+    for (int f0 = 0; f0 < nframes && e == cudaSuccess; f0 += chunk) {
+        const int n = nframes - f0 < chunk ? nframes - f0 : chunk;
+        Run rc, rd, rm;
+        for (int f = f0; f < f0 + n && e == cudaSuccess; ++f) {
+            const exw_frame &h = frames_host[f], &d = frames_dev[f];
+            // the device descriptors are the staging buffers this call fills
+            e = copy_run(rc, const_cast<void *>(d.color), h.color, cb, cudaMemcpyHostToDevice, hs->in, false);
+            if (e == cudaSuccess)
+                e = copy_run(rd, const_cast<float *>(d.depth), h.depth, px * 4, cudaMemcpyHostToDevice, hs->in, false);
+            if (e == cudaSuccess)
+                e = copy_run(rm, const_cast<float *>(d.mv), h.mv, px * 8, cudaMemcpyHostToDevice, hs->in, false);
+        }
+        for (Run *r : {&rc, &rd, &rm})
+            if (e == cudaSuccess) e = copy_run(*r, nullptr, nullptr, 0, cudaMemcpyHostToDevice, hs->in, true);
+        if (e == cudaSuccess) e = cudaEventRecord(hs->copied, hs->in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, hs->copied, 0);
+        if (e != cudaSuccess) break;
+        const exw_status st =
+            exw_extrapolate(frames_dev + f0, n, nfrac, flags, const_cast<exw_frame_out *>(out_dev) + (size_t)f0 * nfrac,
+                            ws, ws_bytes, stream);
+        if (st != EXW_OK) return st;
+        e = cudaEventRecord(hs->done, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(hs->out, hs->done, 0);
+        Run oc, om;
+        for (int q = f0 * nfrac; q < (f0 + n) * nfrac && e == cudaSuccess; ++q) {
+            e = copy_run(oc, out_host[q].color, out_dev[q].color, cb, cudaMemcpyDeviceToHost, hs->out, false);
+            if (e == cudaSuccess)
+                e = copy_run(om, out_host[q].mask, out_dev[q].mask, px, cudaMemcpyDeviceToHost, hs->out, false);
+        }
+        for (Run *r : {&oc, &om})
+            if (e == cudaSuccess) e = copy_run(*r, nullptr, nullptr, 0, cudaMemcpyDeviceToHost, hs->out, true);
+    }
+    // the caller's stream completes once the last outputs are in host memory
+    if (e == cudaSuccess) e = cudaEventRecord(hs->back, hs->out);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, hs->back, 0);
+    return e == cudaSuccess ? EXW_OK : EXW_ERR_CUDA;
+}
+
 exw_status exw_warp_backward(const float *grad_out, const void *color, exw_dtype cdt, const float *depth,
                              const float *mv, const uint64_t *keys, int W, int H, int k, int denom, float *grad_color,
                              float *grad_mv, void *ws, size_t ws_bytes, exw_stream_t stream) {
