@@ -182,7 +182,8 @@ EXW_API exw_status exw_extrapolate(const exw_frame *frames, int nframes, int nfr
  * copied back on another.  frames_host [nframes] and out_host [nframes * nfrac] are HOST arrays of descriptors
  * holding host pointers (page-locked memory for the copies to overlap; any host memory works), frames_dev and
  * out_dev the same shapes in device memory, owned by the caller and written here (staging: every frame has its
- * own device buffers, nothing is allocated).  Workspace: exw_workspace_bytes(EXW_OP_EXTRAPOLATE, W, H, cdt,
+ * own device buffers, nothing is allocated).  out_dev NULL: the engine writes the outputs straight into the host
+ * buffers, which must then be page-locked and mapped (cudaHostGetDevicePointer; EXW_ERR_INVALID_ARG otherwise).  Workspace: exw_workspace_bytes(EXW_OP_EXTRAPOLATE, W, H, cdt,
  * min(chunk, nframes), nfrac).  The call returns once the work is queued; when `stream` completes, the outputs are
  * in host memory.  The internal streams and events are created at the first call on a device; calls on one device
  * are serialised by the caller.  Errors as exw_extrapolate. */

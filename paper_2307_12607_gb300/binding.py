@@ -197,12 +197,13 @@ def exw_extrapolate(color, depth, mv, nfrac: int = 3, fill: bool = True, out=Non
 
 
 def exw_extrapolate_host(color, depth, mv, nfrac: int = 3, fill: bool = True, out=None, mask=None, dev_in=None,
-                         dev_out=None, ws=None, chunk: int = 8, stream=None, tma: bool = True):
+                         dev_out=None, ws=None, chunk: int = 8, stream=None, tma: bool = True, direct: bool = False):
     """exw_extrapolate for a sequence in HOST memory ([F][3][H][W] colour, [F][H][W] depth, [F][2][H][W] motion;
     page-locked for the copies to overlap): the copies in, the work and the copies out run chunk by chunk on
     three streams inside the call.  Returns host (out [F][nfrac][3][H][W], mask [F][nfrac][H][W]) once the
     caller's stream has been synchronised.  dev_in = (colour, depth, motion) and dev_out = (out, mask): device
-    staging tensors of the same shapes (allocated here when None)."""
+    staging tensors of the same shapes (allocated here when None).  direct=True: the engine writes the outputs
+    straight into the (page-locked) host tensors; dev_out is not used."""
     F, _, H, W = (int(v) for v in color.shape)
     cdt = _cdt(color)
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -216,15 +217,16 @@ def exw_extrapolate_host(color, depth, mv, nfrac: int = 3, fill: bool = True, ou
     if dev_in is None:
         dev_in = (torch.empty_like(color, device=dev), torch.empty_like(depth, device=dev),
                   torch.empty_like(mv, device=dev))
-    if dev_out is None:
+    if dev_out is None and not direct:
         dev_out = (torch.empty_like(out, device=dev), torch.empty_like(mask, device=dev))
     dc, dd, dm = dev_in
-    do, dk = dev_out
+    do, dk = dev_out if not direct else (out, mask)
     _dev(dc, "dev color", color.dtype, (F, 3, H, W))
     _dev(dd, "dev depth", torch.float32, (F, H, W))
     _dev(dm, "dev mv", torch.float32, (F, 2, H, W))
-    _dev(do, "dev out", color.dtype, (F, nfrac, 3, H, W))
-    _dev(dk, "dev mask", torch.uint8, (F, nfrac, H, W))
+    if not direct:
+        _dev(do, "dev out", color.dtype, (F, nfrac, 3, H, W))
+        _dev(dk, "dev mask", torch.uint8, (F, nfrac, H, W))
     need = exw_workspace_bytes(OP_EXTRAPOLATE, W, H, cdt, min(chunk, F) if chunk > 0 else min(8, F), nfrac)
     if ws is None:
         ws = workspace(need, dev)
@@ -241,7 +243,8 @@ def exw_extrapolate_host(color, depth, mv, nfrac: int = 3, fill: bool = True, ou
     flags = (0 if fill else FLAG_NO_FILL) | (0 if tma else FLAG_NO_TMA)
     _check(lib().exw_extrapolate_host(ctypes.cast(fh, ctypes.c_void_p), ctypes.cast(fd, ctypes.c_void_p), F,
                                       int(nfrac), flags, ctypes.cast(oh, ctypes.c_void_p),
-                                      ctypes.cast(od, ctypes.c_void_p), int(chunk), ws.data_ptr(), ws.numel(),
+                                      None if direct else ctypes.cast(od, ctypes.c_void_p), int(chunk),
+                                      ws.data_ptr(), ws.numel(),
                                       _stream(stream, dev)))
     return out, mask
 

@@ -286,8 +286,8 @@ cudaError_t copy_run(Run &r, void *dst, const void *src, size_t bytes, cudaMemcp
 exw_status exw_extrapolate_host(const exw_frame *frames_host, const exw_frame *frames_dev, int nframes, int nfrac,
                                 unsigned flags, const exw_frame_out *out_host, const exw_frame_out *out_dev, int chunk,
                                 void *ws, size_t ws_bytes, exw_stream_t stream) {
-    if (frames_host == nullptr || frames_dev == nullptr || out_host == nullptr || out_dev == nullptr ||
-        nframes < 1 || nfrac < 1 || nfrac > EXW_MAX_FRAC || chunk < 0)
+    if (frames_host == nullptr || frames_dev == nullptr || out_host == nullptr || nframes < 1 || nfrac < 1 ||
+        nfrac > EXW_MAX_FRAC || chunk < 0)
         return EXW_ERR_INVALID_ARG;
     if (chunk == 0) chunk = 8;
     const int W = frames_dev[0].W, H = frames_dev[0].H;
@@ -302,6 +302,20 @@ exw_status exw_extrapolate_host(const exw_frame *frames_host, const exw_frame *f
                 return EXW_ERR_INVALID_ARG;
     }
     if (entry_check() != EXW_OK) return EXW_ERR_CUDA;
+    // out_dev == NULL: the engine writes every output straight into the (page-locked, device-mapped) host buffers
+    std::vector<exw_frame_out> direct;
+    if (out_dev == nullptr) {
+        direct.resize((size_t)nframes * nfrac);
+        for (size_t q = 0; q < direct.size(); ++q) {
+            void *c = nullptr, *m = nullptr;
+            if (cudaHostGetDevicePointer(&c, out_host[q].color, 0) != cudaSuccess ||
+                cudaHostGetDevicePointer(&m, out_host[q].mask, 0) != cudaSuccess) {
+                cudaGetLastError();
+                return EXW_ERR_INVALID_ARG;
+            }
+            direct[q] = exw_frame_out{c, (uint8_t *)m};
+        }
+    }
     HostStreams *hs = nullptr;
     if (!host_streams(hs)) return EXW_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
@@ -326,10 +340,11 @@ exw_status exw_extrapolate_host(const exw_frame *frames_host, const exw_frame *f
         if (e == cudaSuccess) e = cudaEventRecord(hs->copied, hs->in);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, hs->copied, 0);
         if (e != cudaSuccess) break;
-        const exw_status st =
-            exw_extrapolate(frames_dev + f0, n, nfrac, flags, const_cast<exw_frame_out *>(out_dev) + (size_t)f0 * nfrac,
-                            ws, ws_bytes, stream);
+        exw_frame_out *od = out_dev != nullptr ? const_cast<exw_frame_out *>(out_dev) : direct.data();
+        const exw_status st = exw_extrapolate(frames_dev + f0, n, nfrac, flags, od + (size_t)f0 * nfrac, ws, ws_bytes,
+                                              stream);
         if (st != EXW_OK) return st;
+        if (out_dev == nullptr) continue;
         e = cudaEventRecord(hs->done, s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(hs->out, hs->done, 0);
         Run oc, om;
@@ -342,8 +357,8 @@ exw_status exw_extrapolate_host(const exw_frame *frames_host, const exw_frame *f
             if (e == cudaSuccess) e = copy_run(*r, nullptr, nullptr, 0, cudaMemcpyDeviceToHost, hs->out, true);
     }
     // the caller's stream completes once the last outputs are in host memory
-    if (e == cudaSuccess) e = cudaEventRecord(hs->back, hs->out);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, hs->back, 0);
+    if (e == cudaSuccess && out_dev != nullptr) e = cudaEventRecord(hs->back, hs->out);
+    if (e == cudaSuccess && out_dev != nullptr) e = cudaStreamWaitEvent(s, hs->back, 0);
     return e == cudaSuccess ? EXW_OK : EXW_ERR_CUDA;
 }
 

@@ -289,15 +289,16 @@ def test_uniform_tiles_with_foreign_motion_inside_their_source(b):
         assert torch.equal(m2, mask) and torch.equal(o2.view(torch.int32), out.view(torch.int32))
 
 
+@pytest.mark.parametrize("direct", [False, True])
 @pytest.mark.parametrize("chunk", [2, 3, 8])
-def test_host_buffers_match_device_path(b, chunk):
+def test_host_buffers_match_device_path(b, chunk, direct):
     # 7 frames in host memory, chunks of 2 or 3 (a ragged last chunk) or one chunk: copies in, work and copies out
     # overlap on three streams; the results are the device path's, bit for bit
     frames = [frame_case(("scene", 96, 64, 20 + s)) for s in range(7)]
     hc = torch.from_numpy(np.stack([f[0] for f in frames]).astype(np.float16)).pin_memory()
     hd = torch.from_numpy(np.stack([f[1] for f in frames])).pin_memory()
     hm = torch.from_numpy(np.stack([f[2] for f in frames])).pin_memory()
-    out, mask = b.exw_extrapolate_host(hc, hd, hm, nfrac=3, chunk=chunk)
+    out, mask = b.exw_extrapolate_host(hc, hd, hm, nfrac=3, chunk=chunk, direct=direct)
     torch.cuda.synchronize()
     o1, k1 = b.exw_extrapolate(hc.cuda(), hd.cuda(), hm.cuda(), nfrac=3)
     assert torch.equal(mask, k1.cpu()) and torch.equal(out.view(torch.int16), o1.cpu().view(torch.int16))
