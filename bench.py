@@ -67,8 +67,8 @@ def dist_env():
 # capture (a smaller launch; the engine's traffic grows in proportion to the frames of a launch), with the hash of
 # the kernel sources it was taken on: reported only while the sources are unchanged, else null.
 MEASURED_TRAFFIC = {
-    ("exw_engine", "sequence_1080p_fp32"): ((238.29e6 + 278.89e6) / 4, "e75ec16f510c9ddd"),
-    ("exw_engine", "warp_4k_fp16"): (105.38e6 + 129.30e6, "e75ec16f510c9ddd"),
+    ("exw_engine", "sequence_1080p_fp32"): ((238.57e6 + 279.08e6) / 4, "bcb5f60446ec236a"),
+    ("exw_engine", "warp_4k_fp16"): (105.41e6 + 129.62e6, "bcb5f60446ec236a"),
 }
 
 
