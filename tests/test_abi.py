@@ -94,6 +94,26 @@ def test_extrapolate_descriptor_checks(lib):
     assert r == 1                                              # unknown flag
 
 
+def test_extrapolate_host_argument_checks(lib):
+    # null descriptor arrays, a negative chunk, nfrac out of range and mismatched host descriptors are refused on the
+    # host, before any copy is queued
+    from paper_2307_12607_gb300 import _lib
+    fh = (_lib.ExwFrame * 2)()
+    fd = (_lib.ExwFrame * 2)()
+    for f in range(2):
+        fd[f] = _lib.ExwFrame(4096, 8192, 12288, 64, 64, 0)
+        fh[f] = _lib.ExwFrame(4096, 8192, 12288, 64, 64 if f == 0 else 32, 0)   # frame 1's size differs
+    oh = (_lib.ExwFrameOut * 6)()
+    for i in range(6):
+        oh[i] = _lib.ExwFrameOut(16384, 20480)
+    P = lambda a: ctypes.cast(a, ctypes.c_void_p)
+    assert lib.exw_extrapolate_host(None, P(fd), 2, 3, 0, P(oh), None, 2, 4096, 1 << 20, None) == 1
+    assert lib.exw_extrapolate_host(P(fh), P(fd), 2, 3, 0, None, None, 2, 4096, 1 << 20, None) == 1
+    assert lib.exw_extrapolate_host(P(fh), P(fd), 2, 3, 0, P(oh), None, -1, 4096, 1 << 20, None) == 1
+    assert lib.exw_extrapolate_host(P(fh), P(fd), 1, 4, 0, P(oh), None, 2, 4096, 1 << 20, None) == 1
+    assert lib.exw_extrapolate_host(P(fh), P(fd), 2, 3, 0, P(oh), None, 2, 4096, 1 << 20, None) == 1
+
+
 def test_binding_refuses_cpu_tensors():
     torch = pytest.importorskip("torch")
     from paper_2307_12607_gb300 import binding as b
