@@ -57,6 +57,10 @@ def _load():
             lib.oracle_fill_holes.argtypes = [P, P, I, I]
             lib.oracle_warp_backward.argtypes = [P, P, P, P, P, I, I, I, I, P, P]
             lib.oracle_motion_bounds.argtypes = [P, P, I, I, I, P, P]
+            lib.oracle_mv_variance.argtypes = [P, I, I, P]
+            lib.oracle_mv_variance.restype = None
+            lib.oracle_color_mse.argtypes = [P, P, I, I]
+            lib.oracle_color_mse.restype = ctypes.c_double
             for f in (lib.oracle_splat, lib.oracle_mask, lib.oracle_warp, lib.oracle_fill_holes,
                       lib.oracle_warp_backward, lib.oracle_motion_bounds):
                 f.restype = None
@@ -184,3 +188,25 @@ def l2_loss_grad(out, target, mask):
     valid = (np.asarray(mask) == 0)[None, :, :]
     diff = np.where(valid, out - target, 0.0)
     return float(np.sum(diff * diff)), 2.0 * diff
+
+
+def mv_variance(mv):
+    """(count, Var_x, Var_y) of the finite motion vectors of a [2][H][W] field (Sec. IV-C Eq. 1, see the C code)."""
+    mv = _f32(mv)
+    H, W = mv.shape[1], mv.shape[2]
+    out = np.zeros(3, np.float64)
+    _load().oracle_mv_variance(_ptr(mv), W, H, _ptr(out))
+    return float(out[0]), float(out[1]), float(out[2])
+
+
+def color_mse(a, b):
+    """Mean squared difference of two [3][H][W] colour images in FP64 (Sec. IV-C Eq. 3's MSE)."""
+    a = _f64(a)
+    b = _f64(b)
+    return float(_load().oracle_color_mse(_ptr(a), _ptr(b), a.shape[2], a.shape[1]))
+
+
+def psnr(a, b) -> float:
+    """PSNR = 10 log10(255^2 / MSE) of colours in [0, 1] scaled by 255 (Sec. IV-C Eq. 3); inf for equal images."""
+    mse = color_mse(a, b)
+    return float("inf") if mse == 0.0 else 10.0 * np.log10(1.0 / mse)

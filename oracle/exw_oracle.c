@@ -383,3 +383,43 @@ void oracle_motion_bounds(const float *depth, const float *mv, int W, int H, int
         }
     }
 }
+
+/* Motion-variance features Var_x(F_mv), Var_y(F_mv) of the environment vector E_t (Sec. IV-C, Eq. 1; the feature
+ * is motivated in Sec. III-D): over every pixel whose two motion components are finite, the population variance
+ * of the x component and of the y component, by two passes in FP64 -- the mean, then the mean of the squared
+ * deviations.  out[0] = the number of pixels counted, out[1] = Var_x, out[2] = Var_y (0 and 0 for an empty set). */
+void oracle_mv_variance(const float *mv, int W, int H, double *out) {
+    const size_t n = (size_t)W * (size_t)H;
+    double cnt = 0.0, sx = 0.0, sy = 0.0;
+    for (size_t i = 0; i < n; ++i) {
+        if (!isfinite(mv[i]) || !isfinite(mv[n + i])) continue;
+        cnt += 1.0;
+        sx += (double)mv[i];
+        sy += (double)mv[n + i];
+    }
+    out[0] = cnt;
+    out[1] = out[2] = 0.0;
+    if (cnt == 0.0) return;
+    const double mx = sx / cnt, my = sy / cnt;
+    double vx = 0.0, vy = 0.0;
+    for (size_t i = 0; i < n; ++i) {
+        if (!isfinite(mv[i]) || !isfinite(mv[n + i])) continue;
+        const double dx = (double)mv[i] - mx, dy = (double)mv[n + i] - my;
+        vx += dx * dx;
+        vy += dy * dy;
+    }
+    out[1] = vx / cnt;
+    out[2] = vy / cnt;
+}
+
+/* Mean squared difference of two colour images [3][H][W] over all 3 W H values, FP64: the MSE of the reward's
+ * PSNR = 10 log10(255^2 / MSE) (Sec. IV-C, Eq. 3) for colours in [0, 1] scaled by 255. */
+double oracle_color_mse(const double *a, const double *b, int W, int H) {
+    const size_t n = 3 * (size_t)W * (size_t)H;
+    double s = 0.0;
+    for (size_t i = 0; i < n; ++i) {
+        const double d = a[i] - b[i];
+        s += d * d;
+    }
+    return s / (double)n;
+}

@@ -523,3 +523,57 @@ def test_motion_bounds_brute_force(W, H, block):
         for p in np.flatnonzero(ok.ravel()):
             brute = max(brute, abs(exact_offset(cl[0].flat[p], k)[0]), abs(exact_offset(cl[1].flat[p], k)[0]))
         assert oracle.halo(frame, k) == brute
+
+
+# ----------------------------------------------------------------------------------------------------------------
+# Motion-variance features (Sec. IV-C Eq. 1) and the colour MSE / PSNR of the reward (Eq. 3)
+# ----------------------------------------------------------------------------------------------------------------
+
+def _exact_var(values):
+    """Population variance of float32 values by exact rational arithmetic."""
+    vs = [Fraction(float(v)) for v in values]
+    if not vs:
+        return Fraction(0)
+    m = sum(vs) / len(vs)
+    return sum((v - m) ** 2 for v in vs) / len(vs)
+
+
+def test_mv_variance_closed_forms():
+    # constant field: 0; x = column index 0..W-1 on every row: (W^2 - 1) / 12 exactly; y = row index likewise
+    W, H = 13, 7
+    mv = np.zeros((2, H, W), np.float32)
+    mv[0] = 2.5
+    mv[1] = -4.0
+    assert oracle.mv_variance(mv) == (W * H, 0.0, 0.0)
+    mv[0] = np.arange(W, dtype=np.float32)[None, :]
+    mv[1] = np.arange(H, dtype=np.float32)[:, None]
+    n, vx, vy = oracle.mv_variance(mv)
+    assert n == W * H and vx == (W * W - 1) / 12 and vy == (H * H - 1) / 12
+
+
+def test_mv_variance_excludes_non_finite_and_matches_exact_arithmetic():
+    rng = np.random.default_rng(3)
+    mv = (rng.integers(-64, 65, size=(2, 9, 11)) * 0.25).astype(np.float32)
+    mv[0, 1, 2] = np.nan
+    mv[1, 3, 4] = np.inf
+    mv[0, 5, 6] = -np.inf
+    ok = np.isfinite(mv[0]) & np.isfinite(mv[1])
+    n, vx, vy = oracle.mv_variance(mv)
+    assert n == ok.sum() == 9 * 11 - 3
+    assert vx == pytest.approx(float(_exact_var(mv[0][ok])), rel=1e-15, abs=0)
+    assert vy == pytest.approx(float(_exact_var(mv[1][ok])), rel=1e-15, abs=0)
+    # a second routine: numpy's variance of the finite subset
+    assert vx == pytest.approx(float(np.var(mv[0][ok].astype(np.float64))), rel=1e-14)
+    # no finite vector at all: count 0, variances 0
+    assert oracle.mv_variance(np.full((2, 3, 4), np.nan, np.float32)) == (0.0, 0.0, 0.0)
+
+
+def test_color_mse_and_psnr_pins():
+    rng = np.random.default_rng(4)
+    a = rng.uniform(size=(3, 5, 6))
+    assert oracle.color_mse(a, a) == 0.0 and oracle.psnr(a, a) == float("inf")
+    assert oracle.color_mse(a, a + 0.25) == pytest.approx(0.0625, rel=1e-14)       # constant offset: delta^2
+    assert oracle.psnr(a, a + 0.1) == pytest.approx(20.0, abs=1e-9)                 # 10 log10(1 / 0.01)
+    b = rng.uniform(size=(3, 5, 6))
+    exact = sum((Fraction(float(x)) - Fraction(float(y))) ** 2 for x, y in zip(a.ravel(), b.ravel())) / a.size
+    assert oracle.color_mse(a, b) == pytest.approx(float(exact), rel=1e-14)
