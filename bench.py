@@ -265,7 +265,7 @@ def _kernel_means(b, fn):
     return {k: round(v, 2) for k, v in out.items()}
 
 
-EXTRAS = ("warp_4k_fp16", "extrapolate_4k_fp16_fill", "batched_48_streams", "fwd_bwd_1080p")
+EXTRAS = ("warp_4k_fp16", "extrapolate_4k_fp16_fill", "batched_48_streams", "fwd_bwd_1080p", "quality_and_stats")
 
 
 def run_extras(b, devc, names=EXTRAS):
@@ -282,7 +282,48 @@ def run_extras(b, devc, names=EXTRAS):
         _extras_batched(b, devc, ex)
     if "fwd_bwd_1080p" in names:
         _extras_diff(b, devc, ex)
+    if "quality_and_stats" in names:
+        _extras_quality(b, devc, peak, ex)
     return ex
+
+
+def _extras_quality(b, devc, peak, ex):
+    """Context: PSNR (Sec. IV-C, Eq. 3) of P_1..P_3 with fill against the generator's ground truth at t + k/4 for 8
+    frames of the 1080p sequence, and the timing of the two frame statistics (motion-variance features, Eq. 1;
+    colour MSE) against the HBM roofline of the bytes they read (the inputs stay L2-resident between repetitions,
+    so the fractions are upper bounds)."""
+    import torch
+    from paper_2307_12607_gb300 import scenes
+    sc = scenes.sequence_1080p_scene()
+    H, W = 1080, 1920
+    psnr = {1: [], 2: [], 3: []}
+    ws = b.workspace(b.exw_workspace_bytes(b.OP_STATS, W, H), devc)
+    for f in range(8):
+        c, d, m = (torch.from_numpy(x).to(devc) for x in scenes.render(sc, float(f)))
+        out, _ = b.exw_extrapolate(c, d, m, 3)
+        for k in (1, 2, 3):
+            gt = torch.from_numpy(scenes.ground_truth(sc, float(f), k)).to(devc)
+            psnr[k].append(b.exw_psnr(out[k - 1], gt, ws))
+    c, d, m = (torch.from_numpy(x).to(devc) for x in scenes.render(sc, 0.0))
+    gt = torch.from_numpy(scenes.ground_truth(sc, 0.0, 1)).to(devc)
+    out = torch.empty_like(c)
+    res = torch.empty(3, dtype=torch.float64, device=devc)
+
+    def var():
+        b.lib().exw_mv_variance(m.data_ptr(), W, H, res.data_ptr(), ws.data_ptr(), ws.numel(),
+                                b._stream(None, devc))
+
+    def mse():
+        b.lib().exw_color_mse(c.data_ptr(), gt.data_ptr(), b.F32, W, H, res.data_ptr(), ws.data_ptr(), ws.numel(),
+                              b._stream(None, devc))
+    ms_v = _event_ms(var, 50)
+    ms_m = _event_ms(mse, 50)
+    ex["quality_and_stats"] = {
+        "psnr_db_vs_ground_truth": {f"P_{k}": round(sum(v) / len(v), 3) for k, v in psnr.items()},
+        "mv_variance_us": ms_v * 1e3, "mv_variance_hbm_frac": 8 * W * H / (ms_v / 1e3) / 1e9 / peak,
+        "color_mse_us": ms_m * 1e3, "color_mse_hbm_frac": 24 * W * H / (ms_m / 1e3) / 1e9 / peak,
+        "workload": "PSNR: 8 frames of the 1920x1080 FP32 sequence, P_1..P_3 with fill against the scene rendered "
+                    "at t + k/4; statistics: one 1920x1080 frame (8 B/px motion, 2 x 12 B/px colour)"}
 
 
 def _extras_4k(b, devc, names, peak, ex):

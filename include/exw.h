@@ -79,7 +79,8 @@ typedef enum exw_op {
     EXW_OP_MOTION_BOUNDS = 0,
     EXW_OP_FILL_HOLES = 1,
     EXW_OP_EXTRAPOLATE = 2,
-    EXW_OP_WARP_BACKWARD = 3
+    EXW_OP_WARP_BACKWARD = 3,
+    EXW_OP_STATS = 4
 } exw_op;
 
 #define EXW_MASK_EMPTY 1u
@@ -183,14 +184,28 @@ EXW_API exw_status exw_extrapolate(const exw_frame *frames, int nframes, int nfr
  * holding host pointers (page-locked memory for the copies to overlap; any host memory works), frames_dev and
  * out_dev the same shapes in device memory, owned by the caller and written here (staging: every frame has its
  * own device buffers, nothing is allocated).  out_dev NULL: the engine writes the outputs straight into the host
- * buffers, which must then be page-locked and mapped (cudaHostGetDevicePointer; EXW_ERR_INVALID_ARG otherwise).  Workspace: exw_workspace_bytes(EXW_OP_EXTRAPOLATE, W, H, cdt,
- * min(chunk, nframes), nfrac).  The call returns once the work is queued; when `stream` completes, the outputs are
+ * buffers, which must then be page-locked and mapped (cudaHostGetDevicePointer; EXW_ERR_INVALID_ARG otherwise).
+ * Workspace: exw_workspace_bytes(EXW_OP_EXTRAPOLATE, W, H, cdt, min(chunk, nframes), nfrac).  The call returns once the work is queued; when `stream` completes, the outputs are
  * in host memory.  The internal streams and events are created at the first call on a device; calls on one device
  * are serialised by the caller.  Errors as exw_extrapolate. */
 EXW_API exw_status exw_extrapolate_host(const exw_frame *frames_host, const exw_frame *frames_dev, int nframes,
                                         int nfrac, unsigned flags, const exw_frame_out *out_host,
                                         const exw_frame_out *out_dev, int chunk, void *ws, size_t ws_bytes,
                                         exw_stream_t stream);
+
+/* Motion-variance features Var_x(F_mv), Var_y(F_mv) of the decision stage's environment vector E_t (Sec. IV-C,
+ * Eq. 1; the feature is motivated in Sec. III-D): over every pixel of mv [2][H][W] whose two components are
+ * finite, the population variance of the x component and of the y component.  out [3] is a DEVICE float64 array:
+ * the number of pixels counted, Var_x, Var_y (0, 0 for an empty set).  FP64 throughout, merged in a fixed order:
+ * deterministic.  Workspace: exw_workspace_bytes(EXW_OP_STATS, W, H, cdt, 1, 1). */
+EXW_API exw_status exw_mv_variance(const float *mv, int W, int H, double *out, void *ws, size_t ws_bytes,
+                                   exw_stream_t stream);
+
+/* Mean squared difference of two colour images a, b [3][H][W] of type cdt over all 3 W H values (FP64, fixed
+ * order): the MSE of the reward's PSNR = 10 log10(255^2 / MSE) (Sec. IV-C, Eq. 3) for colours in [0, 1] scaled by
+ * 255, i.e. PSNR = -10 log10(out[0]).  out [1] is a DEVICE float64.  Workspace: as exw_mv_variance. */
+EXW_API exw_status exw_color_mse(const void *a, const void *b, exw_dtype cdt, int W, int H, double *out, void *ws,
+                                 size_t ws_bytes, exw_stream_t stream);
 
 /* Adjoint of stage (b) for fraction k/denom with every integer decision held fixed (target, winner, taps, tap
  * participation, mask).  grad_out [3][H][W] float32 = dL/d out_color; accumulates (+=) into grad_color

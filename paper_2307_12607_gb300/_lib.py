@@ -32,6 +32,8 @@ PROTOTYPES = {
     "exw_fill_holes_static": (I, [P, I, P, I, I, P]),
     "exw_extrapolate": (I, [P, I, I, U, P, P, SZ, P]),
     "exw_extrapolate_host": (I, [P, P, I, I, U, P, P, I, P, SZ, P]),
+    "exw_mv_variance": (I, [P, I, I, P, P, SZ, P]),
+    "exw_color_mse": (I, [P, P, I, I, I, P, P, SZ, P]),
     "exw_warp_backward": (I, [P, P, I, P, P, P, I, I, I, I, P, P, P, SZ, P]),
     "exw_l2_loss_grad": (I, [P, P, I, P, I, I, P, P, P]),
     "exw_device_status": (I, [P, P]),

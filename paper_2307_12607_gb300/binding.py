@@ -249,6 +249,46 @@ def exw_extrapolate_host(color, depth, mv, nfrac: int = 3, fill: bool = True, ou
     return out, mask
 
 
+OP_STATS = 4
+
+
+def exw_mv_variance(mv, ws=None, stream=None):
+    """Motion-variance features (count, Var_x, Var_y) of a [2][H][W] float32 motion field (Sec. IV-C, Eq. 1):
+    population variances over the pixels whose two components are finite, FP64 on the device (reads the result
+    back, so it synchronises with the stream)."""
+    H, W = int(mv.shape[1]), int(mv.shape[2])
+    _dev(mv, "mv", torch.float32, (2, H, W))
+    dev = mv.device
+    if ws is None:
+        ws = workspace(exw_workspace_bytes(OP_STATS, W, H, F32, 1, 1), dev)
+    out = torch.empty(3, dtype=torch.float64, device=dev)
+    _check(lib().exw_mv_variance(mv.data_ptr(), W, H, out.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream, dev)))
+    n, vx, vy = out.tolist()
+    return n, vx, vy
+
+
+def exw_color_mse(a, b, ws=None, stream=None) -> float:
+    """Mean squared difference of two [3][H][W] colour images of one dtype over all 3 W H values, FP64 on the
+    device (Sec. IV-C, Eq. 3's MSE; synchronises to read it back)."""
+    H, W = int(a.shape[1]), int(a.shape[2])
+    _dev(a, "a", None, (3, H, W))
+    _dev(b, "b", a.dtype, (3, H, W))
+    dev = a.device
+    if ws is None:
+        ws = workspace(exw_workspace_bytes(OP_STATS, W, H, F32, 1, 1), dev)
+    out = torch.empty(1, dtype=torch.float64, device=dev)
+    _check(lib().exw_color_mse(a.data_ptr(), b.data_ptr(), _cdt(a), W, H, out.data_ptr(), ws.data_ptr(), ws.numel(),
+                               _stream(stream, dev)))
+    return float(out.item())
+
+
+def exw_psnr(a, b, ws=None, stream=None) -> float:
+    """PSNR = 10 log10(255^2 / MSE) of colours in [0, 1] scaled by 255 (Sec. IV-C, Eq. 3); inf for equal images."""
+    import math
+    mse = exw_color_mse(a, b, ws, stream)
+    return math.inf if mse == 0.0 else -10.0 * math.log10(mse)
+
+
 def exw_tuner_create() -> int:
     """Host-side autotuner handle for exw_extrapolate_batched (free it with exw_tuner_destroy)."""
     return int(lib().exw_tuner_create())

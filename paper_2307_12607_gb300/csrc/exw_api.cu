@@ -131,8 +131,26 @@ size_t exw_workspace_bytes(exw_op op, int W, int H, exw_dtype cdt, int nframes, 
             return engine_workspace_bytes(one.data(), nframes, nfrac, true);
         }
         case EXW_OP_WARP_BACKWARD: return ws_layout(W, H, 1, 1, true).total;
+        case EXW_OP_STATS: return stats_workspace_bytes();
     }
     return 0;
+}
+
+exw_status exw_mv_variance(const float *mv, int W, int H, double *out, void *ws, size_t ws_bytes,
+                           exw_stream_t stream) {
+    if (!size_ok(W, H) || !aligned(mv, 4) || !aligned(out, 8)) return EXW_ERR_INVALID_ARG;
+    if (!aligned16(ws) || ws_bytes < stats_workspace_bytes()) return EXW_ERR_WORKSPACE;
+    if (entry_check() != EXW_OK) return EXW_ERR_CUDA;
+    return launch_mv_variance(mv, W, H, out, ws, (cudaStream_t)stream) == cudaSuccess ? EXW_OK : EXW_ERR_CUDA;
+}
+
+exw_status exw_color_mse(const void *a, const void *b, exw_dtype cdt, int W, int H, double *out, void *ws,
+                         size_t ws_bytes, exw_stream_t stream) {
+    if (!size_ok(W, H) || !dtype_ok(cdt) || !aligned(a, csize(cdt)) || !aligned(b, csize(cdt)) || !aligned(out, 8))
+        return EXW_ERR_INVALID_ARG;
+    if (!aligned16(ws) || ws_bytes < stats_workspace_bytes()) return EXW_ERR_WORKSPACE;
+    if (entry_check() != EXW_OK) return EXW_ERR_CUDA;
+    return launch_color_mse(a, b, cdt, W, H, out, ws, (cudaStream_t)stream) == cudaSuccess ? EXW_OK : EXW_ERR_CUDA;
 }
 
 exw_status exw_motion_bounds(const float *depth, const float *mv, int W, int H, float *tile_bounds,
