@@ -61,6 +61,8 @@ def _load():
             lib.oracle_mv_variance.restype = None
             lib.oracle_color_mse.argtypes = [P, P, I, I]
             lib.oracle_color_mse.restype = ctypes.c_double
+            lib.oracle_ssim.argtypes = [P, P, I, I]
+            lib.oracle_ssim.restype = ctypes.c_double
             for f in (lib.oracle_splat, lib.oracle_mask, lib.oracle_warp, lib.oracle_fill_holes,
                       lib.oracle_warp_backward, lib.oracle_motion_bounds):
                 f.restype = None
@@ -210,3 +212,11 @@ def psnr(a, b) -> float:
     """PSNR = 10 log10(255^2 / MSE) of colours in [0, 1] scaled by 255 (Sec. IV-C Eq. 3); inf for equal images."""
     mse = color_mse(a, b)
     return float("inf") if mse == 0.0 else 10.0 * np.log10(1.0 / mse)
+
+
+def ssim(a, b) -> float:
+    """Mean SSIM of two [3][H][W] colour images in [0, 1] (11 x 11 Gaussian window, sigma 1.5, valid positions;
+    Sec. IV-C Eq. 3, see the C code).  NaN when W or H is below 11."""
+    a = _f64(a)
+    b = _f64(b)
+    return float(_load().oracle_ssim(_ptr(a), _ptr(b), a.shape[2], a.shape[1]))

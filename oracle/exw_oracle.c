@@ -423,3 +423,45 @@ double oracle_color_mse(const double *a, const double *b, int W, int H) {
     }
     return s / (double)n;
 }
+
+/* Structural similarity of two colour images [3][H][W] (the SSIM of the reward, Sec. IV-C, Eq. 3; the paper names
+ * it without a formula, read as the standard index of Wang, Bovik, Sheikh and Simoncelli, 2004): per channel and
+ * per position of an 11 x 11 Gaussian window (sigma 1.5, weights normalised to sum 1) lying wholly inside the
+ * image, with weighted means mu, variances sigma^2 = E[v^2] - mu^2 and covariance sigma_xy = E[ab] - mu_a mu_b,
+ *     SSIM = (2 mu_a mu_b + C1)(2 sigma_ab + C2) / ((mu_a^2 + mu_b^2 + C1)(sigma_a^2 + sigma_b^2 + C2)),
+ * C1 = (0.01 L)^2, C2 = (0.03 L)^2, L = 1 (colours in [0, 1]); the result is the mean over channels and positions.
+ * Needs W, H >= 11 (else returns NaN).  Straight FP64 sums over the 121 taps. */
+double oracle_ssim(const double *a, const double *b, int W, int H) {
+    if (W < 11 || H < 11) return NAN;
+    double g[11], gs = 0.0;
+    for (int i = 0; i < 11; ++i) {
+        g[i] = exp(-((double)(i - 5) * (double)(i - 5)) / (2.0 * 1.5 * 1.5));
+        gs += g[i];
+    }
+    for (int i = 0; i < 11; ++i) g[i] /= gs;
+    const double C1 = 0.01 * 0.01, C2 = 0.03 * 0.03;
+    const size_t plane = (size_t)W * (size_t)H;
+    double total = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        const double *pa = a + c * plane, *pb = b + c * plane;
+        for (int y = 0; y + 11 <= H; ++y) {
+            for (int x = 0; x + 11 <= W; ++x) {
+                double ma = 0.0, mb = 0.0, saa = 0.0, sbb = 0.0, sab = 0.0;
+                for (int i = 0; i < 11; ++i) {
+                    for (int j = 0; j < 11; ++j) {
+                        const double w = g[i] * g[j];
+                        const double va = pa[(size_t)(y + i) * W + (x + j)], vb = pb[(size_t)(y + i) * W + (x + j)];
+                        ma += w * va;
+                        mb += w * vb;
+                        saa += w * va * va;
+                        sbb += w * vb * vb;
+                        sab += w * va * vb;
+                    }
+                }
+                const double va2 = saa - ma * ma, vb2 = sbb - mb * mb, cab = sab - ma * mb;
+                total += ((2.0 * ma * mb + C1) * (2.0 * cab + C2)) / ((ma * ma + mb * mb + C1) * (va2 + vb2 + C2));
+            }
+        }
+    }
+    return total / (3.0 * (double)(W - 10) * (double)(H - 10));
+}

@@ -577,3 +577,34 @@ def test_color_mse_and_psnr_pins():
     b = rng.uniform(size=(3, 5, 6))
     exact = sum((Fraction(float(x)) - Fraction(float(y))) ** 2 for x, y in zip(a.ravel(), b.ravel())) / a.size
     assert oracle.color_mse(a, b) == pytest.approx(float(exact), rel=1e-14)
+
+
+def _ssim_reference(a, b):
+    """SSIM by a second route: the Gaussian window as an outer product, numpy's correlation over valid positions."""
+    from scipy.signal import correlate2d
+    x = np.arange(11) - 5
+    g = np.exp(-(x * x) / 4.5)
+    w = np.outer(g, g)
+    w /= w.sum()
+    C1, C2 = 1e-4, 9e-4
+    vals = []
+    for c in range(3):
+        f = lambda img: correlate2d(img, w, mode="valid")
+        ma, mb = f(a[c]), f(b[c])
+        va, vb, cab = f(a[c] * a[c]) - ma * ma, f(b[c] * b[c]) - mb * mb, f(a[c] * b[c]) - ma * mb
+        vals.append(((2 * ma * mb + C1) * (2 * cab + C2)) / ((ma * ma + mb * mb + C1) * (va + vb + C2)))
+    return float(np.mean(vals))
+
+
+def test_ssim_pins():
+    rng = np.random.default_rng(5)
+    a = rng.uniform(size=(3, 19, 23))
+    assert oracle.ssim(a, a) == 1.0                                     # identical images: exactly 1
+    b = np.clip(a + rng.normal(scale=0.1, size=a.shape), 0, 1)
+    assert oracle.ssim(a, b) == pytest.approx(oracle.ssim(b, a), rel=1e-14)   # symmetric
+    assert oracle.ssim(a, b) == pytest.approx(_ssim_reference(a, b), rel=1e-12)
+    # constant images p and q: the structure terms vanish, SSIM = (2pq + C1) / (p^2 + q^2 + C1)
+    p, q = 0.3, 0.7
+    want = (2 * p * q + 1e-4) / (p * p + q * q + 1e-4)
+    assert oracle.ssim(np.full((3, 12, 15), p), np.full((3, 12, 15), q)) == pytest.approx(want, rel=1e-9)
+    assert math.isnan(oracle.ssim(np.zeros((3, 10, 40)), np.zeros((3, 10, 40))))   # no window fits
