@@ -297,6 +297,7 @@ def _extras_quality(b, devc, peak, ex):
     sc = scenes.sequence_1080p_scene()
     H, W = 1080, 1920
     psnr = {1: [], 2: [], 3: []}
+    ssim = {1: [], 2: [], 3: []}
     ws = b.workspace(b.exw_workspace_bytes(b.OP_STATS, W, H), devc)
     for f in range(8):
         c, d, m = (torch.from_numpy(x).to(devc) for x in scenes.render(sc, float(f)))
@@ -304,6 +305,7 @@ def _extras_quality(b, devc, peak, ex):
         for k in (1, 2, 3):
             gt = torch.from_numpy(scenes.ground_truth(sc, float(f), k)).to(devc)
             psnr[k].append(b.exw_psnr(out[k - 1], gt, ws))
+            ssim[k].append(b.exw_ssim(out[k - 1], gt, ws))
     c, d, m = (torch.from_numpy(x).to(devc) for x in scenes.render(sc, 0.0))
     gt = torch.from_numpy(scenes.ground_truth(sc, 0.0, 1)).to(devc)
     out = torch.empty_like(c)
@@ -316,14 +318,20 @@ def _extras_quality(b, devc, peak, ex):
     def mse():
         b.lib().exw_color_mse(c.data_ptr(), gt.data_ptr(), b.F32, W, H, res.data_ptr(), ws.data_ptr(), ws.numel(),
                               b._stream(None, devc))
+    def ssm():
+        b.lib().exw_ssim(c.data_ptr(), gt.data_ptr(), b.F32, W, H, res.data_ptr(), ws.data_ptr(), ws.numel(),
+                         b._stream(None, devc))
     ms_v = _event_ms(var, 50)
     ms_m = _event_ms(mse, 50)
+    ms_s = _event_ms(ssm, 20)
     ex["quality_and_stats"] = {
         "psnr_db_vs_ground_truth": {f"P_{k}": round(sum(v) / len(v), 3) for k, v in psnr.items()},
+        "ssim_vs_ground_truth": {f"P_{k}": round(sum(v) / len(v), 5) for k, v in ssim.items()},
+        "ssim_us": ms_s * 1e3,
         "mv_variance_us": ms_v * 1e3, "mv_variance_hbm_frac": 8 * W * H / (ms_v / 1e3) / 1e9 / peak,
         "color_mse_us": ms_m * 1e3, "color_mse_hbm_frac": 24 * W * H / (ms_m / 1e3) / 1e9 / peak,
-        "workload": "PSNR: 8 frames of the 1920x1080 FP32 sequence, P_1..P_3 with fill against the scene rendered "
-                    "at t + k/4; statistics: one 1920x1080 frame (8 B/px motion, 2 x 12 B/px colour)"}
+        "workload": "PSNR and SSIM: 8 frames of the 1920x1080 FP32 sequence, P_1..P_3 with fill against the scene "
+                    "rendered at t + k/4; statistics: one 1920x1080 frame (8 B/px motion, 2 x 12 B/px colour)"}
 
 
 def _extras_4k(b, devc, names, peak, ex):

@@ -207,6 +207,14 @@ EXW_API exw_status exw_mv_variance(const float *mv, int W, int H, double *out, v
 EXW_API exw_status exw_color_mse(const void *a, const void *b, exw_dtype cdt, int W, int H, double *out, void *ws,
                                  size_t ws_bytes, exw_stream_t stream);
 
+/* Structural similarity of two colour images a, b [3][H][W] of type cdt in [0, 1] (the SSIM of the reward, Sec.
+ * IV-C, Eq. 3, read as the standard index: 11 x 11 Gaussian window, sigma 1.5, C1 = 1e-4, C2 = 9e-4, over every
+ * window position wholly inside the image, averaged over positions and channels).  Moments in FP32 on values
+ * shifted by -1/2, the mean in FP64 in a fixed order.  Needs W, H >= 11.  out [1] is a DEVICE float64.
+ * Workspace: as exw_mv_variance. */
+EXW_API exw_status exw_ssim(const void *a, const void *b, exw_dtype cdt, int W, int H, double *out, void *ws,
+                            size_t ws_bytes, exw_stream_t stream);
+
 /* Adjoint of stage (b) for fraction k/denom with every integer decision held fixed (target, winner, taps, tap
  * participation, mask).  grad_out [3][H][W] float32 = dL/d out_color; accumulates (+=) into grad_color
  * [3][H][W] float32 (dL/d colour: w_t / sum w per participating tap) and grad_mv [2][H][W] float32 (dL/d motion

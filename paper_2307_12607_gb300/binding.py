@@ -282,6 +282,21 @@ def exw_color_mse(a, b, ws=None, stream=None) -> float:
     return float(out.item())
 
 
+def exw_ssim(a, b, ws=None, stream=None) -> float:
+    """Mean SSIM of two [3][H][W] colour images in [0, 1] of one dtype (Sec. IV-C, Eq. 3; 11 x 11 Gaussian window,
+    valid positions; W, H >= 11).  Synchronises to read the result back."""
+    H, W = int(a.shape[1]), int(a.shape[2])
+    _dev(a, "a", None, (3, H, W))
+    _dev(b, "b", a.dtype, (3, H, W))
+    dev = a.device
+    if ws is None:
+        ws = workspace(exw_workspace_bytes(OP_STATS, W, H, F32, 1, 1), dev)
+    out = torch.empty(1, dtype=torch.float64, device=dev)
+    _check(lib().exw_ssim(a.data_ptr(), b.data_ptr(), _cdt(a), W, H, out.data_ptr(), ws.data_ptr(), ws.numel(),
+                          _stream(stream, dev)))
+    return float(out.item())
+
+
 def exw_psnr(a, b, ws=None, stream=None) -> float:
     """PSNR = 10 log10(255^2 / MSE) of colours in [0, 1] scaled by 255 (Sec. IV-C, Eq. 3); inf for equal images."""
     import math

@@ -144,6 +144,16 @@ exw_status exw_mv_variance(const float *mv, int W, int H, double *out, void *ws,
     return launch_mv_variance(mv, W, H, out, ws, (cudaStream_t)stream) == cudaSuccess ? EXW_OK : EXW_ERR_CUDA;
 }
 
+exw_status exw_ssim(const void *a, const void *b, exw_dtype cdt, int W, int H, double *out, void *ws,
+                    size_t ws_bytes, exw_stream_t stream) {
+    if (!size_ok(W, H) || W < 11 || H < 11 || !dtype_ok(cdt) || !aligned(a, csize(cdt)) || !aligned(b, csize(cdt)) ||
+        !aligned(out, 8))
+        return EXW_ERR_INVALID_ARG;
+    if (!aligned16(ws) || ws_bytes < stats_workspace_bytes()) return EXW_ERR_WORKSPACE;
+    if (entry_check() != EXW_OK) return EXW_ERR_CUDA;
+    return launch_ssim(a, b, cdt, W, H, out, ws, (cudaStream_t)stream) == cudaSuccess ? EXW_OK : EXW_ERR_CUDA;
+}
+
 exw_status exw_color_mse(const void *a, const void *b, exw_dtype cdt, int W, int H, double *out, void *ws,
                          size_t ws_bytes, exw_stream_t stream) {
     if (!size_ok(W, H) || !dtype_ok(cdt) || !aligned(a, csize(cdt)) || !aligned(b, csize(cdt)) || !aligned(out, 8))

@@ -135,6 +135,8 @@ size_t stats_workspace_bytes();
 cudaError_t launch_mv_variance(const float *mv, int W, int H, double *out, void *ws, cudaStream_t s);
 cudaError_t launch_color_mse(const void *a, const void *b, exw_dtype cdt, int W, int H, double *out, void *ws,
                              cudaStream_t s);
+cudaError_t launch_ssim(const void *a, const void *b, exw_dtype cdt, int W, int H, double *out, void *ws,
+                        cudaStream_t s);
 cudaError_t launch_warp_tiles(const TileParams &p, exw_dtype cdt, cudaStream_t s);
 cudaError_t launch_fill_tiles(const TileParams &p, exw_dtype cdt, cudaStream_t s);
 cudaError_t launch_fixup(const TileParams &p, exw_dtype cdt, cudaStream_t s);

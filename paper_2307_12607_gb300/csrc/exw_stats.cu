@@ -147,6 +147,107 @@ __global__ void __launch_bounds__(kStatThreads) color_mse_kernel(const CT *__res
     ws->arrived = 0u;
 }
 
+// SSIM (Sec. IV-C, Eq. 3; the standard 11 x 11 Gaussian-window index, sigma 1.5, C1 = 1e-4, C2 = 9e-4 for
+// colours in [0, 1]): each block takes 32 x 32 output positions at a time (a 42 x 42 input tile per channel in
+// shared memory), filters the five maps a, b, a^2, b^2, ab horizontally into shared memory, then vertically per
+// output, in FP32 on values shifted by -1/2 (variances and covariance are shift-invariant; the shift keeps the
+// raw second moments small), and sums the per-position SSIM in FP64 in a fixed order.
+constexpr int kSsimTile = 32, kSsimIn = kSsimTile + 10;
+
+template <typename CT>
+__global__ void __launch_bounds__(kStatThreads) ssim_kernel(const CT *__restrict__ a, const CT *__restrict__ b,
+                                                            int W, int H, StatWs *ws, double *out) {
+    __shared__ float ia[kSsimIn][kSsimIn + 1], ib[kSsimIn][kSsimIn + 1];
+    __shared__ float hor[5][kSsimIn][kSsimTile];
+    __shared__ float g[11];
+    __shared__ double red[kStatThreads / 32];
+    const int tid = threadIdx.x;
+    if (tid < 11) {
+        float e[11], sum = 0.0f;
+        for (int i = 0; i < 11; ++i) {
+            e[i] = expf(-(float)((i - 5) * (i - 5)) / 4.5f);
+            sum += e[i];
+        }
+        g[tid] = e[tid] / sum;
+    }
+    const int OW = W - 10, OH = H - 10;
+    const int ntx = (OW + kSsimTile - 1) / kSsimTile, nt = ntx * ((OH + kSsimTile - 1) / kSsimTile);
+    const size_t plane = (size_t)W * H;
+    const float C1 = 1e-4f, C2 = 9e-4f;
+    double acc = 0.0;
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+        const int X0 = (t % ntx) * kSsimTile, Y0 = (t / ntx) * kSsimTile;
+        for (int c = 0; c < 3; ++c) {
+            __syncthreads();  // the previous channel's tiles are consumed
+            for (int i = tid; i < kSsimIn * kSsimIn; i += kStatThreads) {
+                const int r = i / kSsimIn, q = i - r * kSsimIn, x = X0 + q, y = Y0 + r;
+                const bool in = x < W && y < H;
+                const size_t o = c * plane + (size_t)y * W + x;
+                ia[r][q] = in ? to_f<CT>(a[o]) - 0.5f : 0.0f;
+                ib[r][q] = in ? to_f<CT>(b[o]) - 0.5f : 0.0f;
+            }
+            __syncthreads();
+            for (int i = tid; i < kSsimIn * kSsimTile; i += kStatThreads) {
+                const int r = i / kSsimTile, q = i - r * kSsimTile;
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
+#pragma unroll
+                for (int j = 0; j < 11; ++j) {
+                    const float va = ia[r][q + j], vb = ib[r][q + j], w = g[j];
+                    s0 = fmaf(w, va, s0);
+                    s1 = fmaf(w, vb, s1);
+                    s2 = fmaf(w, va * va, s2);
+                    s3 = fmaf(w, vb * vb, s3);
+                    s4 = fmaf(w, va * vb, s4);
+                }
+                hor[0][r][q] = s0;
+                hor[1][r][q] = s1;
+                hor[2][r][q] = s2;
+                hor[3][r][q] = s3;
+                hor[4][r][q] = s4;
+            }
+            __syncthreads();
+            for (int i = tid; i < kSsimTile * kSsimTile; i += kStatThreads) {
+                const int r = i / kSsimTile, q = i - r * kSsimTile;
+                if (X0 + q >= OW || Y0 + r >= OH) continue;
+                float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int k = 0; k < 11; ++k) {
+                    const float w = g[k];
+#pragma unroll
+                    for (int v = 0; v < 5; ++v) m[v] = fmaf(w, hor[v][r + k][q], m[v]);
+                }
+                const float va2 = m[2] - m[0] * m[0], vb2 = m[3] - m[1] * m[1], cab = m[4] - m[0] * m[1];
+                const float mua = m[0] + 0.5f, mub = m[1] + 0.5f;
+                const float num = (2.0f * mua * mub + C1) * (2.0f * cab + C2);
+                const float den = (mua * mua + mub * mub + C1) * (va2 + vb2 + C2);
+                acc += (double)(num / den);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    __syncthreads();
+    if (tid == 0) {
+        double s = red[0];
+        for (int w = 1; w < kStatThreads / 32; ++w) s += red[w];
+        ws->part[blockIdx.x].n = s;
+    }
+    if (!last_block(&ws->arrived)) return;
+    static_assert(kStatThreads == kStatBlocks, "one partial per thread");
+    double u = tid < (int)gridDim.x ? ws->part[tid].n : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xFFFFFFFFu, u, o);
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = u;
+    __syncthreads();
+    if (tid != 0) return;
+    double s = red[0];
+    for (int w = 1; w < kStatThreads / 32; ++w) s += red[w];
+    out[0] = s / (3.0 * (double)OW * (double)OH);
+    ws->arrived = 0u;
+}
+
 }  // namespace
 
 size_t stats_workspace_bytes() { return (sizeof(StatWs) + 255) & ~(size_t)255; }
@@ -175,6 +276,26 @@ cudaError_t launch_color_mse(const void *a, const void *b, exw_dtype cdt, int W,
                                                                       static_cast<StatWs *>(ws), out);
     count_launch();
     timing_end("exw_color_mse", s);
+    return cudaGetLastError();
+}
+
+}  // namespace exw
+
+namespace exw {
+
+cudaError_t launch_ssim(const void *a, const void *b, exw_dtype cdt, int W, int H, double *out, void *ws,
+                        cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(&static_cast<StatWs *>(ws)->arrived, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    timing_begin("exw_ssim", s);
+    if (cdt == EXW_F16)
+        ssim_kernel<__half><<<kStatBlocks, kStatThreads, 0, s>>>((const __half *)a, (const __half *)b, W, H,
+                                                                  static_cast<StatWs *>(ws), out);
+    else
+        ssim_kernel<float><<<kStatBlocks, kStatThreads, 0, s>>>((const float *)a, (const float *)b, W, H,
+                                                                 static_cast<StatWs *>(ws), out);
+    count_launch();
+    timing_end("exw_ssim", s);
     return cudaGetLastError();
 }
 

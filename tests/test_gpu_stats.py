@@ -70,3 +70,21 @@ def test_color_mse_matches_oracle(b, dtype, W, H):
     assert got == pytest.approx(want, rel=max(1e-12, 3 * W * H * 2.0 ** -53), abs=0)
     assert b.exw_color_mse(xa, ya) == got
     assert b.exw_color_mse(xa, xa) == 0.0 and b.exw_psnr(xa, xa) == float("inf")
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
+@pytest.mark.parametrize("W,H", [(11, 11), (37, 29), (200, 150), (640, 360)])
+def test_ssim_matches_oracle(b, dtype, W, H):
+    # the kernel keeps the window moments in FP32 on values shifted to [-1/2, 1/2]: each moment is within about
+    # 1e-7 of the FP64 one, and an error e in a variance moves a window's SSIM by at most e / C2 (C2 = 9e-4), so
+    # the bar on the mean is 2e-4
+    rng = np.random.default_rng(W * H)
+    x = rng.uniform(size=(3, H, W)).astype(np.float32)
+    y = np.clip(x + rng.normal(scale=0.08, size=x.shape), 0, 1).astype(np.float32)
+    y[:, : H // 3, : W // 3] = 0.25                        # a flat patch: small variances
+    xa, ya = torch.from_numpy(x).to(dtype).cuda(), torch.from_numpy(y).to(dtype).cuda()
+    want = oracle.ssim(xa.cpu().double().numpy(), ya.cpu().double().numpy())
+    got = b.exw_ssim(xa, ya)
+    assert abs(got - want) <= 2e-4
+    assert b.exw_ssim(xa, ya) == got
+    assert abs(b.exw_ssim(xa, xa) - 1.0) <= 1e-6
