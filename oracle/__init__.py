@@ -61,6 +61,8 @@ def _load():
             lib.oracle_mv_variance.restype = None
             lib.oracle_color_mse.argtypes = [P, P, I, I]
             lib.oracle_color_mse.restype = ctypes.c_double
+            lib.oracle_carry_motion.argtypes = [P, P, P, P, I, I, P, P]
+            lib.oracle_carry_motion.restype = None
             lib.oracle_ssim.argtypes = [P, P, I, I]
             lib.oracle_ssim.restype = ctypes.c_double
             for f in (lib.oracle_splat, lib.oracle_mask, lib.oracle_warp, lib.oracle_fill_holes,
@@ -220,3 +222,33 @@ def ssim(a, b) -> float:
     a = _f64(a)
     b = _f64(b)
     return float(_load().oracle_ssim(_ptr(a), _ptr(b), a.shape[2], a.shape[1]))
+
+
+def carry_motion(keys, mask, depth, mv):
+    """Depth [H][W] and motion [2][H][W] of a warped frame for warping it again (Table V, S5/S6; see the C code)."""
+    keys = np.ascontiguousarray(keys).view(np.uint64)
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    depth = _f32(depth)
+    mv = _f32(mv)
+    H, W = depth.shape
+    d_out = np.empty((H, W), np.float32)
+    mv_out = np.empty((2, H, W), np.float32)
+    _load().oracle_carry_motion(_ptr(keys), _ptr(mask), _ptr(depth), _ptr(mv), W, H, _ptr(d_out), _ptr(mv_out))
+    return d_out, mv_out
+
+
+def warp_recursive(color, depth, mv, steps: int, fill: bool = True):
+    """Decision path S6 (Table V): P_1 = W(F), P_{i+1} = W(P_i), each a quarter step (k = 1 of 4) of the motion each
+    pixel carries (carry_motion); FP64 colour, filled after each warp when ``fill``.  Returns [(colour, mask)]."""
+    c = _f64(color)
+    d, m = _f32(depth), _f32(mv)
+    outs = []
+    for _ in range(steps):
+        keys = splat(d, m, 1, 4)
+        out, mask = warp(c, d, m, keys, 1, 4)
+        if fill:
+            out = fill_holes(out, mask)
+        outs.append((out, mask))
+        d, m = carry_motion(keys, mask, d, m)
+        c = out
+    return outs

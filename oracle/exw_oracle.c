@@ -465,3 +465,24 @@ double oracle_ssim(const double *a, const double *b, int W, int H) {
     }
     return total / (3.0 * (double)(W - 10) * (double)(H - 10));
 }
+
+/* Depth and motion of a warped frame, so that it can be warped again (the recursive warps W(P_1), W(P_2) of the
+ * decision paths S5 and S6, Table V; the paper leaves the motion of a predicted frame open, read as the motion of
+ * the surface that landed there): a target that is not a hole (mask 0) takes the depth and motion of its winner,
+ * the source in its key; a hole gets depth NaN (it never lands again) and motion 0. */
+void oracle_carry_motion(const uint64_t *keys, const uint8_t *mask, const float *depth, const float *mv, int W, int H,
+                         float *depth_out, float *mv_out) {
+    const size_t n = (size_t)W * (size_t)H;
+    for (size_t q = 0; q < n; ++q) {
+        if (mask[q] == 0 && keys[q] != ORACLE_EMPTY) {
+            const size_t p = (size_t)(keys[q] & 0xFFFFFFFFull);
+            depth_out[q] = depth[p];
+            mv_out[q] = mv[p];
+            mv_out[n + q] = mv[n + p];
+        } else {
+            depth_out[q] = NAN;
+            mv_out[q] = 0.0f;
+            mv_out[n + q] = 0.0f;
+        }
+    }
+}

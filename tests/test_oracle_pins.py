@@ -608,3 +608,48 @@ def test_ssim_pins():
     want = (2 * p * q + 1e-4) / (p * p + q * q + 1e-4)
     assert oracle.ssim(np.full((3, 12, 15), p), np.full((3, 12, 15), q)) == pytest.approx(want, rel=1e-9)
     assert math.isnan(oracle.ssim(np.zeros((3, 10, 40)), np.zeros((3, 10, 40))))   # no window fits
+
+
+# ----------------------------------------------------------------------------------------------------------------
+# Recursive warps (Table V, S5/S6): the warped frame carries its winners' depth and motion
+# ----------------------------------------------------------------------------------------------------------------
+
+def test_carry_motion_zero_motion_is_identity():
+    # a smooth surface (no crack can form) that does not move: every pixel is its own winner
+    color, _, _ = scenes.random_frame(23, 17, 31)
+    yy, xx = np.mgrid[0:17, 0:23]
+    depth = (40.0 + 0.01 * xx + 0.02 * yy).astype(np.float32)
+    mv = np.zeros((2, 17, 23), np.float32)
+    keys = oracle.splat(depth, mv, 1, 4)
+    out, mask = oracle.warp(color, depth, mv, keys, 1, 4)
+    d1, m1 = oracle.carry_motion(keys, mask, depth, mv)
+    assert np.array_equal(d1, depth) and np.array_equal(m1, mv) and np.array_equal(out, color.astype(np.float64))
+
+
+def test_two_quarter_steps_of_a_translation_equal_one_half_step():
+    # every pixel moves by (8, -4) per frame: a quarter step is (2, -1) whole pixels; warping the warped frame again
+    # (with the carried motion) equals warping the source by 2/4 wherever both sources lie in the frame
+    W, H = 40, 30
+    color, _, _ = scenes.random_frame(W, H, 32)
+    yy, xx = np.mgrid[0:H, 0:W]
+    depth = (40.0 + 0.01 * xx + 0.02 * yy).astype(np.float32)
+    mv = np.empty((2, H, W), np.float32)
+    mv[0], mv[1] = 8.0, -4.0
+    two = oracle.warp_recursive(color, depth, mv, 2, fill=False)
+    keys2 = oracle.splat(depth, mv, 2, 4)
+    half, hmask = oracle.warp(color, depth, mv, keys2, 2, 4)
+    inner = (slice(2, H - 2), slice(4, W - 4))
+    assert np.array_equal(two[1][1][inner], hmask[inner]) and not hmask[inner].any()
+    assert np.array_equal(two[1][0][(slice(None),) + inner], half[(slice(None),) + inner])
+
+
+def test_carried_holes_never_land_again():
+    color, depth, mv = scenes.random_frame(31, 21, 33, mv_scale=6.0, invalid_fraction=0.1)
+    keys = oracle.splat(depth, mv, 1, 4)
+    _, mask = oracle.warp(color, depth, mv, keys, 1, 4)
+    d1, m1 = oracle.carry_motion(keys, mask, depth, mv)
+    holes = mask != 0
+    assert holes.any() and np.isnan(d1[holes]).all() and (m1[:, holes] == 0).all()
+    idx = (keys.view(np.uint64)[~holes] & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    assert np.array_equal(d1[~holes], depth.ravel()[idx])
+    assert np.array_equal(m1[0][~holes], mv[0].ravel()[idx]) and np.array_equal(m1[1][~holes], mv[1].ravel()[idx])
