@@ -324,14 +324,26 @@ def _extras_quality(b, devc, peak, ex):
     ms_v = _event_ms(var, 50)
     ms_m = _event_ms(mse, 50)
     ms_s = _event_ms(ssm, 20)
+    # decision path S6 (Table V): P_1 = W(F), P_2 = W(P_1), P_3 = W(P_2) through the carried depth and motion
+    s6 = {1: [], 2: [], 3: []}
+    for f in range(8):
+        cf, df, mf = (torch.from_numpy(x).to(devc) for x in scenes.render(sc, float(f)))
+        chain = b.exw_warp_recursive(cf, df, mf, 3)
+        for k in (1, 2, 3):
+            gt = torch.from_numpy(scenes.ground_truth(sc, float(f), k)).to(devc)
+            s6[k].append(b.exw_psnr(chain[k - 1][0], gt, ws))
+    ms_chain = _event_ms(lambda: b.exw_warp_recursive(c, d, m, 3), 10)
     ex["quality_and_stats"] = {
         "psnr_db_vs_ground_truth": {f"P_{k}": round(sum(v) / len(v), 3) for k, v in psnr.items()},
         "ssim_vs_ground_truth": {f"P_{k}": round(sum(v) / len(v), 5) for k, v in ssim.items()},
         "ssim_us": ms_s * 1e3,
+        "s6_recursive_psnr_db": {f"P_{k}": round(sum(v) / len(v), 3) for k, v in s6.items()},
+        "s6_recursive_chain_ms": ms_chain,
         "mv_variance_us": ms_v * 1e3, "mv_variance_hbm_frac": 8 * W * H / (ms_v / 1e3) / 1e9 / peak,
         "color_mse_us": ms_m * 1e3, "color_mse_hbm_frac": 24 * W * H / (ms_m / 1e3) / 1e9 / peak,
         "workload": "PSNR and SSIM: 8 frames of the 1920x1080 FP32 sequence, P_1..P_3 with fill against the scene "
-                    "rendered at t + k/4; statistics: one 1920x1080 frame (8 B/px motion, 2 x 12 B/px colour)"}
+                    "rendered at t + k/4 (direct warps of F_t, and the recursive chain of decision path S6); "
+                    "statistics: one 1920x1080 frame (8 B/px motion, 2 x 12 B/px colour)"}
 
 
 def _extras_4k(b, devc, names, peak, ex):

@@ -193,6 +193,16 @@ EXW_API exw_status exw_extrapolate_host(const exw_frame *frames_host, const exw_
                                         const exw_frame_out *out_dev, int chunk, void *ws, size_t ws_bytes,
                                         exw_stream_t stream);
 
+/* Depth and motion of a warped frame, so that it can be warped again -- the recursive warps W(P_1), W(P_2) of the
+ * decision paths S5 and S6 (Table V; the paper leaves the motion of a predicted frame open, read as the motion of
+ * the surface that landed there).  keys [H][W] from exw_splat_motion and mask [H][W] from exw_warp of the same
+ * fraction; depth, mv the source frame's.  A target that is not a hole takes its winner's depth and motion (bit
+ * copies); a hole gets depth NaN (it never lands again) and motion 0.  depth_out [H][W], mv_out [2][H][W] device
+ * float32, written.  Chain: splat, warp (+ fill), carry, then splat and warp the warped colour with the carried
+ * depth and motion (k = 1 of 4 per step). */
+EXW_API exw_status exw_carry_motion(const uint64_t *keys, const uint8_t *mask, const float *depth, const float *mv,
+                                    int W, int H, float *depth_out, float *mv_out, exw_stream_t stream);
+
 /* Motion-variance features Var_x(F_mv), Var_y(F_mv) of the decision stage's environment vector E_t (Sec. IV-C,
  * Eq. 1; the feature is motivated in Sec. III-D): over every pixel of mv [2][H][W] whose two components are
  * finite, the population variance of the x component and of the y component.  out [3] is a DEVICE float64 array:

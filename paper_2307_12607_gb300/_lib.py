@@ -33,6 +33,7 @@ PROTOTYPES = {
     "exw_extrapolate": (I, [P, I, I, U, P, P, SZ, P]),
     "exw_extrapolate_host": (I, [P, P, I, I, U, P, P, I, P, SZ, P]),
     "exw_mv_variance": (I, [P, I, I, P, P, SZ, P]),
+    "exw_carry_motion": (I, [P, P, P, P, I, I, P, P, P]),
     "exw_color_mse": (I, [P, P, I, I, I, P, P, SZ, P]),
     "exw_ssim": (I, [P, P, I, I, I, P, P, SZ, P]),
     "exw_warp_backward": (I, [P, P, I, P, P, P, I, I, I, I, P, P, P, SZ, P]),

@@ -252,6 +252,40 @@ def exw_extrapolate_host(color, depth, mv, nfrac: int = 3, fill: bool = True, ou
 OP_STATS = 4
 
 
+def exw_carry_motion(keys, mask, depth, mv, depth_out=None, mv_out=None, stream=None):
+    """Depth and motion of a warped frame for warping it again (Table V, S5/S6): returns (depth [H][W], motion
+    [2][H][W]) -- the winners' for non-holes, NaN depth and zero motion for holes."""
+    W, H = _hw(depth)
+    dev = depth.device
+    if depth_out is None:
+        depth_out = torch.empty((H, W), dtype=torch.float32, device=dev)
+    if mv_out is None:
+        mv_out = torch.empty((2, H, W), dtype=torch.float32, device=dev)
+    _check(lib().exw_carry_motion(_dev(keys, "keys", torch.int64, (H, W)), _dev(mask, "mask", torch.uint8, (H, W)),
+                                  _dev(depth, "depth", torch.float32), _dev(mv, "mv", torch.float32, (2, H, W)), W, H,
+                                  _dev(depth_out, "depth_out", torch.float32, (H, W)),
+                                  _dev(mv_out, "mv_out", torch.float32, (2, H, W)), _stream(stream, dev)))
+    return depth_out, mv_out
+
+
+def exw_warp_recursive(color, depth, mv, steps: int = 3, fill: bool = True, stream=None):
+    """Decision path S6 (Table V): P_1 = W(F), P_{i+1} = W(P_i), each a quarter step (k = 1 of 4) of the motion
+    every pixel carries (exw_carry_motion).  Returns [(colour [3][H][W], mask [H][W])] for the ``steps`` frames."""
+    W, H = _hw(depth)
+    ws = workspace(exw_workspace_bytes(OP_FILL_HOLES, W, H, _cdt(color)), color.device) if fill else None
+    c, d, m = color, depth, mv
+    outs = []
+    for _ in range(int(steps)):
+        keys = exw_splat_motion(d, m, 1, 4, stream=stream)
+        out, mask = exw_warp(c, d, m, keys, 1, 4, stream=stream)
+        if fill:
+            exw_fill_holes(out, mask, ws, stream=stream)
+        outs.append((out, mask))
+        d, m = exw_carry_motion(keys, mask, d, m, stream=stream)
+        c = out
+    return outs
+
+
 def exw_mv_variance(mv, ws=None, stream=None):
     """Motion-variance features (count, Var_x, Var_y) of a [2][H][W] float32 motion field (Sec. IV-C, Eq. 1):
     population variances over the pixels whose two components are finite, FP64 on the device (reads the result

@@ -136,6 +136,17 @@ size_t exw_workspace_bytes(exw_op op, int W, int H, exw_dtype cdt, int nframes, 
     return 0;
 }
 
+exw_status exw_carry_motion(const uint64_t *keys, const uint8_t *mask, const float *depth, const float *mv, int W,
+                            int H, float *depth_out, float *mv_out, exw_stream_t stream) {
+    if (!size_ok(W, H) || !aligned(keys, 8) || !aligned(mask, 1) || !aligned(depth, 4) || !aligned(mv, 4) ||
+        !aligned(depth_out, 4) || !aligned(mv_out, 4))
+        return EXW_ERR_INVALID_ARG;
+    if (entry_check() != EXW_OK) return EXW_ERR_CUDA;
+    return launch_carry_motion(keys, mask, depth, mv, W, H, depth_out, mv_out, (cudaStream_t)stream) == cudaSuccess
+               ? EXW_OK
+               : EXW_ERR_CUDA;
+}
+
 exw_status exw_mv_variance(const float *mv, int W, int H, double *out, void *ws, size_t ws_bytes,
                            exw_stream_t stream) {
     if (!size_ok(W, H) || !aligned(mv, 4) || !aligned(out, 8)) return EXW_ERR_INVALID_ARG;

@@ -101,6 +101,39 @@ cudaError_t launch_zero(void *p, size_t bytes, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Depth and motion of a warped frame for warping it again (the recursive warps of decision paths S5/S6, Table V):
+// a target that is not a hole takes its winner's depth and motion bits; a hole gets depth NaN (it never lands
+// again) and motion 0.  One target per thread (coalesced reads of keys and mask, gathered reads of the winners).
+__global__ void __launch_bounds__(256) carry_motion_kernel(const uint64_t *__restrict__ keys,
+                                                           const uint8_t *__restrict__ mask,
+                                                           const float *__restrict__ depth,
+                                                           const float *__restrict__ mv, size_t n,
+                                                           float *__restrict__ depth_out, float *__restrict__ mv_out) {
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const uint64_t k = keys[q];
+    if (mask[q] == 0 && k != kKeyEmpty) {
+        const size_t p = (size_t)(k & 0xFFFFFFFFull);
+        depth_out[q] = __ldg(depth + p);
+        mv_out[q] = __ldg(mv + p);
+        mv_out[n + q] = __ldg(mv + n + p);
+    } else {
+        depth_out[q] = __int_as_float(0x7FC00000);
+        mv_out[q] = 0.0f;
+        mv_out[n + q] = 0.0f;
+    }
+}
+
+cudaError_t launch_carry_motion(const uint64_t *keys, const uint8_t *mask, const float *depth, const float *mv,
+                                int W, int H, float *depth_out, float *mv_out, cudaStream_t s) {
+    const size_t n = (size_t)W * H;
+    timing_begin("exw_carry_motion", s);
+    carry_motion_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(keys, mask, depth, mv, n, depth_out, mv_out);
+    count_launch();
+    timing_end("exw_carry_motion", s);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_splat_global(const float *depth, const float *mv, int W, int H, int k, int L, uint64_t *keys,
                                 cudaStream_t s) {
     const dim3 g((unsigned)((W + 255) / 256), (unsigned)H, 1);

@@ -122,6 +122,8 @@ constexpr int kWinXF16 = 64, kWinYF16 = 56;
 // Launchers (exw_fwd.cu, exw_aux.cu, exw_bwd.cu).  Each returns the launch error.
 cudaError_t launch_clear_keys(uint64_t *keys, size_t n, cudaStream_t s);
 cudaError_t launch_zero(void *p, size_t bytes, cudaStream_t s);
+cudaError_t launch_carry_motion(const uint64_t *keys, const uint8_t *mask, const float *depth, const float *mv,
+                                int W, int H, float *depth_out, float *mv_out, cudaStream_t s);
 cudaError_t launch_splat_global(const float *depth, const float *mv, int W, int H, int k, int L, uint64_t *keys,
                                 cudaStream_t s);
 cudaError_t launch_bounds(const float *depth, const float *mv, int W, int H, float4 *tile_bounds, float2 *tile_depth,
