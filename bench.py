@@ -67,8 +67,8 @@ def dist_env():
 # capture (a smaller launch; the engine's traffic grows in proportion to the frames of a launch), with the hash of
 # the kernel sources it was taken on: reported only while the sources are unchanged, else null.
 MEASURED_TRAFFIC = {
-    ("exw_engine", "sequence_1080p_fp32"): ((238.57e6 + 279.08e6) / 4, "bcb5f60446ec236a"),
-    ("exw_engine", "warp_4k_fp16"): (105.41e6 + 129.62e6, "bcb5f60446ec236a"),
+    ("exw_engine", "sequence_1080p_fp32"): ((238.34e6 + 279.37e6) / 4, "f6b4a8501eadcb2d"),
+    ("exw_engine", "warp_4k_fp16"): (105.39e6 + 129.86e6, "f6b4a8501eadcb2d"),
 }
 
 
