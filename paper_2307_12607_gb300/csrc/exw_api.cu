@@ -382,7 +382,11 @@ exw_status exw_extrapolate_host(const exw_frame *frames_host, const exw_frame *f
         exw_frame_out *od = out_dev != nullptr ? const_cast<exw_frame_out *>(out_dev) : direct.data();
         const exw_status st = exw_extrapolate(frames_dev + f0, n, nfrac, flags, od + (size_t)f0 * nfrac, ws, ws_bytes,
                                               stream);
-        if (st != EXW_OK) return st;
+        if (st != EXW_OK) {  // the copies already queued still finish before the caller's stream does
+            if (cudaEventRecord(hs->copied, hs->in) == cudaSuccess) cudaStreamWaitEvent(s, hs->copied, 0);
+            if (cudaEventRecord(hs->back, hs->out) == cudaSuccess) cudaStreamWaitEvent(s, hs->back, 0);
+            return st;
+        }
         if (out_dev == nullptr) continue;
         e = cudaEventRecord(hs->done, s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(hs->out, hs->done, 0);
@@ -395,10 +399,15 @@ exw_status exw_extrapolate_host(const exw_frame *frames_host, const exw_frame *f
         for (Run *r : {&oc, &om})
             if (e == cudaSuccess) e = copy_run(*r, nullptr, nullptr, 0, cudaMemcpyDeviceToHost, hs->out, true);
     }
-    // the caller's stream completes once the last outputs are in host memory
-    if (e == cudaSuccess && out_dev != nullptr) e = cudaEventRecord(hs->back, hs->out);
-    if (e == cudaSuccess && out_dev != nullptr) e = cudaStreamWaitEvent(s, hs->back, 0);
-    return e == cudaSuccess ? EXW_OK : EXW_ERR_CUDA;
+    // the caller's stream completes once the last outputs are in host memory -- and, after an error, once every
+    // copy already queued on the internal streams has finished
+    cudaError_t f = cudaEventRecord(hs->copied, hs->in);
+    if (f == cudaSuccess) f = cudaStreamWaitEvent(s, hs->copied, 0);
+    if (out_dev != nullptr) {
+        if (f == cudaSuccess) f = cudaEventRecord(hs->back, hs->out);
+        if (f == cudaSuccess) f = cudaStreamWaitEvent(s, hs->back, 0);
+    }
+    return e == cudaSuccess && f == cudaSuccess ? EXW_OK : EXW_ERR_CUDA;
 }
 
 exw_status exw_warp_backward(const float *grad_out, const void *color, exw_dtype cdt, const float *depth,
