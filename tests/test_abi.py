@@ -121,3 +121,98 @@ def test_binding_refuses_cpu_tensors():
     m = torch.zeros(2, 8, 8)
     with pytest.raises(ValueError, match="CUDA"):
         b.exw_splat_motion(d, m, 1)
+
+
+def test_recursive_and_statistics_argument_checks(lib):
+    # exw_carry_motion, exw_mv_variance, exw_color_mse, exw_ssim: null / misaligned pointers, bad sizes and colour
+    # types are refused with EXW_ERR_INVALID_ARG (1), a short or misaligned workspace with EXW_ERR_WORKSPACE (5)
+    a = 4096
+    big = 1 << 20
+    assert lib.exw_carry_motion(None, a, a, a, 8, 8, a, a, None) == 1
+    assert lib.exw_carry_motion(a + 4, a, a, a, 8, 8, a, a, None) == 1           # keys not 8-byte aligned
+    assert lib.exw_carry_motion(a, a, a, a, 0, 8, a, a, None) == 1               # W = 0
+    assert lib.exw_carry_motion(a, a, a, a, 8, 8, a + 2, a, None) == 1           # depth_out misaligned
+    assert lib.exw_mv_variance(None, 8, 8, a, a, big, None) == 1
+    assert lib.exw_mv_variance(a, 8, 8, a + 4, a, big, None) == 1                # out not 8-byte aligned
+    assert lib.exw_mv_variance(a, 8, 16385, a, a, big, None) == 1                # H too large
+    assert lib.exw_mv_variance(a, 8, 8, a, a, 16, None) == 5                     # workspace too small
+    assert lib.exw_mv_variance(a, 8, 8, a, a + 8, big, None) == 5                # workspace misaligned
+    assert lib.exw_color_mse(a, a, 7, 8, 8, a, a, big, None) == 1                # unknown colour type
+    assert lib.exw_color_mse(a, a + 2, 0, 8, 8, a, a, big, None) == 1            # FP32 b misaligned
+    assert lib.exw_color_mse(a, a, 1, 8, 8, a, None, big, None) == 5             # no workspace
+    assert lib.exw_ssim(a, a, 0, 10, 64, a, a, big, None) == 1                   # narrower than the window
+    assert lib.exw_ssim(a, a, 0, 64, 10, a, a, big, None) == 1                   # lower than the window
+    assert lib.exw_ssim(a, a + 1, 1, 64, 64, a, a, big, None) == 1               # FP16 b misaligned
+    assert lib.exw_ssim(a, a, 0, 64, 64, a, a, 8, None) == 5
+
+
+def test_backward_bounds_and_fill_argument_checks(lib):
+    a = 4096
+    big = 1 << 20
+    bwd = lib.exw_warp_backward
+    assert bwd(a, a, 0, a, a, a, 8, 8, 1, 3, a, a, a, big, None) == 1            # denom not a power of 2
+    assert bwd(a, a, 0, a, a, a, 8, 8, 5, 4, a, a, a, big, None) == 1            # k > denom
+    assert bwd(a, a, 0, a, a, a + 4, 8, 8, 1, 4, a, a, a, big, None) == 1        # keys misaligned
+    assert bwd(a, a, 0, a, a, a, 8, 8, 1, 4, None, a, a, big, None) == 1         # no grad_color
+    assert bwd(a, a, 0, a, a, None, 8, 8, 1, 4, a, a, a, 16, None) == 5          # keys recomputed: workspace short
+    assert lib.exw_l2_loss_grad(a, a, 0, a, 8, 8, a, None, None) == 1            # no loss scalar
+    assert lib.exw_l2_loss_grad(a, a, 3, a, 8, 8, a, a, None) == 1               # unknown colour type
+    assert lib.exw_motion_bounds(a, a, 8, 8, a + 4, a, a, big, None) == 1        # tile bounds not 16-byte aligned
+    assert lib.exw_motion_bounds(a, a, 8, 8, None, None, a, big, None) == 1      # no frame bounds
+    assert lib.exw_motion_bounds(a, a, 8, 8, None, a, a, 64, None) == 5
+    assert lib.exw_fill_holes_static(a, 0, a, 16385, 8, None) == 1
+    assert lib.exw_fill_holes_static(a + 2, 0, a, 8, 8, None) == 1               # FP32 colour misaligned
+    assert lib.exw_fill_holes_static(a, 1, None, 8, 8, None) == 1                # no mask
+    assert lib.exw_fill_holes_static(a, 0, a, 16384, 16384, None) == 5           # 262,144 fill tiles > 16,384
+    assert lib.exw_device_status(a + 8, None) == 1
+
+
+def _streams(sizes, cdt=0):
+    from paper_2307_12607_gb300 import _lib
+    d = (_lib.ExwStreamDesc * len(sizes))()
+    for i, (W, H) in enumerate(sizes):
+        d[i].src = _lib.ExwFrame(4096, 8192, 12288, W, H, cdt)
+        for j in range(3):
+            d[i].out[j] = _lib.ExwFrameOut(16384, 20480)
+    return d
+
+
+def test_batched_argument_checks_and_workspace(lib):
+    P = lambda x: ctypes.cast(x, ctypes.c_void_p)
+    d = _streams([(64, 64), (128, 72)])
+    ws = 1 << 24
+    assert lib.exw_extrapolate_batched(None, 1, 3, 0, 4096, ws, None, None) == 1
+    assert lib.exw_extrapolate_batched(P(d), 0, 3, 0, 4096, ws, None, None) == 1
+    assert lib.exw_extrapolate_batched(P(d), 2, 4, 0, 4096, ws, None, None) == 1          # nfrac > 3
+    assert lib.exw_extrapolate_batched(P(d), 2, 3, 1 << 7, 4096, ws, None, None) == 1     # unknown flag
+    many = _streams([(64, 64)] * 49)
+    assert lib.exw_extrapolate_batched(P(many), 49, 3, 0, 4096, ws, None, None) == 2      # > 48 streams
+    bad = _streams([(64, 64), (128, 72)])
+    bad[1].src.cdt = 7
+    assert lib.exw_extrapolate_batched(P(bad), 2, 3, 0, 4096, ws, None, None) == 1
+    bad = _streams([(64, 64), (128, 72)])
+    bad[0].out[2].mask = None
+    assert lib.exw_extrapolate_batched(P(bad), 2, 3, 0, 4096, ws, None, None) == 1
+    bad = _streams([(64, 64)], cdt=1)
+    bad[0].src.color = 4097                                                            # FP16 colour misaligned
+    assert lib.exw_extrapolate_batched(P(bad), 1, 3, 0, 4096, ws, None, None) == 1
+    # workspace: zero for bad descriptors, positive and growing with the streams and fractions otherwise
+    wb = lib.exw_batched_workspace_bytes
+    assert wb(None, 1, 3) == 0 and wb(P(d), 0, 3) == 0 and wb(P(d), 2, 0) == 0
+    assert wb(P(_streams([(0, 64)])), 1, 3) == 0
+    one, two = wb(P(d), 1, 3), wb(P(d), 2, 3)
+    assert 0 < one < two
+    assert wb(P(d), 2, 1) <= two
+    assert wb(P(_streams([(64, 64)] * 49)), 49, 3) == 0
+
+
+def test_tuner_lifecycle_on_host(lib):
+    t = lib.exw_tuner_create()
+    assert t
+    try:
+        buf = ctypes.create_string_buffer(64)
+        assert lib.exw_tuner_report(t, buf, 64) == 1 and buf.value == b""       # nothing tuned yet
+        assert lib.exw_tuner_report(None, None, 0) == 1
+    finally:
+        lib.exw_tuner_destroy(t)
+    lib.exw_tuner_destroy(None)                                                     # deleting NULL is a no-op
