@@ -214,6 +214,15 @@ def cpu_baseline(seconds: float, seq):
                       f"hole fill, FP64 C oracle single-threaded, {dt:.1f} s"}
 
 
+def sequence_config(frames: int, world: int) -> dict:
+    """The workload of one step (both arms report it): ``frames`` source frames of the 1080p sequence per GPU."""
+    return {"workload": "1920x1080 FP32 sequence: 60 source frames, 32 moving rectangles (5% 1-3 px slivers), "
+                        "|mv| <= 16 px; P_1..P_3 at t+k/4 with pull-push hole fill = 180 output frames per step per GPU",
+            "frames_per_step": frames, "fractions": NFRAC, "output_pixels_per_step_per_gpu": frames * NFRAC * W1080 * H1080,
+            "l2_flush": "none needed: 3.0 GB inputs and 4.9 GB outputs per step exceed L2",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -235,12 +244,10 @@ def run_reference(args):
     line = {"impl": "reference", "metric": "extrapolated Mpixel/s (fwd) at 1080p", "value": mpx, "unit": "Mpixel/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "1920x1080 FP32 sequence (60 source frames, 32 rectangles, 5% slivers), P_1..P_3 "
-                                   "with hole fill; each reference step = 1 source frame (bounded sample)",
-                       "parallelism": "replicas"},
+            "config": sequence_config(args.frames, world),
             "cpu_baseline": {"value": mpx, "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
-                             "sample": "1 source frame of the 1080p sequence per step, 3 fractions with fill, FP64 C "
-                                       "oracle single-threaded"},
+                             "sample": "each step: 1 source frame of the 1080p sequence (a bounded sample of the "
+                                       "step), 3 fractions with fill, FP64 C oracle single-threaded"},
             "e2e": {"value": mpx, "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -573,12 +580,7 @@ def run_exw(args):
                 "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": "1920x1080 FP32 sequence: 60 source frames, 32 moving rectangles (5% 1-3 px "
-                                       "slivers), |mv| <= 16 px; P_1..P_3 at t+k/4 with pull-push hole fill = 180 "
-                                       "output frames per step per GPU",
-                           "frames_per_step": F, "fractions": NFRAC, "output_pixels_per_step_per_gpu": out_px,
-                           "l2_flush": "none needed: 3.0 GB inputs and 4.9 GB outputs per step exceed L2",
-                           "parallelism": f"replicas x{world}"},
+                "config": sequence_config(F, world),
                 "gpu_launches": launches, "launches_per_step": launches / args.steps,
                 "clocks": clocks.summary(),
                 "roofline": roofline,
