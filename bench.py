@@ -36,6 +36,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 W1080, H1080, NFRAMES, NFRAC = 1920, 1080, 60, 3
+METRIC, UNIT = "extrapolated Mpixel/s (fwd) at 1080p", "Mpixel/s"  # both arms report this metric
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -209,7 +210,7 @@ def cpu_baseline(seconds: float, seq):
         oracle.extrapolate(cd, d, m, NFRAC)
     dt = time.perf_counter() - t0
     mpx = n * NFRAC * s.W * s.H / dt / 1e6
-    return {"value": mpx, "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
+    return {"value": mpx, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{n} of the 60 source frames of the 1920x1080 FP32 sequence, {NFRAC} fractions each with "
                       f"hole fill, FP64 C oracle single-threaded, {dt:.1f} s"}
 
@@ -241,14 +242,14 @@ def run_reference(args):
         oracle.extrapolate(*frames[i % 2], NFRAC)
     dt = (time.perf_counter() - t0) / max(1, args.steps)
     mpx = NFRAC * s.W * s.H / dt / 1e6
-    line = {"impl": "reference", "metric": "extrapolated Mpixel/s (fwd) at 1080p", "value": mpx, "unit": "Mpixel/s",
+    line = {"impl": "reference", "metric": METRIC, "value": mpx, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": sequence_config(args.frames, world),
-            "cpu_baseline": {"value": mpx, "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": mpx, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "each step: 1 source frame of the 1080p sequence (a bounded sample of the "
                                        "step), 3 fractions with fill, FP64 C oracle single-threaded"},
-            "e2e": {"value": mpx, "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": mpx, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -576,7 +577,7 @@ def run_exw(args):
 
     if rank == 0:
         cpu = None if args.no_cpu_baseline else cpu_baseline(args.cpu_seconds, seq)
-        line = {"metric": "extrapolated Mpixel/s (fwd) at 1080p", "value": value, "unit": "Mpixel/s",
+        line = {"metric": METRIC, "value": value, "unit": UNIT,
                 "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
@@ -585,7 +586,7 @@ def run_exw(args):
                 "clocks": clocks.summary(),
                 "roofline": roofline,
                 "cpu_baseline": cpu,
-                "e2e": {"value": whole_job_rate(world, out_px, e2e_s), "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
+                "e2e": {"value": whole_job_rate(world, out_px, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
                 "extras": extras}
         print(json.dumps(line), flush=True)
