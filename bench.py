@@ -14,7 +14,7 @@ Reported (one JSON line on rank 0):
               measured HBM copy bandwidth
   cpu_baseline the CPU oracle (FP64, single thread) on a bounded sample of the same workload
   clocks      nvidia-smi SM clocks and throttle reasons sampled during the timed region
---impl reference times the CPU oracle on the host cores instead (the reference arm of this build).
+--impl reference times the CPU oracle on the host cores instead (the benchmark's reference arm).
 Multi-GPU: one process per GPU (torchrun), each extrapolating its own sequence (replicas, weak scaling, no data
 collective); the step time is the max over ranks.
 """

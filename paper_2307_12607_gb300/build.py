@@ -1,7 +1,7 @@
 """In-tree build of libexw.so (the CUDA path) for sm_103a.
 
 Each translation unit under csrc/ is compiled by nvcc in parallel, then linked into
-``paper_2307_12607_gb300/_build/libexw.so`` (static CUDA runtime, so the library needs nothing but the driver).
+``paper_2307_12607_gb300/_build/libexw.so`` (static CUDA runtime, so the library needs nothing but the NVIDIA driver).
 Rebuilds only what changed.  ``python -m paper_2307_12607_gb300.build [--verbose-ptxas]``.
 """
 from __future__ import annotations
