@@ -29,14 +29,21 @@ MASK_EMPTY = 1
 MASK_CRACK = 2
 
 
+def compile_source(src: str, out: str) -> str:
+    """Compile an oracle C source into the shared library ``out`` (plain C, FP64, no FMA contraction so x86 and Arm
+    give the same bits)."""
+    tmp = out + f".{os.getpid()}.tmp"
+    subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                           "-o", tmp, src, "-lm"])
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle (plain C, FP64, no FMA contraction so x86 and Arm give the same bits)."""
+    """Compile ``exw_oracle.c`` into ``oracle/_build/`` unless the library is up to date."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB_PATH)
+        compile_source(_SRC, _LIB_PATH)
     return _LIB_PATH
 
 
@@ -44,7 +51,9 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
+            # EXW_ORACLE_LIB names another compiled copy to load instead: the mutation test runs the pins against
+            # deliberately broken copies of the oracle this way
+            lib = ctypes.CDLL(os.environ.get("EXW_ORACLE_LIB") or build())
             P = ctypes.c_void_p
             I = ctypes.c_int
             lib.oracle_target_offset.argtypes = [ctypes.c_float, I, I, ctypes.POINTER(ctypes.c_longlong)]
