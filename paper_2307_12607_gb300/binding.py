@@ -52,6 +52,9 @@ def _dev(t: torch.Tensor, name: str, dtype=None, shape=None) -> int:
         raise TypeError(f"{name} must be a torch tensor")
     if not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor (libexw runs on the GPU only)")
+    if t.device.index != torch.cuda.current_device():  # the kernels launch on the current device
+        raise ValueError(f"{name} is on {t.device}, not on the current device cuda:{torch.cuda.current_device()} "
+                         "(select it with torch.cuda.device)")
     if dtype is not None and t.dtype != dtype:
         raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
     if shape is not None and tuple(t.shape) != tuple(shape):
