@@ -653,3 +653,59 @@ def test_carried_holes_never_land_again():
     idx = (keys.view(np.uint64)[~holes] & np.uint64(0xFFFFFFFF)).astype(np.int64)
     assert np.array_equal(d1[~holes], depth.ravel()[idx])
     assert np.array_equal(m1[0][~holes], mv[0].ravel()[idx]) and np.array_equal(m1[1][~holes], mv[1].ravel()[idx])
+
+
+# ----------------------------------------------------------------------------------------------------------------
+# The composite P_1..P_3 (Sec. IV-B): closed forms for zero motion and whole-pixel translations, FP16 storage
+# ----------------------------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("fill", [True, False])
+def test_extrapolate_zero_motion_returns_the_source(fill):
+    color, depth, mv = scenes.random_frame(21, 13, 41)
+    mv[...] = 0.0
+    yy, xx = np.mgrid[0:13, 0:21]
+    depth = (30.0 + 0.01 * xx + 0.02 * yy).astype(np.float32)  # smooth: no pixel is a crack
+    res = oracle.extrapolate(color, depth, mv, 3, fill=fill)
+    ident = (depth.view(np.uint32).astype(np.uint64) << np.uint64(32)) | np.arange(21 * 13, dtype=np.uint64).reshape(13, 21)
+    for out, mask, keys in res:
+        assert not mask.any()
+        assert np.array_equal(keys.view(np.uint64), ident)
+        assert np.array_equal(out, color.astype(np.float64))
+
+
+def test_extrapolate_translation_uncovers_a_strip_that_the_fill_closes():
+    # every pixel moves by (8, 4) per frame on one depth: P_k is the source shifted by (2k, k) whole pixels; the
+    # first 2k columns and k rows are uncovered (EMPTY) and, with the fill, take values inside the frame's range
+    W, H = 24, 16
+    color, depth, mv = scenes.random_frame(W, H, 42)
+    depth[...] = 3.0
+    mv[0], mv[1] = 8.0, 4.0
+    c64 = color.astype(np.float64)
+    for fill in (False, True):
+        for k, (out, mask, _) in enumerate(oracle.extrapolate(color, depth, mv, 3, fill=fill), start=1):
+            yy, xx = np.mgrid[0:H, 0:W]
+            uncovered = (xx < 2 * k) | (yy < k)
+            assert np.array_equal(mask != 0, uncovered) and np.all(mask[uncovered] == oracle.MASK_EMPTY)
+            assert np.array_equal(out[:, k:, 2 * k:], c64[:, :H - k, :W - 2 * k])
+            if fill:
+                lo, hi = c64[:, :H - k, :W - 2 * k].min(), c64[:, :H - k, :W - 2 * k].max()
+                assert np.all(out[:, uncovered] >= lo) and np.all(out[:, uncovered] <= hi)
+            else:
+                assert np.all(out[:, uncovered] == 0.0)
+
+
+def test_extrapolate_fp16_storage_rounds_the_warped_colour_once():
+    # a half-pixel shift averages two taps; with FP16 storage the valid pixels are those averages rounded to FP16
+    # (reading 9), and a frame without holes is left as stored
+    W, H = 16, 9
+    color, depth, mv = scenes.random_frame(W, H, 43)
+    color = color.astype(np.float16).astype(np.float32)
+    depth[...] = 5.0
+    mv[0], mv[1] = 2.0, 0.0                           # k = 1: half a pixel to the right
+    out, mask, _ = oracle.extrapolate(color, depth, mv, 1, storage=np.float16, fill=True)[0]
+    c = color.astype(np.float64)
+    # T(p) = p + floor(1/2 + 1/2) = p + 1, rho = 1 - 1/2 = +1/2: the tap is p + 1 -> q's colour averages
+    # source columns q - 1 and q (the winner p = q - 1 and its right neighbour)
+    avg = 0.5 * (c[:, :, :-1] + c[:, :, 1:])
+    assert not mask[:, 1:].any() and np.all(mask[:, 0] == oracle.MASK_EMPTY)
+    assert np.array_equal(out[:, :, 1:], avg.astype(np.float16).astype(np.float64))
