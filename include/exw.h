@@ -122,8 +122,9 @@ EXW_API int exw_version(void);
 EXW_API size_t exw_workspace_bytes(exw_op op, int W, int H, exw_dtype cdt, int nframes, int nfrac);
 
 /* Stage (a0): motion bounds that limit how far any fraction of the motion can carry a source pixel (the halo of
- * the splat's search window).  Over the pixels that can land (positive finite depth, finite motion), with each
- * motion component clamped to [-65536, 65536] and -0 read as +0:
+ * the splat's search window; a step of this library that the paper does not have: it reads the per-pixel
+ * motion-vector buffer of Sec. III-D that the warp of Sec. III-B uses).  Over the pixels that can land (positive
+ * finite depth, finite motion), with each motion component clamped to [-65536, 65536] and -0 read as +0:
  *   tile_bounds  [ceil(H/8)][ceil(W/8)][4] float32 device, or NULL: [min mv_x, max mv_x, min mv_y, max mv_y] per
  *                8 x 8 tile; a tile with no such pixel gets [+inf, -inf, +inf, -inf];
  *   frame_bounds [4] float32 device: the same over the whole frame.
@@ -177,17 +178,17 @@ EXW_API exw_status exw_fill_holes_static(void *color, exw_dtype cdt, const uint8
 EXW_API exw_status exw_extrapolate(const exw_frame *frames, int nframes, int nfrac, unsigned flags, exw_frame_out *out,
                            void *ws, size_t ws_bytes, exw_stream_t stream);
 
-/* exw_extrapolate for frames held in HOST memory (Sec. IV-B, all stages), with the host <-> device copies
- * inside the call and overlapped with the work: the frames go in chunks of `chunk` frames (0: 8); chunk j's inputs
- * are copied in on one internal stream while chunk j - 1 is extrapolated on `stream` and chunk j - 2's outputs are
- * copied back on another.  frames_host [nframes] and out_host [nframes * nfrac] are HOST arrays of descriptors
- * holding host pointers (page-locked memory for the copies to overlap; any host memory works), frames_dev and
- * out_dev the same shapes in device memory, owned by the caller and written here (staging: every frame has its
- * own device buffers, nothing is allocated).  out_dev NULL: the engine writes the outputs straight into the host
- * buffers, which must then be page-locked and mapped (cudaHostGetDevicePointer; EXW_ERR_INVALID_ARG otherwise).
- * Workspace: exw_workspace_bytes(EXW_OP_EXTRAPOLATE, W, H, cdt, min(chunk, nframes), nfrac).  The call returns once the work is queued; when `stream` completes, the outputs are
- * in host memory.  The internal streams and events are created at the first call on a device; calls on one device
- * are serialised by the caller.  Errors as exw_extrapolate. */
+/* exw_extrapolate for frames held in HOST memory (Sec. IV-B, all stages), with the host <-> device copies inside the
+ * call and overlapped with the work: the frames go in chunks of `chunk` frames (0: 8); chunk j's inputs are copied in
+ * on one internal stream while chunk j - 1 is extrapolated on `stream` and chunk j - 2's outputs are copied back on
+ * another. frames_host [nframes] and out_host [nframes * nfrac] are HOST arrays of descriptors holding host pointers
+ * (page-locked memory for the copies to overlap; any host memory works), frames_dev and out_dev the same shapes in
+ * device memory, owned by the caller and written here (staging: every frame has its own device buffers, nothing is
+ * allocated). out_dev NULL: the engine writes the outputs straight into the host buffers, which must then be
+ * page-locked and mapped (cudaHostGetDevicePointer; EXW_ERR_INVALID_ARG otherwise).  Workspace:
+ * exw_workspace_bytes(EXW_OP_EXTRAPOLATE, W, H, cdt, min(chunk, nframes), nfrac).  The call returns once the work is
+ * queued; when `stream` completes, the outputs are in host memory.  The internal streams and events are created at the
+ * first call on a device; calls on one device are serialised by the caller.  Errors as exw_extrapolate. */
 EXW_API exw_status exw_extrapolate_host(const exw_frame *frames_host, const exw_frame *frames_dev, int nframes,
                                         int nfrac, unsigned flags, const exw_frame_out *out_host,
                                         const exw_frame_out *out_dev, int chunk, void *ws, size_t ws_bytes,
@@ -225,13 +226,13 @@ EXW_API exw_status exw_color_mse(const void *a, const void *b, exw_dtype cdt, in
 EXW_API exw_status exw_ssim(const void *a, const void *b, exw_dtype cdt, int W, int H, double *out, void *ws,
                             size_t ws_bytes, exw_stream_t stream);
 
-/* Adjoint of stage (b) for fraction k/denom with every integer decision held fixed (target, winner, taps, tap
- * participation, mask).  grad_out [3][H][W] float32 = dL/d out_color; accumulates (+=) into grad_color
- * [3][H][W] float32 (dL/d colour: w_t / sum w per participating tap) and grad_mv [2][H][W] float32 (dL/d motion
- * through rho, d rho / d mv = -k/denom).  keys: those of the forward pass, or NULL to recompute them into the
- * workspace (activation checkpointing).  Deterministic: each output element is summed by one thread in a fixed
- * order.  Workspace: exw_workspace_bytes(EXW_OP_WARP_BACKWARD, W, H, cdt, 1, 1) (0 bytes suffice when keys is
- * given). */
+/* Adjoint of stage (b) (the gather of Sec. II-B and Sec. III-B; the paper does not differentiate the warp, so this is
+ * a library facility for training against it) for fraction k/denom with every integer decision held fixed (target,
+ * winner, taps, tap participation, mask). grad_out [3][H][W] float32 = dL/d out_color; accumulates (+=) into grad_color
+ * [3][H][W] float32 (dL/d colour: w_t / sum w per participating tap) and grad_mv [2][H][W] float32 (dL/d motion through
+ * rho, d rho / d mv = -k/denom). keys: those of the forward pass, or NULL to recompute them into the workspace
+ * (activation checkpointing).  Deterministic: each output element is summed by one thread in a fixed order.  Workspace:
+ * exw_workspace_bytes(EXW_OP_WARP_BACKWARD, W, H, cdt, 1, 1) (0 bytes suffice when keys is given). */
 EXW_API exw_status exw_warp_backward(const float *grad_out, const void *color, exw_dtype cdt, const float *depth,
                              const float *mv, const uint64_t *keys, int W, int H, int k, int denom,
                              float *grad_color, float *grad_mv, void *ws, size_t ws_bytes, exw_stream_t stream);
@@ -265,12 +266,12 @@ EXW_API size_t exw_tuner_report(const exw_tuner *t, char *buf, size_t len);
 /* Workspace of exw_extrapolate_batched for n streams (host array of descriptors) with nfrac fractions. */
 EXW_API size_t exw_batched_workspace_bytes(const exw_stream_desc *d, int n, int nfrac);
 
-/* Stages (a0)+(a)+(b)+(c) for n independent streams of possibly different sizes (each with its own colour type)
- * in ONE persistent kernel launch: CTAs pull (stream, stage, tile) work items from a queue in the workspace; a
- * stage waits for the one before it in the same stream with a bounded spin (EXW_ERR_TIMEOUT via
- * exw_device_status if it runs out).  Capturable in a CUDA graph.  d [n] is a HOST array.  t (nullable) picks the
- * CTA count by timing candidates on the first call for a given set of sizes; NULL uses the SM count x occupancy.
- * Results are bit-identical to exw_extrapolate on each stream. */
+/* Stages (a0)+(a)+(b)+(c) -- P_1..P_nfrac at t + k/4 (Sec. IV-B), as exw_extrapolate -- for n independent streams of
+ * possibly different sizes (each with its own colour type) in ONE persistent kernel launch: CTAs pull (stream, stage,
+ * tile) work items from a queue in the workspace; a stage waits for the one before it in the same stream with a bounded
+ * spin (EXW_ERR_TIMEOUT via exw_device_status if it runs out).  Capturable in a CUDA graph. d [n] is a HOST array. t
+ * (nullable) picks the CTA count by timing candidates on the first call for a given set of sizes; NULL uses the SM
+ * count x occupancy.  Results are bit-identical to exw_extrapolate on each stream. */
 EXW_API exw_status exw_extrapolate_batched(const exw_stream_desc *d, int n, int nfrac, unsigned flags, void *ws,
                                    size_t ws_bytes, exw_tuner *t, exw_stream_t stream);
 
