@@ -79,3 +79,50 @@ def test_every_mutant_fails_a_pin(tmp_path):
     # exit status 1 = tests ran and failed (not a collection or usage error)
     missed = {name: r.returncode for name, r in results.items() if r.returncode != 1}
     assert not missed, f"mutants not caught (pytest exit status): {missed}"
+
+
+# Mistakes in the oracle's Python compositions (function: (text in its source, replacement)); each mutant function
+# is rebuilt from its edited source inside the pin run's process before the pins are collected.
+PY_MUTANTS = {
+    "extrapolate_without_storage_rounding": ("extrapolate", "stored = out.astype(storage).astype(np.float64)",
+                                             "stored = out"),
+    "extrapolate_fill_before_warp_rounding": ("extrapolate", "out = fill_holes(stored, mask)",
+                                              "out = fill_holes(out, mask)"),
+    "psnr_with_20_log10": ("psnr", "10.0 * np.log10(1.0 / mse)", "20.0 * np.log10(1.0 / mse)"),
+    "l2_gradient_without_factor_2": ("l2_loss_grad", "2.0 * diff", "diff"),
+    "halo_signed": ("halo", "max(abs(target_offset(float(v), k, denom)) for v in frame_bounds)",
+                    "max(target_offset(float(v), k, denom) for v in frame_bounds)"),
+    "recursive_warp_without_carry": ("warp_recursive", "d, m = carry_motion(keys, mask, d, m)", "pass"),
+}
+
+_PY_RUNNER = """
+import inspect, sys, textwrap
+sys.path.insert(0, {root!r})
+import numpy as np
+import oracle
+import pytest
+src = textwrap.dedent(inspect.getsource(getattr(oracle, {fn!r})))
+assert src.count({old!r}) == 1
+ns = dict(vars(oracle))
+exec(compile(src.replace({old!r}, {new!r}), "mutant", "exec"), ns)
+setattr(oracle, {fn!r}, ns[{fn!r}])
+sys.exit(pytest.main([{pins!r}, "-x", "-q", "-p", "no:cacheprovider"]))
+"""
+
+
+def _run_py_mutant(spec):
+    fn, old, new = spec
+    code = _PY_RUNNER.format(root=ROOT, fn=fn, old=old, new=new,
+                             pins=os.path.join(ROOT, "tests", "test_oracle_pins.py"))
+    return subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT, timeout=900)
+
+
+def test_every_python_composition_mutant_fails_a_pin():
+    specs = dict(PY_MUTANTS)
+    specs["unmutated"] = ("psnr", "10.0 * np.log10(1.0 / mse)", "10.0 * np.log10(1.0 / mse)")
+    with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        results = dict(zip(specs, ex.map(_run_py_mutant, specs.values())))
+    base = results.pop("unmutated")
+    assert base.returncode == 0, base.stdout[-2000:] + base.stderr[-2000:]
+    missed = {name: r.returncode for name, r in results.items() if r.returncode != 1}
+    assert not missed, f"mutants not caught (pytest exit status): {missed}"

@@ -525,6 +525,13 @@ def test_motion_bounds_brute_force(W, H, block):
         assert oracle.halo(frame, k) == brute
 
 
+def test_halo_is_the_largest_offset_magnitude():
+    # all motion leftwards and upwards: the farthest reach is the most negative bound, -40 px per frame -> 10 k px
+    frame = np.array([-40.0, -3.0, -20.0, -1.0], np.float32)
+    assert [oracle.halo(frame, k) for k in (1, 2, 3)] == [10, 20, 30]
+    assert oracle.halo(np.array([np.inf, -np.inf, np.inf, -np.inf], np.float32), 3) == 0  # nothing can land
+
+
 # ----------------------------------------------------------------------------------------------------------------
 # Motion-variance features (Sec. IV-C Eq. 1) and the colour MSE / PSNR of the reward (Eq. 3)
 # ----------------------------------------------------------------------------------------------------------------
@@ -640,6 +647,9 @@ def test_two_quarter_steps_of_a_translation_equal_one_half_step():
     half, hmask = oracle.warp(color, depth, mv, keys2, 2, 4)
     inner = (slice(2, H - 2), slice(4, W - 4))
     assert np.array_equal(two[1][1][inner], hmask[inner]) and not hmask[inner].any()
+    # the holes of P_1 carry no motion and never land again, so P_2 is uncovered exactly where the half step is
+    yy, xx = np.mgrid[0:H, 0:W]
+    assert np.array_equal(two[1][1] != 0, (xx < 4) | (yy >= H - 2)) and np.array_equal(two[1][1], hmask)
     assert np.array_equal(two[1][0][(slice(None),) + inner], half[(slice(None),) + inner])
 
 
