@@ -161,8 +161,9 @@ EXW_API exw_status exw_fill_holes(void *color, exw_dtype cdt, const uint8_t *mas
  * call, code that only receives raw device pointers.  The paper has no counterpart; this is a library facility.
  * Scratch: one built-in device array of 768 KiB, held by every GPU that loads the library until the process exits;
  * frames up to 16384 fill tiles of 32 x 32 pixels (for example 4096 x 4096 or 8192 x 2048) fit, larger ones
- * return EXW_ERR_WORKSPACE.  The call allocates nothing: the first call on each device looks up the array's device
- * address (cudaGetSymbolAddress) and caches it, so make that first call before any stream capture.  All calls
+ * return EXW_ERR_WORKSPACE.  The call allocates nothing: each call looks up the array's device address on the current
+ * device (cudaGetSymbolAddress, so it stays valid after cudaDeviceReset); the first call on a device also loads the
+ * library's device code there, so make that first call before any stream capture.  All calls
  * share the one array and each clears the counters it needs at its start: calls that may overlap on the GPU
  * (different streams, or concurrent host threads) race on it and must be serialised by the caller.
  * color [3][H][W] (cdt) device, read and written; mask [H][W] device, read. */

@@ -53,22 +53,6 @@ void timing_end(const char *name, cudaStream_t s) {
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
-// ------------------------------------------------------------------------------------------------------------
-// Argument checks
-// ------------------------------------------------------------------------------------------------------------
-static bool aligned(const void *p, uintptr_t a) { return p != nullptr && ((uintptr_t)p & (a - 1)) == 0; }
-static bool aligned16(const void *p) { return aligned(p, 16); }
-static uintptr_t csize(exw_dtype d) { return d == EXW_F16 ? 2 : 4; }
-static bool size_ok(int W, int H) { return W >= 1 && H >= 1 && W <= 16384 && H <= 16384; }
-static bool dtype_ok(exw_dtype d) { return d == EXW_F32 || d == EXW_F16; }
-static int log2_pow2(int d) {
-    if (d < 1 || d > 64 || (d & (d - 1)) != 0) return -1;
-    int l = 0;
-    while ((1 << l) != d) ++l;
-    return l;
-}
-static exw_status from_cuda(cudaError_t e) { return e == cudaSuccess ? EXW_OK : EXW_ERR_CUDA; }
-static exw_status entry_check() { return cudaGetLastError() == cudaSuccess ? EXW_OK : EXW_ERR_CUDA; }
 
 static TileParams tile_params(const WsLayout &l, void *ws, int W, int H, int nfrac, int L, int k0, int frame) {
     TileParams p{};

@@ -342,7 +342,7 @@ static void specs_from(const exw_stream_desc *d, int n, std::vector<EngineSpec> 
 size_t exw_batched_workspace_bytes(const exw_stream_desc *d, int n, int nfrac) {
     if (d == nullptr || n < 1 || n > kMaxStreams || nfrac < 1 || nfrac > EXW_MAX_FRAC) return 0;
     for (int i = 0; i < n; ++i)
-        if (d[i].src.W < 1 || d[i].src.H < 1 || d[i].src.W > 16384 || d[i].src.H > 16384) return 0;
+        if (!size_ok(d[i].src.W, d[i].src.H)) return 0;
     std::vector<EngineSpec> specs;
     specs_from(d, n, specs);
     return engine_workspace_bytes(specs.data(), n, nfrac, false);
@@ -356,7 +356,7 @@ exw_status exw_extrapolate_batched(const exw_stream_desc *d, int n, int nfrac, u
     for (int i = 0; i < n; ++i) {
         const exw_frame &f = d[i].src;
         const uintptr_t cs = f.cdt == EXW_F16 ? 2 : 4;
-        if (f.W < 1 || f.H < 1 || f.W > 16384 || f.H > 16384 || (f.cdt != EXW_F32 && f.cdt != EXW_F16) ||
+        if (!size_ok(f.W, f.H) || !dtype_ok(f.cdt) ||
             f.color == nullptr || f.depth == nullptr || f.mv == nullptr || ((uintptr_t)f.color & (cs - 1)) ||
             ((uintptr_t)f.depth & 3u) || ((uintptr_t)f.mv & 3u))
             return EXW_ERR_INVALID_ARG;

@@ -10,6 +10,26 @@
 
 namespace exw {
 
+// ------------------------------------------------------------------------------------------------------------
+// Argument checks shared by every entry point (the rules of include/exw.h)
+// ------------------------------------------------------------------------------------------------------------
+constexpr int kMaxSide = 16384;     // largest W or H
+constexpr int kFillTileSide = 32;  // side of the fill tiles (pyramid levels 1..5 of one tile)
+inline bool aligned(const void *p, uintptr_t a) { return p != nullptr && ((uintptr_t)p & (a - 1)) == 0; }
+inline bool aligned16(const void *p) { return aligned(p, 16); }
+inline uintptr_t csize(exw_dtype d) { return d == EXW_F16 ? 2 : 4; }
+inline bool size_ok(int W, int H) { return W >= 1 && H >= 1 && W <= kMaxSide && H <= kMaxSide; }
+inline bool dtype_ok(exw_dtype d) { return d == EXW_F32 || d == EXW_F16; }
+inline int log2_pow2(int d) {  // log2 of a power of two in [1, 64]; -1 otherwise
+    if (d < 1 || d > 64 || (d & (d - 1)) != 0) return -1;
+    int l = 0;
+    while ((1 << l) != d) ++l;
+    return l;
+}
+inline exw_status from_cuda(cudaError_t e) { return e == cudaSuccess ? EXW_OK : EXW_ERR_CUDA; }
+// A sticky error left by earlier work is reported before anything is enqueued.
+inline exw_status entry_check() { return cudaGetLastError() == cudaSuccess ? EXW_OK : EXW_ERR_CUDA; }
+
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 inline int ceil_div(int a, int b) { return (a + b - 1) / b; }

@@ -6,8 +6,6 @@
 // fill's scratch (pyramid nodes, the list of tiles without a valid pixel, their fill values, the coarse levels and
 // the per-call counters) lives in one file-scope __device__ array of fixed size instead of a caller workspace.
 // The array occupies kStaticScratchBytes on every GPU that loads this library, until the process exits.
-#include <mutex>
-
 #include "exw_internal.h"
 
 namespace exw {
@@ -18,24 +16,15 @@ constexpr size_t kStaticScratchBytes = 768u * 1024u;
 
 static __device__ __align__(256) unsigned char g_fill_scratch[kStaticScratchBytes];
 
-static std::mutex g_static_mu;
-static void *g_static_ptr[64] = {};  // device address of g_fill_scratch, per device ordinal
-
 // The device address of the scratch array on the current device.  In host code g_fill_scratch is only a
-// host-side stand-in for the symbol, so the address comes from cudaGetSymbolAddress, once per device.
+// host-side stand-in for the symbol, so the address comes from cudaGetSymbolAddress.  It is looked up on every
+// call (cheap once the module is loaded), so it stays right after cudaDeviceReset or in a new context, where the
+// array may sit elsewhere.  The first call on a device loads the module: make it before any stream capture.
 static cudaError_t static_scratch(void **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_fill_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> g(g_static_mu);
-    if (g_static_ptr[dev] == nullptr) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_fill_scratch);
-        if (e != cudaSuccess) return e;
-        g_static_ptr[dev] = p;
-    }
-    *out = g_static_ptr[dev];
+    *out = p;
     return cudaSuccess;
 }
 
@@ -45,14 +34,14 @@ using namespace exw;
 
 extern "C" exw_status exw_fill_holes_static(void *color, exw_dtype cdt, const uint8_t *mask, int W, int H,
                                             exw_stream_t stream) {
-    if (W < 1 || H < 1 || W > 16384 || H > 16384 || (cdt != EXW_F32 && cdt != EXW_F16) || color == nullptr ||
-        mask == nullptr || ((uintptr_t)color & (cdt == EXW_F16 ? 1u : 3u)) != 0)
+    // the argument rules of exw_fill_holes (shared helpers), then the size limit of the built-in array
+    if (!size_ok(W, H) || !dtype_ok(cdt) || !aligned(color, csize(cdt)) || !aligned(mask, 1))
         return EXW_ERR_INVALID_ARG;
     // Fill-only layout: status word, one frame header, then per-tile nodes, invalid-tile list, fill values and the
     // coarse pyramid levels (the motion-bounds tiles of the general workspace are not needed here).
     WsLayout l{};
-    l.n5x = ceil_div(W, 32);
-    l.n5y = ceil_div(H, 32);
+    l.n5x = ceil_div(W, kFillTileSide);
+    l.n5y = ceil_div(H, kFillTileSide);
     l.ncoarse = coarse_nodes(l.n5x, l.n5y);
     const size_t n5 = (size_t)l.n5x * l.n5y;
     if (n5 > (size_t)kStaticMaxTiles) return EXW_ERR_WORKSPACE;
@@ -64,7 +53,7 @@ extern "C" exw_status exw_fill_holes_static(void *color, exw_dtype cdt, const ui
     l.coarse = l.fillval + align_up(n5 * 16);
     l.total = l.coarse + align_up((size_t)(l.ncoarse > 0 ? l.ncoarse : 1) * 16);
     if (l.total > kStaticScratchBytes) return EXW_ERR_WORKSPACE;
-    if (cudaGetLastError() != cudaSuccess) return EXW_ERR_CUDA;
+    if (entry_check() != EXW_OK) return EXW_ERR_CUDA;
     void *ws = nullptr;
     if (static_scratch(&ws) != cudaSuccess) return EXW_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
@@ -88,5 +77,5 @@ extern "C" exw_status exw_fill_holes_static(void *color, exw_dtype cdt, const ui
     cudaError_t e = launch_zero(ws, l.headers + sizeof(FrameHeader), s);
     if (e == cudaSuccess) e = launch_fill_tiles(p, cdt, s);
     if (e == cudaSuccess) e = launch_fixup(p, cdt, s);
-    return e == cudaSuccess ? EXW_OK : EXW_ERR_CUDA;
+    return from_cuda(e);
 }

@@ -1,6 +1,7 @@
-"""GPU tests of the batched persistent path: results bit-identical to exw_extrapolate per stream (mixed sizes, colour
-types and widths that do or do not allow TMA staging), the autotuner, replay from a CUDA graph, and a bounded wait
-that runs out (injected on the host with EXW_FAULT=timeout) reporting EXW_ERR_TIMEOUT without faulting the GPU."""
+"""GPU tests of the batched persistent path: every stream against the FP64 CPU oracle (masks bit-exact, colour within
+2e-6 for float32 storage and 1e-3 for float16 storage), and bit-identical to exw_extrapolate per stream (mixed sizes,
+colour types and widths that do or do not allow TMA staging); the autotuner, replay from a CUDA graph, and a bounded
+wait that runs out (injected on the host with EXW_FAULT=timeout) reporting EXW_ERR_TIMEOUT without faulting the GPU."""
 import os
 
 import numpy as np
@@ -8,6 +9,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle  # noqa: E402
 from paper_2307_12607_gb300 import scenes  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -40,6 +42,35 @@ def same(a, b_):
     return torch.equal(a.view(iv), b_.view(iv))
 
 
+TOL = {torch.float32: 2e-6, torch.float16: 1e-3}
+NPDT = {torch.float32: np.float32, torch.float16: np.float16}
+
+
+def assert_matches_oracle(stream, out, nfrac, fill, what=""):
+    """One stream's batched outputs against the oracle run on the same inputs: the warped colour rounded once to
+    the storage type before the fill, masks bit-exact, colour within the storage type's tolerance."""
+    c, d, m = stream
+    o, k = out
+    cs = c.cpu().numpy()
+    ref = oracle.extrapolate(cs.astype(np.float64), d.cpu().numpy(), m.cpu().numpy(), nfrac, storage=NPDT[c.dtype],
+                             fill=fill)
+    for j, (wo, wm, _) in enumerate(ref):
+        np.testing.assert_array_equal(k[j].cpu().numpy(), wm, err_msg=f"{what} mask of P_{j + 1}")
+        np.testing.assert_allclose(o[j].float().cpu().numpy().astype(np.float64), wo, rtol=0, atol=TOL[c.dtype],
+                                   err_msg=f"{what} colour of P_{j + 1}")
+
+
+@pytest.mark.parametrize("fill", [True, False])
+@pytest.mark.parametrize("tma", [True, False])
+def test_batched_matches_oracle(b, fill, tma):
+    # every stream of the mixed set (sizes, FP16 / FP32 colour, widths with and without TMA staging) against the
+    # oracle itself, not only against the single-stream launch
+    streams = make_streams(seed=5)
+    outs = b.exw_extrapolate_batched(streams, nfrac=3, fill=fill, tma=tma)
+    for i, (s, o) in enumerate(zip(streams, outs)):
+        assert_matches_oracle(s, o, 3, fill, f"stream {i} {tuple(s[1].shape)} {s[0].dtype}")
+
+
 @pytest.mark.parametrize("fill", [True, False])
 @pytest.mark.parametrize("tma", [True, False])
 def test_batched_matches_single_stream(b, fill, tma):
@@ -60,6 +91,8 @@ def test_batched_with_tuner_and_fewer_fractions(b):
             for (c, d, m), (o, k) in zip(streams, outs):
                 o1, k1 = b.exw_extrapolate(c, d, m, nfrac=nfrac)
                 assert torch.equal(k, k1) and same(o, o1)
+            for i in (0, 3, 4):
+                assert_matches_oracle(streams[i], outs[i], nfrac, True, f"tuned, nfrac {nfrac}, stream {i}")
         rep = b.exw_tuner_report(t)
         assert rep.count("best") == 2 and "lag" in rep
     finally:
@@ -92,9 +125,10 @@ def test_batched_graph_capture_and_replay(b):
             g.replay()
             torch.cuda.synchronize()
             assert b.exw_device_status(ws) == 0
-            for (c, d, m), (o, k) in zip(streams, outs):
+            for i, ((c, d, m), (o, k)) in enumerate(zip(streams, outs)):
                 o1, k1 = b.exw_extrapolate(c, d, m, nfrac=nfrac)
                 assert torch.equal(k, k1) and same(o, o1)
+                assert_matches_oracle((c, d, m), (o, k), nfrac, True, f"replay {rep} stream {i}")
     finally:
         b.exw_tuner_destroy(t)
 
@@ -125,7 +159,8 @@ def test_batched_full_config_sampled(b):
         c, d, m = scenes.render(s, 0.0, np.float16)
         streams.append((torch.from_numpy(c).cuda(), torch.from_numpy(d).cuda(), torch.from_numpy(m).cuda()))
     outs = b.exw_extrapolate_batched(streams, 3)
-    for i in (0, 13, 30, 47):
+    for i in (0, 13, 30, 47):   # one stream of each resolution: 720p, 1080p, 1440p, 4K
         c, d, m = streams[i]
         o1, k1 = b.exw_extrapolate(c, d, m, nfrac=3)
         assert torch.equal(outs[i][1], k1) and same(outs[i][0], o1)
+        assert_matches_oracle(streams[i], outs[i], 3, True, f"48-stream launch, stream {i} {tuple(d.shape)}")

@@ -41,14 +41,16 @@ def call_static(lib, color, mask):
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
 def test_static_fill_matches_workspace_fill_twice(lib, dtype):
     from paper_2307_12607_gb300 import binding
-    tol = 2e-6 if dtype == torch.float32 else 1e-3
+    iv = torch.int32 if dtype == torch.float32 else torch.int16
     for W, H, seed in ((1920, 1080, 1), (333, 517, 2)):   # two calls in a row, different frames
         color, mask = holes(W, H, seed, dtype)
         want = binding.exw_fill_holes(color.clone(), mask)
         got = color.clone()
         assert call_static(lib, got, mask) == 0
         torch.cuda.synchronize()
-        assert torch.max(torch.abs(got.float() - want.float())).item() <= tol
+        # the same kernels on the same scratch layout: the results are identical bit for bit (a stale node or fill
+        # value left in the shared array by the previous call would show here)
+        assert torch.equal(got.view(iv), want.view(iv))
         valid = (mask == 0).unsqueeze(0).expand_as(got)
         assert torch.equal(got[valid], color[valid])
 
