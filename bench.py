@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["exw", "reference"], default="exw")
     ap.add_argument("--frames", type=int, default=NFRAMES)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=0, help="end-to-end steps (0: as many as --steps)")
     ap.add_argument("--e2e-chunk", type=int, default=2, help="frames per overlapped copy/compute chunk (e2e)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -194,25 +194,48 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _oracle_frames(inputs, threads):
+    """Run the oracle's extrapolation (3 fractions with fill) over ``inputs`` on ``threads`` host threads; returns the
+    wall time.  The oracle is C behind ctypes, which releases the GIL, so threads run it on separate cores."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    t0 = time.perf_counter()
+    if threads <= 1:
+        for cd, d, m in inputs:
+            oracle.extrapolate(cd, d, m, NFRAC)
+    else:
+        with ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(lambda a: oracle.extrapolate(a[0], a[1], a[2], NFRAC), inputs))
+    return time.perf_counter() - t0
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def cpu_baseline(seconds: float, seq):
-    """The CPU oracle as it stands (FP64 C, single thread) on whole frames of the benchmark's own 1080p sequence:
-    one frame is timed first, then as many frames as fit in ~``seconds`` are timed together."""
+    """The CPU oracle as it stands (FP64 C) on whole frames of the benchmark's own 1080p sequence, timed on one
+    thread and on every host core (one frame per thread at a time): one frame is timed first, then as many frames
+    as fit in about ``seconds`` of single-thread work, and every frame of the sequence (at most) on all cores."""
     import oracle
     oracle.build()
     s, col, dep, mv = seq
-    t0 = time.perf_counter()
-    oracle.extrapolate(col[0].astype(np.float64), dep[0], mv[0], NFRAC)
-    one = time.perf_counter() - t0
-    n = int(max(1, min(len(col), seconds // max(one, 1e-3))))
-    inputs = [(col[f].astype(np.float64), dep[f], mv[f]) for f in range(n)]
-    t0 = time.perf_counter()
-    for cd, d, m in inputs:
-        oracle.extrapolate(cd, d, m, NFRAC)
-    dt = time.perf_counter() - t0
-    mpx = n * NFRAC * s.W * s.H / dt / 1e6
-    return {"value": mpx, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} of the 60 source frames of the 1920x1080 FP32 sequence, {NFRAC} fractions each with "
-                      f"hole fill, FP64 C oracle single-threaded, {dt:.1f} s"}
+    inputs = lambda n: [(col[f].astype(np.float64), dep[f], mv[f]) for f in range(n)]
+    one = _oracle_frames(inputs(1), 1)
+    n1 = int(max(1, min(len(col), seconds // max(one, 1e-3))))
+    dt1 = _oracle_frames(inputs(n1), 1)
+    cores = host_cores()
+    nm = int(max(1, min(len(col), cores * max(1, seconds // max(one, 1e-3)) // 2)))
+    dtm = _oracle_frames(inputs(nm), cores)
+    px = NFRAC * s.W * s.H
+    return {"value": nm * px / dtm / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{nm} of the 60 source frames of the 1920x1080 FP32 sequence on {cores} host threads (one "
+                      f"frame per thread), {NFRAC} fractions each with hole fill, FP64 C oracle, {dtm:.1f} s",
+            "single_thread": {"value": n1 * px / dt1 / 1e6, "unit": UNIT, "cores": 1,
+                              "sample": f"{n1} frames on one thread, {dt1:.1f} s"}}
 
 
 def sequence_config(frames: int, world: int) -> dict:
@@ -232,23 +255,25 @@ def run_reference(args):
     from paper_2307_12607_gb300 import scenes
     oracle.build()
     s = scenes.sequence_1080p_scene()
-    frames = [scenes.render(s, float(f)) for f in range(2)]
+    cores = host_cores()
+    nf = min(cores, 16)
+    frames = [scenes.render(s, float(f)) for f in range(nf)]
     frames = [(c.astype(np.float64), d, m) for c, d, m in frames]
-    # each step extrapolates one source frame (a bounded sample of the 60-frame step)
+    # each step extrapolates nf source frames, one per host thread (a bounded sample of the 60-frame step)
     for i in range(args.warmup):
-        oracle.extrapolate(*frames[i % 2], NFRAC)
-    t0 = time.perf_counter()
+        _oracle_frames(frames[:1], 1)
+    dt = 0.0
     for i in range(args.steps):
-        oracle.extrapolate(*frames[i % 2], NFRAC)
-    dt = (time.perf_counter() - t0) / max(1, args.steps)
-    mpx = NFRAC * s.W * s.H / dt / 1e6
+        dt += _oracle_frames(frames, nf)
+    dt /= max(1, args.steps)
+    mpx = nf * NFRAC * s.W * s.H / dt / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": mpx, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": sequence_config(args.frames, world),
-            "cpu_baseline": {"value": mpx, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "each step: 1 source frame of the 1080p sequence (a bounded sample of the "
-                                       "step), 3 fractions with fill, FP64 C oracle single-threaded"},
+            "cpu_baseline": {"value": mpx, "unit": UNIT, "cores": nf, "kind": "oracle",
+                             "sample": f"each step: {nf} source frames of the 1080p sequence (a bounded sample of "
+                                       f"the step) on {nf} host threads, 3 fractions with fill, FP64 C oracle"},
             "e2e": {"value": mpx, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -466,6 +491,51 @@ def _extras_diff(b, devc, ex):
                                        "recomputed in the backward (activation checkpointing)"}
 
 
+def copy_ceiling(host_in, dev_in, dev_out, host_out, reps=3):
+    """The host link's own limit for one end-to-end step: the step's inputs copied host -> device and its outputs
+    device -> host as single large cudaMemcpyAsync calls from page-locked memory, each direction alone and both at
+    once on two streams (best of ``reps``, CUDA events).  No step can move its bytes faster than the
+    both-directions time."""
+    import torch
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def h2d():
+        for d, h in zip(dev_in, host_in):
+            d.copy_(h, non_blocking=True)
+
+    def d2h():
+        for h, d in zip(host_out, dev_out):
+            h.copy_(d, non_blocking=True)
+
+    def timed(fns_streams):
+        best = float("inf")
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            starts, ends = [], []
+            for fn, st in fns_streams:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(st):
+                    e0.record(st)
+                    fn()
+                    e1.record(st)
+                starts.append(e0)
+                ends.append(e1)
+            torch.cuda.synchronize()
+            t = max(starts[0].elapsed_time(e) for e in ends)
+            for e0 in starts[1:]:
+                t = max(t, max(e0.elapsed_time(e) for e in ends))
+            best = min(best, t)
+        return best
+
+    ms_in = timed([(h2d, s_in)])
+    ms_out = timed([(d2h, s_out)])
+    ms_both = timed([(h2d, s_in), (d2h, s_out)])
+    bin_ = sum(t.numel() * t.element_size() for t in host_in)
+    bout = sum(t.numel() * t.element_size() for t in host_out)
+    return {"h2d_gbs": bin_ / ms_in / 1e6, "d2h_gbs": bout / ms_out / 1e6, "h2d_ms": ms_in, "d2h_ms": ms_out,
+            "both_directions_ms": ms_both}
+
+
 def run_exw(args):
     import torch
     import torch.distributed as dist
@@ -564,14 +634,16 @@ def run_exw(args):
     e2e_step()
     torch.cuda.synchronize()
     barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
+    e2e_steps = args.e2e_steps if args.e2e_steps > 0 else args.steps
+    t0 = time.perf_counter()   # wall clock: the host's own work per call counts too
+    for _ in range(e2e_steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, devc)
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, devc)
     barrier()
     h2d = (hc.numel() * 4 + hd.numel() * 4 + hm.numel() * 4)
     d2h = ho.numel() * 4 + hmask.numel()
+    ceiling = copy_ceiling((hc, hd, hm), (c, d, m), (out, mask), (ho, hmask))
 
     extras = {} if (args.no_extras or world > 1) else run_extras(b, devc)
 
@@ -587,7 +659,9 @@ def run_exw(args):
                 "roofline": roofline,
                 "cpu_baseline": cpu,
                 "e2e": {"value": whole_job_rate(world, out_px, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                        "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
+                        "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3, "steps": e2e_steps,
+                        "copy_ceiling": ceiling,
+                        "frac_of_copy_ceiling": ceiling["both_directions_ms"] / (e2e_s * 1e3)},
                 "extras": extras}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -80,7 +80,8 @@ typedef enum exw_op {
     EXW_OP_FILL_HOLES = 1,
     EXW_OP_EXTRAPOLATE = 2,
     EXW_OP_WARP_BACKWARD = 3,
-    EXW_OP_STATS = 4
+    EXW_OP_STATS = 4,
+    EXW_OP_WARP_RECURSIVE = 5
 } exw_op;
 
 #define EXW_MASK_EMPTY 1u
@@ -205,6 +206,17 @@ EXW_API exw_status exw_extrapolate_host(const exw_frame *frames_host, const exw_
 EXW_API exw_status exw_carry_motion(const uint64_t *keys, const uint8_t *mask, const float *depth, const float *mv,
                                     int W, int H, float *depth_out, float *mv_out, exw_stream_t stream);
 
+/* The recursive warps of decision paths S5 and S6 (Table V): P_1 = W(F_t), P_{i+1} = W(P_i), each a quarter step
+ * (k = 1 of 4) of the motion the warped frame carries (exw_carry_motion's reading).  Per step: exw_splat_motion,
+ * exw_warp and (unless flags has EXW_FLAG_NO_FILL) exw_fill_holes, then exw_carry_motion for the next step; all
+ * on the device, chained in this call.  color [3][H][W] (cdt), depth [H][W], mv [2][H][W]: the source frame
+ * (device, read).  out [steps] is a HOST array of descriptors of device buffers: out[i] receives P_{i+1}'s colour
+ * (cdt) and hole mask.  steps in [1, 64].  Workspace: exw_workspace_bytes(EXW_OP_WARP_RECURSIVE, W, H, cdt, 1, 1)
+ * (the keys, the carried depth and motion, the fill's scratch). */
+EXW_API exw_status exw_warp_recursive(const void *color, exw_dtype cdt, const float *depth, const float *mv, int W,
+                                      int H, int steps, unsigned flags, exw_frame_out *out, void *ws, size_t ws_bytes,
+                                      exw_stream_t stream);
+
 /* Motion-variance features Var_x(F_mv), Var_y(F_mv) of the decision stage's environment vector E_t (Sec. IV-C,
  * Eq. 1; the feature is motivated in Sec. III-D): over every pixel of mv [2][H][W] whose two components are
  * finite, the population variance of the x component and of the y component.  out [3] is a DEVICE float64 array:
@@ -218,6 +230,12 @@ EXW_API exw_status exw_mv_variance(const float *mv, int W, int H, double *out, v
  * 255, i.e. PSNR = -10 log10(out[0]).  out [1] is a DEVICE float64.  Workspace: as exw_mv_variance. */
 EXW_API exw_status exw_color_mse(const void *a, const void *b, exw_dtype cdt, int W, int H, double *out, void *ws,
                                  size_t ws_bytes, exw_stream_t stream);
+
+/* PSNR of the reward (Sec. IV-C, Eq. 3): out [2] DEVICE float64 receives the MSE of exw_color_mse and
+ * 10 log10(255^2 / MSE) = -10 log10(MSE) in dB for colours in [0, 1] scaled by 255 (+inf when the images are
+ * equal), both computed on the device.  Workspace: as exw_mv_variance. */
+EXW_API exw_status exw_psnr(const void *a, const void *b, exw_dtype cdt, int W, int H, double *out, void *ws,
+                            size_t ws_bytes, exw_stream_t stream);
 
 /* Structural similarity of two colour images a, b [3][H][W] of type cdt in [0, 1] (the SSIM of the reward, Sec.
  * IV-C, Eq. 3, read as the standard index: 11 x 11 Gaussian window, sigma 1.5, C1 = 1e-4, C2 = 9e-4, over every

@@ -35,6 +35,8 @@ PROTOTYPES = {
     "exw_mv_variance": (I, [P, I, I, P, P, SZ, P]),
     "exw_carry_motion": (I, [P, P, P, P, I, I, P, P, P]),
     "exw_color_mse": (I, [P, P, I, I, I, P, P, SZ, P]),
+    "exw_psnr": (I, [P, P, I, I, I, P, P, SZ, P]),
+    "exw_warp_recursive": (I, [P, I, P, P, I, I, I, U, P, P, SZ, P]),
     "exw_ssim": (I, [P, P, I, I, I, P, P, SZ, P]),
     "exw_warp_backward": (I, [P, P, I, P, P, P, I, I, I, I, P, P, P, SZ, P]),
     "exw_l2_loss_grad": (I, [P, P, I, P, I, I, P, P, P]),

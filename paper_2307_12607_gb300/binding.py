@@ -253,6 +253,7 @@ def exw_extrapolate_host(color, depth, mv, nfrac: int = 3, fill: bool = True, ou
 
 
 OP_STATS = 4
+OP_WARP_RECURSIVE = 5
 
 
 def exw_carry_motion(keys, mask, depth, mv, depth_out=None, mv_out=None, stream=None):
@@ -271,22 +272,30 @@ def exw_carry_motion(keys, mask, depth, mv, depth_out=None, mv_out=None, stream=
     return depth_out, mv_out
 
 
-def exw_warp_recursive(color, depth, mv, steps: int = 3, fill: bool = True, stream=None):
+def exw_warp_recursive(color, depth, mv, steps: int = 3, fill: bool = True, out=None, mask=None, ws=None,
+                       stream=None):
     """Decision path S6 (Table V): P_1 = W(F), P_{i+1} = W(P_i), each a quarter step (k = 1 of 4) of the motion
-    every pixel carries (exw_carry_motion).  Returns [(colour [3][H][W], mask [H][W])] for the ``steps`` frames."""
+    every pixel carries, chained on the device by the library (exw_warp_recursive).  Returns [(colour [3][H][W],
+    mask [H][W])] for the ``steps`` frames (views of ``out`` [steps][3][H][W] and ``mask`` [steps][H][W])."""
     W, H = _hw(depth)
-    ws = workspace(exw_workspace_bytes(OP_FILL_HOLES, W, H, _cdt(color)), color.device) if fill else None
-    c, d, m = color, depth, mv
-    outs = []
-    for _ in range(int(steps)):
-        keys = exw_splat_motion(d, m, 1, 4, stream=stream)
-        out, mask = exw_warp(c, d, m, keys, 1, 4, stream=stream)
-        if fill:
-            exw_fill_holes(out, mask, ws, stream=stream)
-        outs.append((out, mask))
-        d, m = exw_carry_motion(keys, mask, d, m, stream=stream)
-        c = out
-    return outs
+    dev = color.device
+    steps = int(steps)
+    if out is None:
+        out = torch.empty((steps, 3, H, W), dtype=color.dtype, device=dev)
+    if mask is None:
+        mask = torch.empty((steps, H, W), dtype=torch.uint8, device=dev)
+    _dev(out, "out", color.dtype, (steps, 3, H, W))
+    _dev(mask, "mask", torch.uint8, (steps, H, W))
+    if ws is None:
+        ws = workspace(exw_workspace_bytes(OP_WARP_RECURSIVE, W, H, _cdt(color)), dev)
+    outs = (_lib.ExwFrameOut * steps)()
+    for i in range(steps):
+        outs[i] = _lib.ExwFrameOut(out[i].data_ptr(), mask[i].data_ptr())
+    _check(lib().exw_warp_recursive(_dev(color, "color", None, (3, H, W)), _cdt(color),
+                                    _dev(depth, "depth", torch.float32), _dev(mv, "mv", torch.float32, (2, H, W)), W,
+                                    H, steps, 0 if fill else FLAG_NO_FILL, ctypes.cast(outs, ctypes.c_void_p),
+                                    ws.data_ptr(), ws.numel(), _stream(stream, dev)))
+    return [(out[i], mask[i]) for i in range(steps)]
 
 
 def exw_mv_variance(mv, ws=None, stream=None):
@@ -335,10 +344,18 @@ def exw_ssim(a, b, ws=None, stream=None) -> float:
 
 
 def exw_psnr(a, b, ws=None, stream=None) -> float:
-    """PSNR = 10 log10(255^2 / MSE) of colours in [0, 1] scaled by 255 (Sec. IV-C, Eq. 3); inf for equal images."""
-    import math
-    mse = exw_color_mse(a, b, ws, stream)
-    return math.inf if mse == 0.0 else -10.0 * math.log10(mse)
+    """PSNR = 10 log10(255^2 / MSE) of colours in [0, 1] scaled by 255 (Sec. IV-C, Eq. 3), computed on the device
+    (exw_psnr); inf for equal images.  Synchronises to read it back."""
+    H, W = int(a.shape[1]), int(a.shape[2])
+    _dev(a, "a", None, (3, H, W))
+    _dev(b, "b", a.dtype, (3, H, W))
+    dev = a.device
+    if ws is None:
+        ws = workspace(exw_workspace_bytes(OP_STATS, W, H, F32, 1, 1), dev)
+    out = torch.empty(2, dtype=torch.float64, device=dev)
+    _check(lib().exw_psnr(a.data_ptr(), b.data_ptr(), _cdt(a), W, H, out.data_ptr(), ws.data_ptr(), ws.numel(),
+                          _stream(stream, dev)))
+    return float(out[1].item())
 
 
 def exw_tuner_create() -> int:

@@ -80,6 +80,31 @@ static TileParams tile_params(const WsLayout &l, void *ws, int W, int H, int nfr
     return p;
 }
 
+// Workspace of exw_warp_recursive: the keys of the current step, two ping-pong copies of the carried depth and
+// motion, then the fill's workspace.
+struct RecursiveLayout {
+    size_t keys, depth[2], mv[2], fill, total;
+};
+static RecursiveLayout recursive_layout(int W, int H) {
+    const size_t px = (size_t)W * H;
+    RecursiveLayout r{};
+    size_t off = 0;
+    r.keys = off;
+    off += align_up(px * 8);
+    for (int i = 0; i < 2; ++i) {
+        r.depth[i] = off;
+        off += align_up(px * 4);
+        r.mv[i] = off;
+        off += align_up(px * 8);
+    }
+    r.fill = off;
+    off += ws_layout(W, H, 1, 1, false).total;
+    r.total = off;
+    return r;
+}
+
+size_t recursive_workspace_bytes(int W, int H) { return recursive_layout(W, H).total; }
+
 }  // namespace exw
 
 using namespace exw;
@@ -116,6 +141,7 @@ size_t exw_workspace_bytes(exw_op op, int W, int H, exw_dtype cdt, int nframes, 
         }
         case EXW_OP_WARP_BACKWARD: return ws_layout(W, H, 1, 1, true).total;
         case EXW_OP_STATS: return stats_workspace_bytes();
+        case EXW_OP_WARP_RECURSIVE: return recursive_workspace_bytes(W, H);
     }
     return 0;
 }
@@ -156,6 +182,15 @@ exw_status exw_color_mse(const void *a, const void *b, exw_dtype cdt, int W, int
     if (!aligned16(ws) || ws_bytes < stats_workspace_bytes()) return EXW_ERR_WORKSPACE;
     if (entry_check() != EXW_OK) return EXW_ERR_CUDA;
     return launch_color_mse(a, b, cdt, W, H, out, ws, (cudaStream_t)stream) == cudaSuccess ? EXW_OK : EXW_ERR_CUDA;
+}
+
+exw_status exw_psnr(const void *a, const void *b, exw_dtype cdt, int W, int H, double *out, void *ws, size_t ws_bytes,
+                    exw_stream_t stream) {
+    if (!size_ok(W, H) || !dtype_ok(cdt) || !aligned(a, csize(cdt)) || !aligned(b, csize(cdt)) || !aligned(out, 8))
+        return EXW_ERR_INVALID_ARG;
+    if (!aligned16(ws) || ws_bytes < stats_workspace_bytes()) return EXW_ERR_WORKSPACE;
+    if (entry_check() != EXW_OK) return EXW_ERR_CUDA;
+    return from_cuda(launch_color_mse(a, b, cdt, W, H, out, ws, (cudaStream_t)stream, true));
 }
 
 exw_status exw_motion_bounds(const float *depth, const float *mv, int W, int H, float *tile_bounds,
@@ -392,6 +427,63 @@ exw_status exw_extrapolate_host(const exw_frame *frames_host, const exw_frame *f
         if (f == cudaSuccess) f = cudaStreamWaitEvent(s, hs->back, 0);
     }
     return e == cudaSuccess && f == cudaSuccess ? EXW_OK : EXW_ERR_CUDA;
+}
+
+exw_status exw_warp_recursive(const void *color, exw_dtype cdt, const float *depth, const float *mv, int W, int H,
+                              int steps, unsigned flags, exw_frame_out *out, void *ws, size_t ws_bytes,
+                              exw_stream_t stream) {
+    if (!size_ok(W, H) || !dtype_ok(cdt) || steps < 1 || steps > 64 || out == nullptr ||
+        (flags & ~EXW_FLAG_NO_FILL) != 0 || !aligned(color, csize(cdt)) || !aligned(depth, 4) || !aligned(mv, 4))
+        return EXW_ERR_INVALID_ARG;
+    for (int i = 0; i < steps; ++i)
+        if (!aligned(out[i].color, csize(cdt)) || !aligned(out[i].mask, 1)) return EXW_ERR_INVALID_ARG;
+    const RecursiveLayout r = recursive_layout(W, H);
+    if (!aligned16(ws) || ws_bytes < r.total) return EXW_ERR_WORKSPACE;
+    if (entry_check() != EXW_OK) return EXW_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    char *b = (char *)ws;
+    uint64_t *keys = (uint64_t *)(b + r.keys);
+    const WsLayout fl = ws_layout(W, H, 1, 1, false);
+    void *fws = b + r.fill;
+    const void *c = color;
+    const float *d = depth, *m = mv;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < steps && e == cudaSuccess; ++i) {
+        // step i: warp the previous frame (the source for i = 0) by a quarter step of the motion it carries
+        e = launch_clear_keys(keys, (size_t)W * H, s);
+        if (e == cudaSuccess) e = launch_splat_global(d, m, W, H, 1, 2, keys, s);
+        TileParams p{};
+        p.color = c;
+        p.depth = d;
+        p.mv = m;
+        p.keys = keys;
+        p.W = W;
+        p.H = H;
+        p.nfrac = 1;
+        p.L = 2;
+        p.k0 = 1;
+        p.out_color[0] = out[i].color;
+        p.out_mask[0] = out[i].mask;
+        p.n5x = ceil_div(W, kFillTileSide);
+        p.n5y = ceil_div(H, kFillTileSide);
+        if (e == cudaSuccess) e = launch_warp_tiles(p, cdt, s);
+        if (e == cudaSuccess && (flags & EXW_FLAG_NO_FILL) == 0) {
+            TileParams f = tile_params(fl, fws, W, H, 1, 0, 0, 0);
+            f.mask_in = out[i].mask;
+            f.out_color[0] = out[i].color;
+            e = launch_zero(fws, fl.headers + sizeof(FrameHeader), s);
+            if (e == cudaSuccess) e = launch_fill_tiles(f, cdt, s);
+            if (e == cudaSuccess) e = launch_fixup(f, cdt, s);
+        }
+        if (e == cudaSuccess && i + 1 < steps) {  // the warped frame's depth and motion for the next step
+            float *dn = (float *)(b + r.depth[i & 1]), *mn = (float *)(b + r.mv[i & 1]);
+            e = launch_carry_motion(keys, out[i].mask, d, m, W, H, dn, mn, s);
+            d = dn;
+            m = mn;
+        }
+        c = out[i].color;
+    }
+    return from_cuda(e);
 }
 
 exw_status exw_warp_backward(const float *grad_out, const void *color, exw_dtype cdt, const float *depth,

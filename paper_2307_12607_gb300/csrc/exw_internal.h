@@ -152,11 +152,13 @@ cudaError_t launch_bounds_finalize(const FrameHeader *fh, float *frame_bounds, c
 
 cudaError_t launch_plan(const TileParams &p, exw_dtype cdt, cudaStream_t s);
 
+size_t recursive_workspace_bytes(int W, int H);
+
 // Frame statistics (exw_stats.cu): FP64 reductions into a small fixed workspace.
 size_t stats_workspace_bytes();
 cudaError_t launch_mv_variance(const float *mv, int W, int H, double *out, void *ws, cudaStream_t s);
 cudaError_t launch_color_mse(const void *a, const void *b, exw_dtype cdt, int W, int H, double *out, void *ws,
-                             cudaStream_t s);
+                             cudaStream_t s, bool psnr = false);
 cudaError_t launch_ssim(const void *a, const void *b, exw_dtype cdt, int W, int H, double *out, void *ws,
                         cudaStream_t s);
 cudaError_t launch_warp_tiles(const TileParams &p, exw_dtype cdt, cudaStream_t s);

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kStatThreads) mv_variance_kernel(const float *
 
 template <typename CT>
 __global__ void __launch_bounds__(kStatThreads) color_mse_kernel(const CT *__restrict__ a, const CT *__restrict__ b,
-                                                                 size_t n, StatWs *ws, double *out) {
+                                                                 size_t n, StatWs *ws, double *out, bool psnr) {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     double s = 0.0;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -143,7 +143,10 @@ __global__ void __launch_bounds__(kStatThreads) color_mse_kernel(const CT *__res
     if (!last_block(&ws->arrived) || threadIdx.x != 0) return;
     double t = 0.0;
     for (int k = 0; k < (int)gridDim.x; ++k) t += ws->part[k].n;
-    out[0] = t / (double)n;
+    const double mse = t / (double)n;
+    out[0] = mse;
+    // PSNR of colours in [0, 1] scaled by 255: 10 log10(255^2 / MSE) = -10 log10(MSE); +inf for equal images
+    if (psnr) out[1] = mse == 0.0 ? __longlong_as_double(0x7FF0000000000000ll) : -10.0 * log10(mse);
     ws->arrived = 0u;
 }
 
@@ -263,17 +266,17 @@ cudaError_t launch_mv_variance(const float *mv, int W, int H, double *out, void 
 }
 
 cudaError_t launch_color_mse(const void *a, const void *b, exw_dtype cdt, int W, int H, double *out, void *ws,
-                             cudaStream_t s) {
+                             cudaStream_t s, bool psnr) {
     cudaError_t e = cudaMemsetAsync(&static_cast<StatWs *>(ws)->arrived, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
     const size_t n = 3 * (size_t)W * H;
     timing_begin("exw_color_mse", s);
     if (cdt == EXW_F16)
         color_mse_kernel<__half><<<kStatBlocks, kStatThreads, 0, s>>>((const __half *)a, (const __half *)b, n,
-                                                                       static_cast<StatWs *>(ws), out);
+                                                                       static_cast<StatWs *>(ws), out, psnr);
     else
         color_mse_kernel<float><<<kStatBlocks, kStatThreads, 0, s>>>((const float *)a, (const float *)b, n,
-                                                                      static_cast<StatWs *>(ws), out);
+                                                                      static_cast<StatWs *>(ws), out, psnr);
     count_launch();
     timing_end("exw_color_mse", s);
     return cudaGetLastError();

@@ -146,6 +146,33 @@ def test_recursive_and_statistics_argument_checks(lib):
     assert lib.exw_ssim(a, a, 0, 64, 64, a, a, 8, None) == 5
 
 
+def test_psnr_and_recursive_warp_argument_checks(lib):
+    # exw_psnr follows exw_color_mse's rules; exw_warp_recursive refuses bad steps, flags, sizes and descriptors
+    # with EXW_ERR_INVALID_ARG (1) and a short workspace with EXW_ERR_WORKSPACE (5), before any launch
+    from paper_2307_12607_gb300 import _lib, binding as b
+    a = 4096
+    big = 1 << 26
+    assert lib.exw_psnr(a, a, 7, 8, 8, a, a, big, None) == 1                     # unknown colour type
+    assert lib.exw_psnr(a, a, 0, 8, 8, a + 4, a, big, None) == 1                 # out not 8-byte aligned
+    assert lib.exw_psnr(a, a, 0, 8, 8, a, a, 8, None) == 5                       # workspace too small
+    outs = (_lib.ExwFrameOut * 3)()
+    for i in range(3):
+        outs[i] = _lib.ExwFrameOut(16384, 20480)
+    P = lambda x: ctypes.cast(x, ctypes.c_void_p)
+    rec = lib.exw_warp_recursive
+    assert rec(a, 0, a, a, 64, 64, 0, 0, P(outs), a, big, None) == 1             # no step
+    assert rec(a, 0, a, a, 64, 64, 65, 0, P(outs), a, big, None) == 1            # too many steps
+    assert rec(a, 0, a, a, 64, 64, 3, 2, P(outs), a, big, None) == 1             # only EXW_FLAG_NO_FILL is known
+    assert rec(a, 0, a, a, 64, 64, 3, 0, None, a, big, None) == 1                # no descriptors
+    assert rec(a + 2, 0, a, a, 64, 64, 3, 0, P(outs), a, big, None) == 1         # FP32 colour misaligned
+    outs[1].mask = None
+    assert rec(a, 0, a, a, 64, 64, 3, 0, P(outs), a, big, None) == 1            # a step without a mask buffer
+    outs[1].mask = 20480
+    need = b.exw_workspace_bytes(b.OP_WARP_RECURSIVE, 64, 64)
+    assert need >= 64 * 64 * (8 + 2 * 12)                                        # keys + two carried fields
+    assert rec(a, 0, a, a, 64, 64, 3, 0, P(outs), a, need - 1, None) == 5
+
+
 def test_backward_bounds_and_fill_argument_checks(lib):
     a = 4096
     big = 1 << 20

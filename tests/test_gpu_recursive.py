@@ -59,3 +59,21 @@ def test_recursive_chain_matches_oracle(b, c, fill):
     for s, ((go, gm), (wo, wmask)) in enumerate(zip(got, want)):
         np.testing.assert_array_equal(gm.cpu().numpy(), wmask, err_msg=f"step {s + 1}")
         np.testing.assert_allclose(go.cpu().numpy(), wo, rtol=0, atol=(s + 1) * 2e-6, err_msg=f"step {s + 1}")
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
+def test_recursive_chain_is_the_staged_composition(b, dtype):
+    # exw_warp_recursive chains splat, warp, fill and carry on the device: bit-identical to the same entry points
+    # called one by one (FP16 colour too, rounded once per step as each exw_warp rounds its output)
+    color, depth, mv = case(("scene", 257, 131, 45))
+    c = torch.from_numpy(color).to(dtype).cuda()
+    d, m = torch.from_numpy(depth).cuda(), torch.from_numpy(mv).cuda()
+    got = b.exw_warp_recursive(c, d, m, 3)
+    iv = torch.int16 if dtype == torch.float16 else torch.int32
+    for s, (go, gm) in enumerate(got):
+        keys = b.exw_splat_motion(d, m, 1, 4)
+        out, mask = b.exw_warp(c, d, m, keys, 1, 4)
+        b.exw_fill_holes(out, mask)
+        assert torch.equal(mask, gm) and torch.equal(out.view(iv), go.view(iv)), f"step {s + 1}"
+        d, m = b.exw_carry_motion(keys, mask, d, m)
+        c = out

@@ -70,6 +70,9 @@ def test_color_mse_matches_oracle(b, dtype, W, H):
     assert got == pytest.approx(want, rel=max(1e-12, 3 * W * H * 2.0 ** -53), abs=0)
     assert b.exw_color_mse(xa, ya) == got
     assert b.exw_color_mse(xa, xa) == 0.0 and b.exw_psnr(xa, xa) == float("inf")
+    # PSNR on the device: -10 log10 of the same MSE (the log adds a few ulp)
+    assert b.exw_psnr(xa, ya) == pytest.approx(oracle.psnr(xa.cpu().double().numpy(), ya.cpu().double().numpy()),
+                                               rel=1e-12 + 3 * W * H * 2.0 ** -53, abs=0)
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
