@@ -31,8 +31,7 @@ constexpr int kGroupThreads = 256;                          // one fraction: 16 
 constexpr int kConsumerThreads = kMaxFrac * kGroupThreads;  // 768
 constexpr int kConsumerWarps = kConsumerThreads / 32;       // 24
 constexpr int kEngineThreads = kConsumerThreads + 32;       // + the producer warp
-constexpr int kBarConsumers = 1;                            // named barriers: 1 all consumers, 2 + g group g,
-constexpr int kBarPair = 11;                                // 11 + g group g on a paired smooth tile
+constexpr int kBarConsumers = 1;                            // named barriers: 1 all consumers, 2 + g group g
 constexpr int kMaxStreams = 48;                             // streams per launch (kernel-parameter space)
 constexpr int kRegionsPerItem = 2 * kMaxFrac;               // a bounds item: one region per half group (4 warps)
 constexpr int kPlansPerItem = kConsumerWarps;               // a plan item: one tile per consumer warp
@@ -95,6 +94,7 @@ struct alignas(16) TileSlot {
 };
 
 constexpr int kWindowBytes = 64512;  // both window shapes (56 x 48 FP32, 64 x 56 FP16) hold 64,512 bytes
+static_assert(64 * 16 * kConsumerWarps <= kWindowBytes, "the coarse pass's per-warp scratch fits one buffer");
 static_assert(sizeof(Window<float, kWinXF32, kWinYF32>) == kWindowBytes &&
                   sizeof(Window<__half, kWinXF16, kWinYF16>) == kWindowBytes,
               "one buffer size for both colour types");
@@ -908,40 +908,180 @@ __device__ __forceinline__ void fill_store_block(EngineSmem &s, const TileParams
     store_block<CT>(d, oc, om, TX, TY, c, m, write, vec);
 }
 
-// Coarse levels of the pyramid and the value of every tile without a valid pixel (all consumer threads).
+// Level-2 node of a column pair's 4 x 4 block from this lane's column of four pixels (all valid; the same pyramid
+// as mean4 over valid children): level 1 by a shuffle with the neighbouring column, level 2 with the next pair.
+// Meaningful on lanes with (lane & 3) == 0: the node (row band, lane >> 2).
+template <typename CT>
+__device__ __forceinline__ float4 smooth_level2(const CT out[4][3]) {
+    const int lane = threadIdx.x & 31;
+    float4 px[4], pp[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        px[r] = make_float4(to_f<CT>(out[r][0]), to_f<CT>(out[r][1]), to_f<CT>(out[r][2]), 1.0f);
+        pp[r] = make_float4(__shfl_xor_sync(0xFFFFFFFFu, px[r].x, 1), __shfl_xor_sync(0xFFFFFFFFu, px[r].y, 1),
+                            __shfl_xor_sync(0xFFFFFFFFu, px[r].z, 1), 1.0f);
+    }
+    const bool odd = lane & 1;
+    // level 1: rows 0-1 (A) and 2-3 (B) of this column pair, children in (row, column) order
+    const float4 A = odd ? mean4(pp[0], px[0], pp[1], px[1]) : mean4(px[0], pp[0], px[1], pp[1]);
+    const float4 B = odd ? mean4(pp[2], px[2], pp[3], px[3]) : mean4(px[2], pp[2], px[3], pp[3]);
+    const float4 Ap = make_float4(__shfl_xor_sync(0xFFFFFFFFu, A.x, 2), __shfl_xor_sync(0xFFFFFFFFu, A.y, 2),
+                                  __shfl_xor_sync(0xFFFFFFFFu, A.z, 2), 1.0f);
+    const float4 Bp = make_float4(__shfl_xor_sync(0xFFFFFFFFu, B.x, 2), __shfl_xor_sync(0xFFFFFFFFu, B.y, 2),
+                                  __shfl_xor_sync(0xFFFFFFFFu, B.z, 2), 1.0f);
+    const bool right = lane & 2;
+    return right ? mean4(Ap, A, Bp, B) : mean4(A, Ap, B, Bp);
+}
+
+// Lazy level-5 nodes.  A smooth tile has no hole, so the fill never changes it, and its level-5 node matters only to
+// the coarse pass of a fraction with a tile without any valid pixel -- which most frames never run.  The tile
+// publishes kNodeLazy instead of building its pyramid; when a coarse pass needs the node (it lies under the first
+// valid ancestor of an invalid tile), one warp recomputes it: the tile's outputs again from the source colour (the
+// same arithmetic as smooth_column_t, so the same bits), then the same pyramid.
+constexpr float kNodeLazy = 2.0f;    // .w of a valid node that is not computed
+constexpr float kNodeNeeded = 3.0f;  // .w of a lazy node the coarse pass needs
+
+template <typename CT>
+__device__ float4 smooth_node(const TileParams &p, int tile, int kk, float4 *l2) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t umx = __ldcg(&p.plans[tile].umx), umy = __ldcg(&p.plans[tile].umy);
+    const int k = p.k0 + kk;
+    // the fraction's constants, as uniform_frac computes them
+    const int ox = axis_off_of(umx, k, p.L), oy = axis_off_of(umy, k, p.L);
+    int sx, sy;
+    const float rx = residual(__uint_as_float(umx), k, p.L, ox, sx);
+    const float ry = residual(__uint_as_float(umy), k, p.L, oy, sy);
+    const float wx1 = fabsf(rx), wy1 = fabsf(ry);
+    const float wx0 = 1.0f - wx1, wy0 = 1.0f - wy1;
+    const float W00 = wx0 * wy0, W10 = wx1 * wy0, W01 = wx0 * wy1, W11 = wx1 * wy1;
+    const bool EX = sx != 0, EY = sy != 0;
+    const int j = (EX ? 1 : 0) | (EY ? 2 : 0) | (EX && EY ? 4 : 0);
+    const float inv = __frcp_rn(((W00 + ((j & 1) ? W10 : 0.0f)) + ((j & 2) ? W01 : 0.0f)) + ((j & 4) ? W11 : 0.0f));
+    const int X0 = (tile % p.n5x) * kFillTile, Y0 = (tile / p.n5x) * kFillTile;
+    const size_t plane = (size_t)p.W * p.H;
+    const CT *col = (const CT *)p.color;
+    const int cx = X0 + lane - ox, tx = cx + sx;  // source column and tap column (inside the frame: a smooth tile)
+#pragma unroll 2
+    for (int w = 0; w < kFillTile / 4; ++w) {
+        CT out[4][3];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int cy = Y0 + 4 * w + r - oy, ty = cy + sy;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                const CT *cp = col + ch * plane;
+                float n = W00 * to_f<CT>(cp[(size_t)cy * p.W + cx]);
+                if (EX) n = fmaf(W10, to_f<CT>(cp[(size_t)cy * p.W + tx]), n);
+                if (EY) n = fmaf(W01, to_f<CT>(cp[(size_t)ty * p.W + cx]), n);
+                if (EX && EY) n = fmaf(W11, to_f<CT>(cp[(size_t)ty * p.W + tx]), n);
+                out[r][ch] = to_storage<CT>(n * inv);
+            }
+        }
+        const float4 n2 = smooth_level2<CT>(out);
+        if ((lane & 3) == 0) l2[w * 8 + (lane >> 2)] = n2;
+    }
+    __syncwarp();
+    float4 l3, l4, l5;
+    upper_levels(l2, l3, l4, l5);
+    __syncwarp();
+    return l5;
+}
+
+// Coarse levels of the pyramid of one fraction above level 5 (all consumer threads): level 6 from the level-5
+// nodes, each further level from the one below, mean4 over the valid children.
+__device__ inline void coarse_levels(const float4 *nodes, float4 *cz, int n5x, int n5y) {
+    const int tid = threadIdx.x, nt = kConsumerThreads;
+    const float4 *child = nodes;
+    int cw = n5x, ch = n5y, off = 0;
+    while (cw > 1 || ch > 1) {
+        const int pw = (cw + 1) / 2, ph = (ch + 1) / 2;
+        float4 *par = cz + off;
+        for (int node = tid; node < pw * ph; node += nt) {
+            const int i = node / pw, j = node - i * pw;
+            float4 c[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int ci = 2 * i + (q >> 1), cj = 2 * j + (q & 1);
+                c[q] = (ci < ch && cj < cw) ? __ldcg(child + ci * cw + cj) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            par[node] = mean4(c[0], c[1], c[2], c[3]);
+        }
+        __threadfence_block();
+        bar_sync(kBarConsumers, kConsumerThreads);
+        child = par;
+        off += pw * ph;
+        cw = pw;
+        ch = ph;
+    }
+}
+
+// Coarse levels of the pyramid and the value of every tile without a valid pixel (all consumer threads).  Lazy
+// level-5 nodes are computed first where a fill value depends on them: under the first valid ancestor of some tile
+// without a valid pixel.  scratch: 64 float4 per consumer warp of shared memory.
 // (Not inlined, like the fix-up slice: the engine's throughput depends on how compact the code of its frequent
 // items stays in the instruction cache.)
-static __device__ __noinline__ void engine_coarse_pass(const TileParams &p) {
-    const int tid = threadIdx.x, nt = kConsumerThreads;
+// Coarse levels of the pyramid and the value of every tile without a valid pixel (all consumer threads).  Lazy
+// level-5 nodes are computed first where a fill value depends on them: in the subtree of the first valid ancestor
+// of some tile without a valid pixel.  That ancestor is found without the pyramid: an ancestor d levels above
+// level 5 is valid when a level-5 node of its 2^d x 2^d block is (a lazy node is valid).  scratch: 64 float4 per
+// consumer warp of shared memory.
+// (Not inlined, like the fix-up slice: the engine's throughput depends on how compact the code of its frequent
+// items stays in the instruction cache.)
+static __device__ __noinline__ void engine_coarse_pass(const TileParams &p, float4 *scratch, int cdt) {
+    const int tid = threadIdx.x, nt = kConsumerThreads, lane = tid & 31, wid = tid >> 5;
     const int n5 = p.n5x * p.n5y;
     for (int kk = 0; kk < p.nfrac; ++kk) {
         const uint32_t cnt = __ldcg(&p.fh->ninvalid[kk]);
         if (cnt == 0u) continue;
-        const float4 *child = p.nodes + (size_t)kk * n5;
+        float4 *nodes = p.nodes + (size_t)kk * n5;
         float4 *cz = p.coarse + (size_t)kk * p.ncoarse;
-        int cw = p.n5x, ch = p.n5y, off = 0;
-        while (cw > 1 || ch > 1) {
-            const int pw = (cw + 1) / 2, ph = (ch + 1) / 2;
-            float4 *par = cz + off;
-            for (int node = tid; node < pw * ph; node += nt) {
-                const int i = node / pw, j = node - i * pw;
-                float4 c[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int ci = 2 * i + (q >> 1), cj = 2 * j + (q & 1);
-                    c[q] = (ci < ch && cj < cw) ? __ldcg(child + ci * cw + cj) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const uint32_t *list = p.list + (size_t)kk * n5;
+        // 1. per tile without a valid pixel (a warp each): the block of its first valid ancestor; its lazy nodes
+        //    are needed
+        bool any = false;
+        for (uint32_t e = wid; e < cnt; e += kConsumerWarps) {
+            const uint32_t tile = __ldcg(list + e);
+            const int tx = (int)(tile % (uint32_t)p.n5x), ty = (int)(tile / (uint32_t)p.n5x);
+            for (int d = 1; (1 << (d - 1)) < max(p.n5x, p.n5y); ++d) {
+                const int bx0 = (tx >> d) << d, by0 = (ty >> d) << d;
+                const int bw = min(1 << d, p.n5x - bx0), bh = min(1 << d, p.n5y - by0);
+                bool valid = false;
+                for (int c = lane; c < bw * bh && !valid; c += 32)
+                    valid = __ldcg(&nodes[(by0 + c / bw) * p.n5x + bx0 + c % bw].w) != 0.0f;
+                if (!__any_sync(0xFFFFFFFFu, valid)) continue;
+                for (int c = lane; c < bw * bh; c += 32) {
+                    float *w = &nodes[(by0 + c / bw) * p.n5x + bx0 + c % bw].w;
+                    if (__ldcg(w) == kNodeLazy) {
+                        *w = kNodeNeeded;
+                        any = true;
+                    }
                 }
-                par[node] = mean4(c[0], c[1], c[2], c[3]);
+                break;
+            }
+        }
+        __threadfence_block();
+        // 2. the needed lazy nodes, one warp per tile
+        if (bar_red_or(kBarConsumers, kConsumerThreads, any)) {
+            float4 *l2 = scratch + 64 * wid;
+            for (int base = 32 * wid; base < n5; base += 32 * kConsumerWarps) {
+                const int i = base + lane;
+                unsigned m = __ballot_sync(0xFFFFFFFFu, i < n5 && __ldcg(&nodes[i].w) == kNodeNeeded);
+                while (m) {
+                    const int t = base + __ffs(m) - 1;
+                    m &= m - 1u;
+                    const float4 v =
+                        cdt == EXW_F16 ? smooth_node<__half>(p, t, kk, l2) : smooth_node<float>(p, t, kk, l2);
+                    if (lane == 0) nodes[t] = v;
+                }
             }
             __threadfence_block();
             bar_sync(kBarConsumers, kConsumerThreads);
-            child = par;
-            off += pw * ph;
-            cw = pw;
-            ch = ph;
         }
+        // 3. the coarse levels (the ancestors of lazy nodes that were not needed are never read), then each invalid
+        //    tile's first valid ancestor
+        coarse_levels(nodes, cz, p.n5x, p.n5y);
         for (uint32_t e = tid; e < cnt; e += nt) {
-            const uint32_t tile = __ldcg(p.list + (size_t)kk * n5 + e);
+            const uint32_t tile = __ldcg(list + e);
             int ax = (int)(tile % (uint32_t)p.n5x), ay = (int)(tile / (uint32_t)p.n5x);
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             int w = p.n5x, h = p.n5y, o = 0;
@@ -1041,53 +1181,6 @@ __device__ __forceinline__ void store_column(const FrameDims &p, CT *oc, uint8_t
     }
 }
 
-__device__ __forceinline__ void smooth_tail(EngineSmem &s, const TileParams &p, int g, int kk, int tile, int buf,
-                                            int bar);
-
-// Level-5 node of a tile whose pixels are all valid, from columns of four pixels (same pyramid as mean4 over
-// valid children): levels 1 and 2 by shuffles, the level-2 row of each warp to shared memory, levels 3-5 by
-// warp tw, which publishes it (defer: warp tw only arrives; it builds the levels later, by smooth_tail).  The
-// other warps only arrive at the group barrier.
-template <typename CT>
-__device__ __forceinline__ void smooth_publish(EngineSmem &s, const TileParams &p, int g, int kk, int tile, int buf,
-                                               int bar, int tw, bool defer, const CT out[4][3]) {
-    const int tg = threadIdx.x & (kGroupThreads - 1);
-    const int lane = tg & 31, w = tg >> 5;
-    float4 px[4], pp[4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        px[r] = make_float4(to_f<CT>(out[r][0]), to_f<CT>(out[r][1]), to_f<CT>(out[r][2]), 1.0f);
-        pp[r] = make_float4(__shfl_xor_sync(0xFFFFFFFFu, px[r].x, 1), __shfl_xor_sync(0xFFFFFFFFu, px[r].y, 1),
-                            __shfl_xor_sync(0xFFFFFFFFu, px[r].z, 1), 1.0f);
-    }
-    const bool odd = lane & 1;
-    // level 1: rows 0-1 (A) and 2-3 (B) of this column pair, children in (row, column) order
-    const float4 A = odd ? mean4(pp[0], px[0], pp[1], px[1]) : mean4(px[0], pp[0], px[1], pp[1]);
-    const float4 B = odd ? mean4(pp[2], px[2], pp[3], px[3]) : mean4(px[2], pp[2], px[3], pp[3]);
-    const float4 Ap = make_float4(__shfl_xor_sync(0xFFFFFFFFu, A.x, 2), __shfl_xor_sync(0xFFFFFFFFu, A.y, 2),
-                                  __shfl_xor_sync(0xFFFFFFFFu, A.z, 2), 1.0f);
-    const float4 Bp = make_float4(__shfl_xor_sync(0xFFFFFFFFu, B.x, 2), __shfl_xor_sync(0xFFFFFFFFu, B.y, 2),
-                                  __shfl_xor_sync(0xFFFFFFFFu, B.z, 2), 1.0f);
-    const bool right = lane & 2;
-    const float4 n2 = right ? mean4(Ap, A, Bp, B) : mean4(A, Ap, B, Bp);
-    float4 *l2 = s.l2[g][buf];
-    if ((lane & 3) == 0) l2[w * 8 + (lane >> 2)] = n2;
-    if (w != tw) {
-        asm volatile("bar.arrive %0, %1;" ::"r"(bar), "r"(kGroupThreads) : "memory");
-        return;
-    }
-    if (!defer) smooth_tail(s, p, g, kk, tile, buf, bar);
-}
-
-// Levels 3-5 and the node of a smooth tile once every warp of the group has left its level-2 row (one warp).
-__device__ __forceinline__ void smooth_tail(EngineSmem &s, const TileParams &p, int g, int kk, int tile, int buf,
-                                            int bar) {
-    bar_sync(bar, kGroupThreads);
-    float4 l3, l4, l5;
-    upper_levels(s.l2[g][buf], l3, l4, l5);
-    if ((threadIdx.x & 31) == 0) publish_node(p, l5, kk, tile);
-}
-
 // ------------------------------------------------------------------------------------------------------------
 // Consumers
 // ------------------------------------------------------------------------------------------------------------
@@ -1116,13 +1209,12 @@ __device__ __forceinline__ void tile_group(EngineSmem &s, const TileSlot &sl, in
             smooth_column<CT, WX, WY>(col, q ? sl.wx02 : wx0, q ? sl.wy02 : wy0, q ? sl.u2[kk] : sl.u[kk], x0, y0,
                                       out);
             store_column<CT>(d, oc, om, x0, y0, out);
-            // a pair: warp 0 builds the first tile's levels after its part of the second, warp 7 the second's, so
-            // the two tails overlap
-            if (FILL)
-                smooth_publish<CT>(s, p, g, kk, q ? sl.index2 : tile, buf ^ q, q ? kBarPair + g : 2 + g,
-                                   q ? kGroupThreads / 32 - 1 : 0, n == 2 && q == 0, out);
         }
-        if (FILL && n == 2 && (threadIdx.x & (kGroupThreads - 1)) < 32) smooth_tail(s, p, g, kk, tile, buf, 2 + g);
+        // no hole: the fill leaves the tile as it is, and its level-5 node is computed only if a coarse pass needs it
+        if (FILL && (threadIdx.x & (kGroupThreads - 1)) == 0) {
+            publish_node(p, make_float4(0.f, 0.f, 0.f, kNodeLazy), kk, tile);
+            if (n == 2) publish_node(p, make_float4(0.f, 0.f, 0.f, kNodeLazy), kk, sl.index2);
+        }
         return;
     }
     float4 c[4];
@@ -1248,7 +1340,9 @@ __device__ void engine_consumer(EngineSmem &s, uint32_t *status) {
         } else if (kind == kSlotFixup) {
             if (sl.index == 0) {  // every node of the stream is counted: build the coarse levels, then release
                 __threadfence();
-                engine_coarse_pass(p);
+                float4 *scratch = reinterpret_cast<float4 *>(s.win[b]);  // no window lands in a fix-up slot's buffer
+                engine_coarse_pass(p, scratch, sl.cdt);
+                fence_proxy_async_smem();  // the scratch writes before a later window lands in this buffer
                 __threadfence();
                 bar_sync(kBarConsumers, kConsumerThreads);
                 if (tid == 0) asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&p.fh->cready), "r"(1u) : "memory");

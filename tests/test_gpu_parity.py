@@ -261,6 +261,40 @@ def test_smooth_tiles_every_residual_sign(b, pan, dtype):
             np.testing.assert_allclose(out[j].cpu().numpy().astype(np.float64), wo, rtol=0, atol=tol)
 
 
+@pytest.mark.parametrize("dtype", [np.float32, np.float16])
+@pytest.mark.parametrize("hole", [(128, 256, 64, 160), (0, 384, 0, 256), (32, 480, 96, 168)])
+def test_lazy_smooth_nodes_under_large_holes(b, dtype, hole):
+    # smooth tiles (one motion over a smooth surface) do not build their pyramid; when a fraction has tiles without
+    # any valid pixel, the coarse pass recomputes the smooth tiles' level-5 nodes it needs -- up to most of the frame
+    # when the hole covers three quarters of it -- and the fill must equal the staged fill bit for bit
+    W, H = 512, 256
+    rng = np.random.default_rng(sum(hole))
+    color = rng.uniform(size=(3, H, W)).astype(np.float32).astype(dtype)
+    yy, xx = np.mgrid[0:H, 0:W]
+    depth = (40.0 + 0.002 * xx + 0.003 * yy).astype(np.float32)
+    x0, x1, y0, y1 = hole
+    depth[y0:y1, x0:x1] = np.nan                      # sources that never land: whole tiles without a valid pixel
+    mv = np.empty((2, H, W), np.float32)
+    mv[0], mv[1] = 1.3, -0.7
+    c, d, m = dev(color), dev(depth), dev(mv)
+    ws = b.workspace(b.exw_workspace_bytes(b.OP_EXTRAPOLATE, W, H, b.F16 if dtype == np.float16 else b.F32, 1, 3),
+                     c.device)
+    out, mask = b.exw_extrapolate(c, d, m, fill=True, ws=ws)
+    st = b.frame_stats(ws)
+    assert st["tiles_smooth"] > 0 and min(st["tiles_without_valid_pixel"]) > 0
+    iv = torch.int16 if dtype == np.float16 else torch.int32
+    for j in range(3):
+        keys = b.exw_splat_motion(d, m, j + 1, 4)
+        so, sm = b.exw_warp(c, d, m, keys, j + 1, 4)
+        b.exw_fill_holes(so, sm)
+        assert torch.equal(sm, mask[j]) and torch.equal(so.view(iv), out[j].view(iv)), f"P_{j + 1}"
+    ref = oracle.extrapolate(color.astype(np.float64), depth, mv, 3, storage=dtype)
+    tol = 1e-3 if dtype == np.float16 else 2e-6
+    for j, (wo, wm, _) in enumerate(ref):
+        np.testing.assert_array_equal(mask[j].cpu().numpy(), wm)
+        np.testing.assert_allclose(out[j].cpu().numpy().astype(np.float64), wo, rtol=0, atol=tol)
+
+
 def test_uniform_tiles_with_foreign_motion_inside_their_source(b):
     # a uniformly panning background holds a small object moving so fast that it lands far away: tiles whose
     # candidate sources all pan are uniform, yet their source window contains the object's pixels, which must not
