@@ -481,14 +481,40 @@ def _extras_diff(b, devc, ex):
                 b.exw_warp(c, d, m, keys, k, 4, out, mask)
                 b.exw_l2_loss_grad(out, targets[f][k - 1], mask, gout, loss)
                 b.exw_warp_backward(gout, c, d, m, None, k, 4, gc, gm, wsd)   # keys recomputed (checkpointing)
+    # the fused, batched pass: one call for the 8 frames and 3 fractions (keys recomputed per frame, each source
+    # tile read once, deterministic gradients)
+    c_all = torch.stack([f[0] for f in fr])
+    d_all = torch.stack([f[1] for f in fr])
+    m_all = torch.stack([f[2] for f in fr])
+    t_all = torch.stack([torch.stack(t) for t in targets])
+    gcb = torch.zeros((8, 3, H, W), device=devc)
+    gmb = torch.zeros((8, 2, H, W), device=devc)
+    lossb = torch.empty(8, dtype=torch.float64, device=devc)
+    wsf = b.workspace(b.exw_workspace_bytes(b.OP_WARP_L2_GRAD, W, H, b.F32, 1, 3), devc)
+
+    def fused():
+        b.exw_warp_l2_grad(c_all, d_all, m_all, t_all, 3, grad_color=gcb, grad_mv=gmb, loss=lossb, ws=wsf)
     ms_f = _event_ms(fwd, 3)
     ms_fb = _event_ms(fwd_bwd, 3)
+    ms_fused = _event_ms(fused, 10)
     px = 8 * 3 * W * H
-    ex["fwd_bwd_1080p"] = {"value": px / ms_fb / 1e3, "unit": "Mpixel/s", "fwd_only": px / ms_f / 1e3,
-                           "ms_per_step": ms_fb, "kernel_us": _kernel_means(b, fwd_bwd),
-                           "workload": "8 frames 1920x1080 FP32, k = 1..3: splat + warp + L2 loss against the ground "
-                                       "truth at t + k/4 + adjoint w.r.t. colour and motion with the splat keys "
-                                       "recomputed in the backward (activation checkpointing)"}
+    peak, _ = peaks()
+    # algorithmic bytes per source pixel of one frame (3 fractions): the source read once (colour 12, depth 4,
+    # motion 8), the three targets (36), the colour and motion gradients read and written once (2 x (12 + 8))
+    alg = (12 + 4 + 8) + 3 * 12 + 2 * (12 + 8)
+    ex["fwd_bwd_1080p"] = {"value": px / ms_fused / 1e3, "unit": "Mpixel/s", "ms_per_step": ms_fused,
+                           "kernel_us": _kernel_means(b, fused),
+                           "roofline": {"bound": "hbm", "algorithmic_bytes_per_source_px": alg,
+                                        "achieved_gbs": alg * 8 * W * H / (ms_fused / 1e3) / 1e9,
+                                        "frac": alg * 8 * W * H / (ms_fused / 1e3) / 1e9 / peak},
+                           "staged_path": {"value": px / ms_fb / 1e3, "ms_per_step": ms_fb,
+                                           "fwd_only": px / ms_f / 1e3, "kernel_us": _kernel_means(b, fwd_bwd)},
+                           "ratio_vs_staged": ms_fb / ms_fused,
+                           "workload": "8 frames 1920x1080 FP32, k = 1..3: forward warp + L2 loss against the ground "
+                                       "truth at t + k/4 + adjoint w.r.t. colour and motion, the splat keys "
+                                       "recomputed (activation checkpointing); value: the fused batched pass "
+                                       "(exw_warp_l2_grad, one call); staged_path: splat, warp, loss and adjoint "
+                                       "per frame and fraction"}
 
 
 def copy_ceiling(host_in, dev_in, dev_out, host_out, reps=3):

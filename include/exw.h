@@ -81,7 +81,8 @@ typedef enum exw_op {
     EXW_OP_EXTRAPOLATE = 2,
     EXW_OP_WARP_BACKWARD = 3,
     EXW_OP_STATS = 4,
-    EXW_OP_WARP_RECURSIVE = 5
+    EXW_OP_WARP_RECURSIVE = 5,
+    EXW_OP_WARP_L2_GRAD = 6
 } exw_op;
 
 #define EXW_MASK_EMPTY 1u
@@ -255,6 +256,29 @@ EXW_API exw_status exw_ssim(const void *a, const void *b, exw_dtype cdt, int W, 
 EXW_API exw_status exw_warp_backward(const float *grad_out, const void *color, exw_dtype cdt, const float *depth,
                              const float *mv, const uint64_t *keys, int W, int H, int k, int denom,
                              float *grad_color, float *grad_mv, void *ws, size_t ws_bytes, exw_stream_t stream);
+
+/* One frame of the training pass exw_warp_l2_grad (device pointers). */
+typedef struct exw_train_frame {
+    exw_frame src;                     /* F_t: colour (cdt), depth, motion */
+    const void *target[EXW_MAX_FRAC];  /* [3][H][W] (cdt): what P_k should be, k = 1..nfrac */
+    float *grad_color;                 /* [3][H][W] float32, accumulated (+=): dL/d colour */
+    float *grad_mv;                    /* [2][H][W] float32, accumulated (+=): dL/d motion */
+} exw_train_frame;
+
+/* The warp of stage (b) (Sec. II-B, Sec. III-B) inside a training loss, for nframes frames of one size and colour
+ * type and the fractions k/4, k = 1..nfrac (Sec. IV-B): the forward warp P_k, the loss
+ *     L_f = sum over k, over non-hole targets q of P_k and over the 3 channels of (P_k(q) - target_k(q))^2,
+ * and its adjoint with every integer decision held fixed, as exw_splat_motion + exw_warp + exw_l2_loss_grad +
+ * exw_warp_backward with keys = NULL would give per fraction -- fused: per frame one pass computes the keys of
+ * every fraction (activation checkpointing: nothing of the forward is kept between calls), then one pass over
+ * 32 x 32 source tiles reads each tile once, recomputes each winner's forward value with stage (b)'s arithmetic
+ * and adds the gradients of all fractions (deterministic: each element is summed by one thread, fractions in
+ * order, so the gradients equal nfrac exw_warp_backward calls bit for bit).  The paper does not differentiate the
+ * warp; this is a library facility.  frames [nframes] is a HOST array of descriptors; loss [nframes] is a DEVICE
+ * float64 array, written (summed in FP64 in a fixed order).  Workspace: exw_workspace_bytes(EXW_OP_WARP_L2_GRAD,
+ * W, H, cdt, 1, nfrac) (the key planes of one frame; frames run one after another on the stream). */
+EXW_API exw_status exw_warp_l2_grad(const exw_train_frame *frames, int nframes, int nfrac, double *loss, void *ws,
+                                    size_t ws_bytes, exw_stream_t stream);
 
 /* L2 loss of a warped frame against a target over its non-hole pixels (the loss the differentiation workload
  * trains against): loss += sum over mask == 0 and 3 channels of (out - target)^2 (float32 device scalar,

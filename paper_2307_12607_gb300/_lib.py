@@ -40,6 +40,7 @@ PROTOTYPES = {
     "exw_ssim": (I, [P, P, I, I, I, P, P, SZ, P]),
     "exw_warp_backward": (I, [P, P, I, P, P, P, I, I, I, I, P, P, P, SZ, P]),
     "exw_l2_loss_grad": (I, [P, P, I, P, I, I, P, P, P]),
+    "exw_warp_l2_grad": (I, [P, I, I, P, P, SZ, P]),
     "exw_device_status": (I, [P, P]),
     "exw_tuner_create": (P, []),
     "exw_tuner_destroy": (None, [P]),
@@ -59,6 +60,10 @@ class ExwFrame(ctypes.Structure):
 
 class ExwFrameOut(ctypes.Structure):
     _fields_ = [("color", P), ("mask", P)]
+
+
+class ExwTrainFrame(ctypes.Structure):
+    _fields_ = [("src", ExwFrame), ("target", P * 3), ("grad_color", P), ("grad_mv", P)]
 
 
 class ExwStreamDesc(ctypes.Structure):

@@ -254,6 +254,7 @@ def exw_extrapolate_host(color, depth, mv, nfrac: int = 3, fill: bool = True, ou
 
 OP_STATS = 4
 OP_WARP_RECURSIVE = 5
+OP_WARP_L2_GRAD = 6
 
 
 def exw_carry_motion(keys, mask, depth, mv, depth_out=None, mv_out=None, stream=None):
@@ -439,6 +440,43 @@ def exw_warp_backward(grad_out, color, depth, mv, keys, k: int, denom: int = 4, 
                                    _dev(grad_mv, "grad_mv", torch.float32, (2, H, W)), wsp, wsn,
                                    _stream(stream, dev)))
     return grad_color, grad_mv
+
+
+def exw_warp_l2_grad(color, depth, mv, targets, nfrac: int = 3, grad_color=None, grad_mv=None, loss=None, ws=None,
+                     stream=None):
+    """Forward warp, L2 loss and adjoint of P_1..P_nfrac for a batch of frames in one call (exw_warp_l2_grad):
+    colour [F][3][H][W], depth [F][H][W], motion [F][2][H][W], targets [F][nfrac][3][H][W] (the colour dtype).
+    Returns (loss [F] float64 -- per frame, the sum over fractions, non-hole targets and channels of the squared
+    difference --, grad_color [F][3][H][W], grad_mv [F][2][H][W]); the gradients are accumulated into the tensors
+    passed (zeros when None)."""
+    F, _, H, W = (int(v) for v in color.shape)
+    dev = color.device
+    cdt = _cdt(color)
+    if grad_color is None:
+        grad_color = torch.zeros((F, 3, H, W), dtype=torch.float32, device=dev)
+    if grad_mv is None:
+        grad_mv = torch.zeros((F, 2, H, W), dtype=torch.float32, device=dev)
+    if loss is None:
+        loss = torch.empty(F, dtype=torch.float64, device=dev)
+    _dev(color, "color", None, (F, 3, H, W))
+    _dev(depth, "depth", torch.float32, (F, H, W))
+    _dev(mv, "mv", torch.float32, (F, 2, H, W))
+    _dev(targets, "targets", color.dtype, (F, nfrac, 3, H, W))
+    _dev(grad_color, "grad_color", torch.float32, (F, 3, H, W))
+    _dev(grad_mv, "grad_mv", torch.float32, (F, 2, H, W))
+    _dev(loss, "loss", torch.float64, (F,))
+    if ws is None:
+        ws = workspace(exw_workspace_bytes(OP_WARP_L2_GRAD, W, H, cdt, 1, nfrac), dev)
+    frames = (_lib.ExwTrainFrame * F)()
+    for f in range(F):
+        frames[f].src = _lib.ExwFrame(color[f].data_ptr(), depth[f].data_ptr(), mv[f].data_ptr(), W, H, cdt)
+        for j in range(nfrac):
+            frames[f].target[j] = targets[f, j].data_ptr()
+        frames[f].grad_color = grad_color[f].data_ptr()
+        frames[f].grad_mv = grad_mv[f].data_ptr()
+    _check(lib().exw_warp_l2_grad(ctypes.cast(frames, ctypes.c_void_p), F, int(nfrac), loss.data_ptr(),
+                                  ws.data_ptr(), ws.numel(), _stream(stream, dev)))
+    return loss, grad_color, grad_mv
 
 
 def exw_l2_loss_grad(out, target, mask, grad_out=None, loss=None, stream=None):

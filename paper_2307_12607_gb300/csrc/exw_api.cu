@@ -142,6 +142,9 @@ size_t exw_workspace_bytes(exw_op op, int W, int H, exw_dtype cdt, int nframes, 
         case EXW_OP_WARP_BACKWARD: return ws_layout(W, H, 1, 1, true).total;
         case EXW_OP_STATS: return stats_workspace_bytes();
         case EXW_OP_WARP_RECURSIVE: return recursive_workspace_bytes(W, H);
+        case EXW_OP_WARP_L2_GRAD:
+            if (nfrac < 1 || nfrac > EXW_MAX_FRAC) return 0;
+            return train_workspace_bytes(W, H, nfrac);
     }
     return 0;
 }
@@ -509,6 +512,29 @@ exw_status exw_warp_backward(const float *grad_out, const void *color, exw_dtype
         return EXW_ERR_CUDA;
     }
     return from_cuda(launch_backward(grad_out, color, cdt, depth, mv, kp, W, H, k, L, grad_color, grad_mv, s));
+}
+
+exw_status exw_warp_l2_grad(const exw_train_frame *frames, int nframes, int nfrac, double *loss, void *ws,
+                            size_t ws_bytes, exw_stream_t stream) {
+    if (frames == nullptr || nframes < 1 || nfrac < 1 || nfrac > EXW_MAX_FRAC || !aligned(loss, 8))
+        return EXW_ERR_INVALID_ARG;
+    const int W = frames[0].src.W, H = frames[0].src.H;
+    const exw_dtype cdt = frames[0].src.cdt;
+    if (!size_ok(W, H) || !dtype_ok(cdt)) return EXW_ERR_INVALID_ARG;
+    for (int f = 0; f < nframes; ++f) {
+        const exw_train_frame &t = frames[f];
+        if (t.src.W != W || t.src.H != H || t.src.cdt != cdt || !aligned(t.src.color, csize(cdt)) ||
+            !aligned(t.src.depth, 4) || !aligned(t.src.mv, 4) || !aligned(t.grad_color, 4) || !aligned(t.grad_mv, 4))
+            return EXW_ERR_INVALID_ARG;
+        for (int j = 0; j < nfrac; ++j)
+            if (!aligned(t.target[j], csize(cdt))) return EXW_ERR_INVALID_ARG;
+    }
+    if (!aligned16(ws) || ws_bytes < train_workspace_bytes(W, H, nfrac)) return EXW_ERR_WORKSPACE;
+    if (entry_check() != EXW_OK) return EXW_ERR_CUDA;
+    cudaError_t e = cudaSuccess;
+    for (int f = 0; f < nframes && e == cudaSuccess; ++f)
+        e = launch_train_frame(frames[f], nfrac, loss + f, ws, (cudaStream_t)stream);
+    return from_cuda(e);
 }
 
 exw_status exw_l2_loss_grad(const void *out, const void *target, exw_dtype cdt, const uint8_t *mask, int W, int H,

@@ -165,53 +165,12 @@ __device__ __forceinline__ bool is_crack(uint32_t dq, uint32_t d0, uint32_t d1, 
 // non-positive tap depth fails it.
 __device__ __forceinline__ bool tap_agrees(float Dt, float Dp) { return 32.0f * fabsf(Dt - Dp) <= Dp; }
 
-// Bilinear gather for target (qx, qy) at its winner (px, py): taps p, p+sx, p+sy, p+sx+sy (in this order),
-// renormalised over the participating ones.  Returns the colour in out[3].
-template <class Acc>
-__device__ __forceinline__ void gather_at(const Acc &a, uint32_t dbits, int px, int py, int qx, int qy, int k, int L,
-                                          int W, int H, float out[3]) {
-    const auto i00 = a.at(px, py);
-    int sx, sy;
-    const float rx = residual(a.mx(i00), k, L, qx - px, sx);
-    const float ry = residual(a.my(i00), k, L, qy - py, sy);
-    const float Dp = __uint_as_float(dbits);
-    const float ax = fabsf(rx), ay = fabsf(ry);
-    const float wx0 = 1.0f - ax, wy0 = 1.0f - ay;
-    const bool inx = sx != 0 && (unsigned)(px + sx) < (unsigned)W;
-    const bool iny = sy != 0 && (unsigned)(py + sy) < (unsigned)H;
-    const auto i10 = i00 + sx;
-    const auto i01 = sy > 0 ? i00 + a.stride() : i00 - a.stride();
-    const auto i11 = i01 + sx;
-    float w = wx0 * wy0;
-    float den = w;
-    float n0 = w * a.c(0, i00), n1 = w * a.c(1, i00), n2 = w * a.c(2, i00);
-    if (inx && tap_agrees(a.d(i10), Dp)) {
-        w = ax * wy0;
-        den += w;
-        n0 += w * a.c(0, i10);
-        n1 += w * a.c(1, i10);
-        n2 += w * a.c(2, i10);
-    }
-    if (iny) {
-        if (tap_agrees(a.d(i01), Dp)) {
-            w = wx0 * ay;
-            den += w;
-            n0 += w * a.c(0, i01);
-            n1 += w * a.c(1, i01);
-            n2 += w * a.c(2, i01);
-        }
-        if (inx && tap_agrees(a.d(i11), Dp)) {
-            w = ax * ay;
-            den += w;
-            n0 += w * a.c(0, i11);
-            n1 += w * a.c(1, i11);
-            n2 += w * a.c(2, i11);
-        }
-    }
-    const float inv = __frcp_rn(den);
-    out[0] = n0 * inv;
-    out[1] = n1 * inv;
-    out[2] = n2 * inv;
+// The products and sums of the gather are written with explicit round-to-nearest intrinsics (never fused into an
+// FMA by the compiler), so every path that computes a gather -- the per-tile passes, the engine's window, uniform
+// and smooth tiles, the recomputation in the fused training pass -- gets the same bits in any context.
+// Sum of the bilinear weights of the participating taps (0 for the others), in the order 00, 10, 01, 11.
+__device__ __forceinline__ float weight_sum(float w00, float w10, float w01, float w11) {
+    return __fadd_rn(__fadd_rn(__fadd_rn(w00, w10), w01), w11);
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -230,7 +189,7 @@ __device__ __forceinline__ float4 mean4(float4 c0, float4 c1, float4 c2, float4 
     if (c3.w != 0.0f) { a0 += c3.x; a1 += c3.y; a2 += c3.z; ++cnt; }
     if (cnt == 0) return make_float4(0.f, 0.f, 0.f, 0.f);
     const float inv = cnt == 1 ? 1.0f : cnt == 2 ? 0.5f : cnt == 3 ? (1.0f / 3.0f) : 0.25f;
-    return make_float4(a0 * inv, a1 * inv, a2 * inv, 1.0f);
+    return make_float4(__fmul_rn(a0, inv), __fmul_rn(a1, inv), __fmul_rn(a2, inv), 1.0f);
 }
 
 __device__ __forceinline__ float4 shfl4_xor(float4 v, int m) {

@@ -168,8 +168,9 @@ __device__ __forceinline__ void uniform_frac(UniformFrac &u, const TileParams &p
     const float ry = residual(__uint_as_float(umy), k, p.L, oy, sy);
     const float wx1 = fabsf(rx), wy1 = fabsf(ry);
     const float wx0 = 1.0f - wx1, wy0 = 1.0f - wy1;
-    const float W00 = wx0 * wy0, W10 = wx1 * wy0, W01 = wx0 * wy1, W11 = wx1 * wy1;
-    u.inv[j] = __frcp_rn(((W00 + ((j & 1) ? W10 : 0.0f)) + ((j & 2) ? W01 : 0.0f)) + ((j & 4) ? W11 : 0.0f));
+    const float W00 = __fmul_rn(wx0, wy0), W10 = __fmul_rn(wx1, wy0), W01 = __fmul_rn(wx0, wy1),
+                W11 = __fmul_rn(wx1, wy1);
+    u.inv[j] = __frcp_rn(weight_sum(W00, (j & 1) ? W10 : 0.0f, (j & 2) ? W01 : 0.0f, (j & 4) ? W11 : 0.0f));
     if (j == 0) {
         u.ox = ox;
         u.oy = oy;
@@ -517,11 +518,11 @@ __device__ __forceinline__ void uniform_block(const Window<CT, WX, WY> &w, int w
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int i = q >> 1, j = q & 1;  // mirrored pixel (i + 1, j + 1)
-            float n = u.W00 * C[i][j];
+            float n = __fmul_rn(u.W00, C[i][j]);
             n = (sel[q] & 1) ? fmaf(u.W10, C[i][j + 1], n) : n;
             n = (sel[q] & 2) ? fmaf(u.W01, C[i + 1][j], n) : n;
             n = (sel[q] & 4) ? fmaf(u.W11, C[i + 1][j + 1], n) : n;
-            out[q][ch] = ok[q] ? storage_round<CT>(n * inv[q]) : 0.0f;
+            out[q][ch] = ok[q] ? storage_round<CT>(__fmul_rn(n, inv[q])) : 0.0f;
         }
     }
     // true pixel t = (ti, tj) <- mirrored pixel (MY ? 1 - ti : ti, MX ? 1 - tj : tj), by selects
@@ -743,15 +744,15 @@ __device__ __forceinline__ void gather_pixel(const uint32_t *kw, const Acc &a, c
     const bool a10 = ex && tap_agrees(a.d(i10), Dp);
     const bool a01 = ey && tap_agrees(a.d(i01), Dp);
     const bool a11 = ex && ey && tap_agrees(a.d(i11), Dp);
-    const float w00 = wx0 * wy0;
-    const float w10 = a10 ? wx1 * wy0 : 0.0f;
-    const float w01 = a01 ? wx0 * wy1 : 0.0f;
-    const float w11 = a11 ? wx1 * wy1 : 0.0f;
-    const float den = ((w00 + w10) + w01) + w11;
+    const float w00 = __fmul_rn(wx0, wy0);
+    const float w10 = a10 ? __fmul_rn(wx1, wy0) : 0.0f;
+    const float w01 = a01 ? __fmul_rn(wx0, wy1) : 0.0f;
+    const float w11 = a11 ? __fmul_rn(wx1, wy1) : 0.0f;
+    const float den = weight_sum(w00, w10, w01, w11);
     float v[3];
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
-        float n = w00 * a.c(ch, i00);
+        float n = __fmul_rn(w00, a.c(ch, i00));
         const float c10 = a.c(ch, i10), c01 = a.c(ch, i01), c11 = a.c(ch, i11);
         n = a10 ? fmaf(w10, c10, n) : n;
         n = a01 ? fmaf(w01, c01, n) : n;
@@ -759,8 +760,9 @@ __device__ __forceinline__ void gather_pixel(const uint32_t *kw, const Acc &a, c
         v[ch] = n;
     }
     const float inv = __frcp_rn(den);
-    c = make_float4(ok ? storage_round<CT>(v[0] * inv) : 0.0f, ok ? storage_round<CT>(v[1] * inv) : 0.0f,
-                    ok ? storage_round<CT>(v[2] * inv) : 0.0f, ok ? 1.0f : 0.0f);
+    c = make_float4(ok ? storage_round<CT>(__fmul_rn(v[0], inv)) : 0.0f,
+                    ok ? storage_round<CT>(__fmul_rn(v[1], inv)) : 0.0f,
+                    ok ? storage_round<CT>(__fmul_rn(v[2], inv)) : 0.0f, ok ? 1.0f : 0.0f);
 }
 
 template <typename CT, class Acc>
@@ -953,10 +955,11 @@ __device__ float4 smooth_node(const TileParams &p, int tile, int kk, float4 *l2)
     const float ry = residual(__uint_as_float(umy), k, p.L, oy, sy);
     const float wx1 = fabsf(rx), wy1 = fabsf(ry);
     const float wx0 = 1.0f - wx1, wy0 = 1.0f - wy1;
-    const float W00 = wx0 * wy0, W10 = wx1 * wy0, W01 = wx0 * wy1, W11 = wx1 * wy1;
+    const float W00 = __fmul_rn(wx0, wy0), W10 = __fmul_rn(wx1, wy0), W01 = __fmul_rn(wx0, wy1),
+                W11 = __fmul_rn(wx1, wy1);
     const bool EX = sx != 0, EY = sy != 0;
     const int j = (EX ? 1 : 0) | (EY ? 2 : 0) | (EX && EY ? 4 : 0);
-    const float inv = __frcp_rn(((W00 + ((j & 1) ? W10 : 0.0f)) + ((j & 2) ? W01 : 0.0f)) + ((j & 4) ? W11 : 0.0f));
+    const float inv = __frcp_rn(weight_sum(W00, (j & 1) ? W10 : 0.0f, (j & 2) ? W01 : 0.0f, (j & 4) ? W11 : 0.0f));
     const int X0 = (tile % p.n5x) * kFillTile, Y0 = (tile / p.n5x) * kFillTile;
     const size_t plane = (size_t)p.W * p.H;
     const CT *col = (const CT *)p.color;
@@ -970,11 +973,11 @@ __device__ float4 smooth_node(const TileParams &p, int tile, int kk, float4 *l2)
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
                 const CT *cp = col + ch * plane;
-                float n = W00 * to_f<CT>(cp[(size_t)cy * p.W + cx]);
+                float n = __fmul_rn(W00, to_f<CT>(cp[(size_t)cy * p.W + cx]));
                 if (EX) n = fmaf(W10, to_f<CT>(cp[(size_t)cy * p.W + tx]), n);
                 if (EY) n = fmaf(W01, to_f<CT>(cp[(size_t)ty * p.W + cx]), n);
                 if (EX && EY) n = fmaf(W11, to_f<CT>(cp[(size_t)ty * p.W + tx]), n);
-                out[r][ch] = to_storage<CT>(n * inv);
+                out[r][ch] = to_storage<CT>(__fmul_rn(n, inv));
             }
         }
         const float4 n2 = smooth_level2<CT>(out);
@@ -1133,11 +1136,11 @@ __device__ __forceinline__ void smooth_column_t(const CT *col, int wx0, int wy0,
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int ic = MY ? r + 1 : r, it = MY ? r : r + 1;  // centre row, tap row
-            float n = W00 * C[ic][0];
+            float n = __fmul_rn(W00, C[ic][0]);
             if (EX) n = fmaf(W10, C[ic][1], n);
             if (EY) n = fmaf(W01, C[it][0], n);
             if (EX && EY) n = fmaf(W11, C[it][1], n);
-            out[r][ch] = to_storage<CT>(n * inv);
+            out[r][ch] = to_storage<CT>(__fmul_rn(n, inv));
         }
     }
 }

@@ -153,6 +153,8 @@ cudaError_t launch_bounds_finalize(const FrameHeader *fh, float *frame_bounds, c
 cudaError_t launch_plan(const TileParams &p, exw_dtype cdt, cudaStream_t s);
 
 size_t recursive_workspace_bytes(int W, int H);
+size_t train_workspace_bytes(int W, int H, int nfrac);
+cudaError_t launch_train_frame(const exw_train_frame &f, int nfrac, double *loss, void *ws, cudaStream_t s);
 
 // Frame statistics (exw_stats.cu): FP64 reductions into a small fixed workspace.
 size_t stats_workspace_bytes();

@@ -386,15 +386,15 @@ __device__ void finish_fraction(TileSmem &s, const Acc &a, const Src &src, const
         const bool a10 = ex[j] && tap_agrees(a.d(i10[j]), Dp);
         const bool a01 = ey[j] && tap_agrees(a.d(i01[j]), Dp);
         const bool a11 = ex[j] && ey[j] && tap_agrees(a.d(i11[j]), Dp);
-        const float w00 = wx0[j] * wy0[j];
-        const float w10 = a10 ? wx1[j] * wy0[j] : 0.0f;
-        const float w01 = a01 ? wx0[j] * wy1[j] : 0.0f;
-        const float w11 = a11 ? wx1[j] * wy1[j] : 0.0f;
-        const float den = ((w00 + w10) + w01) + w11;
+        const float w00 = __fmul_rn(wx0[j], wy0[j]);
+        const float w10 = a10 ? __fmul_rn(wx1[j], wy0[j]) : 0.0f;
+        const float w01 = a01 ? __fmul_rn(wx0[j], wy1[j]) : 0.0f;
+        const float w11 = a11 ? __fmul_rn(wx1[j], wy1[j]) : 0.0f;
+        const float den = weight_sum(w00, w10, w01, w11);
         float v[3];
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
-            float n = w00 * a.c(ch, i00[j]);
+            float n = __fmul_rn(w00, a.c(ch, i00[j]));
             const float c10 = a.c(ch, i10[j]), c01 = a.c(ch, i01[j]), c11 = a.c(ch, i11[j]);
             n = a10 ? fmaf(w10, c10, n) : n;
             n = a01 ? fmaf(w01, c01, n) : n;
@@ -403,8 +403,9 @@ __device__ void finish_fraction(TileSmem &s, const Acc &a, const Src &src, const
         }
         const float inv = __frcp_rn(den);
         const bool okj = ok[j];
-        c[j] = make_float4(okj ? storage_round<CT>(v[0] * inv) : 0.0f, okj ? storage_round<CT>(v[1] * inv) : 0.0f,
-                           okj ? storage_round<CT>(v[2] * inv) : 0.0f, okj ? 1.0f : 0.0f);
+        c[j] = make_float4(okj ? storage_round<CT>(__fmul_rn(v[0], inv)) : 0.0f,
+                           okj ? storage_round<CT>(__fmul_rn(v[1], inv)) : 0.0f,
+                           okj ? storage_round<CT>(__fmul_rn(v[2], inv)) : 0.0f, okj ? 1.0f : 0.0f);
     }
     if (!FILL) {
 #pragma unroll
