@@ -303,6 +303,9 @@ typedef struct exw_tuner exw_tuner; /* opaque host-side autotuner state */
 
 EXW_API exw_tuner *exw_tuner_create(void);
 EXW_API void exw_tuner_destroy(exw_tuner *t);
+/* Make the tuner run one schedule for every batch instead of timing candidates: window shape 0 or 1 (see
+ * exw_extrapolate_batched), queue distance lag in [1, 4], pair 0 or 1.  EXW_ERR_INVALID_ARG for other values. */
+EXW_API exw_status exw_tuner_fix(exw_tuner *t, int shape, int lag, int pair);
 /* Text summary of the tuner's choices (NUL-terminated, truncated to len bytes).  Returns bytes needed. */
 EXW_API size_t exw_tuner_report(const exw_tuner *t, char *buf, size_t len);
 
@@ -313,8 +316,11 @@ EXW_API size_t exw_batched_workspace_bytes(const exw_stream_desc *d, int n, int 
  * possibly different sizes (each with its own colour type) in ONE persistent kernel launch: CTAs pull (stream, stage,
  * tile) work items from a queue in the workspace; a stage waits for the one before it in the same stream with a bounded
  * spin (EXW_ERR_TIMEOUT via exw_device_status if it runs out).  Capturable in a CUDA graph. d [n] is a HOST array. t
- * (nullable) picks the CTA count by timing candidates on the first call for a given set of sizes; NULL uses the SM
- * count x occupancy.  Results are bit-identical to exw_extrapolate on each stream. */
+ * (nullable) is the autotuner: on the first call for a given set of sizes (outside any stream capture) it times
+ * every schedule -- the shape of the shared-memory staging windows (FP32 56 x 48 or 64 x 42, FP16 64 x 56 or
+ * 56 x 64 pixels), the queue distance between the stages of a stream (1 or 2) and whether two smooth tiles of a
+ * stream share one slot -- and keeps the fastest for later calls; NULL runs the default schedule (the first shape,
+ * distance 1, sharing on).  Results are bit-identical to exw_extrapolate on each stream, whatever the schedule. */
 EXW_API exw_status exw_extrapolate_batched(const exw_stream_desc *d, int n, int nfrac, unsigned flags, void *ws,
                                    size_t ws_bytes, exw_tuner *t, exw_stream_t stream);
 

@@ -44,6 +44,7 @@ PROTOTYPES = {
     "exw_device_status": (I, [P, P]),
     "exw_tuner_create": (P, []),
     "exw_tuner_destroy": (None, [P]),
+    "exw_tuner_fix": (I, [P, I, I, I]),
     "exw_tuner_report": (SZ, [P, ctypes.c_char_p, SZ]),
     "exw_batched_workspace_bytes": (SZ, [P, I, I]),
     "exw_extrapolate_batched": (I, [P, I, I, U, P, SZ, P, P]),

@@ -368,6 +368,11 @@ def exw_tuner_destroy(tuner: int):
     lib().exw_tuner_destroy(tuner)
 
 
+def exw_tuner_fix(tuner: int, shape: int, lag: int = 1, pair: bool = True):
+    """Make ``tuner`` run one schedule (window shape 0 or 1, queue distance, smooth-tile sharing) for every batch."""
+    _check(lib().exw_tuner_fix(tuner, int(shape), int(lag), 1 if pair else 0))
+
+
 def exw_tuner_report(tuner: int) -> str:
     need = int(lib().exw_tuner_report(tuner, None, 0))
     buf = ctypes.create_string_buffer(need)

@@ -7,8 +7,10 @@
 // stream d - 2 lag and the fix-up items of stream d - 3 lag.  A stage's items thus come after every item of the
 // previous stage of the same stream, so the producer's wait for them only spins when they have not finished yet.
 //
-// The autotuner times the schedule choices (TMA windows or global-memory reads, the queue lag) on the caller's
-// streams the first time it sees a set of sizes, outside any stream capture, and keeps the fastest.
+// The autotuner times the schedule choices -- the shape of the staging windows (two per colour type), the queue
+// lag and whether two smooth tiles share a slot -- on the caller's streams the first time it sees a set of sizes,
+// outside any stream capture, and keeps the fastest.  Global-memory reads instead of TMA windows (EXW_FLAG_NO_TMA)
+// stay a flag: they always lose, so they are not timed.
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -22,7 +24,7 @@
 
 namespace exw {
 
-cudaError_t launch_engine(const EngineParams &ep, bool fill, int grid, cudaStream_t s);
+cudaError_t launch_engine(const EngineParams &ep, bool fill, int shape, int grid, cudaStream_t s);
 
 constexpr size_t kEngineHeader = 256;  // status word
 
@@ -84,8 +86,10 @@ static bool encode(PFN_cuTensorMapEncodeTiled_v12000 fn, CUtensorMap *m, CUtenso
 }
 
 struct Schedule {
-    int tma;  // 1: TMA windows where a stream allows them; 0: global-memory reads everywhere
-    int lag;  // queue distance between consecutive stages of one stream
+    int tma;    // 1: TMA windows where a stream allows them; 0: global-memory reads everywhere
+    int lag;    // queue distance between consecutive stages of one stream
+    int shape;  // staging window shape (WinShape)
+    int pair;   // two smooth tiles of a stream that follow each other share one slot
 };
 
 // Kernel parameters for streams [first, first + n) of specs, in slots 0 .. n - 1.  The bounds and plans of
@@ -97,6 +101,7 @@ static bool build_params(EngineParams *ep, const EngineSpec *specs, int first, i
     FrameHeader *headers = (FrameHeader *)(ws + bl.headers) + first;
     ep->n = n;
     ep->inject = inject ? 1 : 0;
+    ep->pair_smooth = sc.pair;
     ep->ahead = 1ull;
     ep->status = (uint32_t *)ws;
     ep->queue = &headers[0].queue;
@@ -140,7 +145,7 @@ static bool build_params(EngineParams *ep, const EngineSpec *specs, int first, i
         st.tma = sc.tma && fn != nullptr && (f.W % a) == 0 && ((uintptr_t)f.color & 15u) == 0 &&
                  ((uintptr_t)f.depth & 15u) == 0 && ((uintptr_t)f.mv & 15u) == 0;
         if (st.tma) {
-            const int bx = f.cdt == EXW_F16 ? kWinXF16 : kWinXF32, by = f.cdt == EXW_F16 ? kWinYF16 : kWinYF32;
+            const int bx = win_x(sc.shape, f.cdt), by = win_y(sc.shape, f.cdt);
             const bool ok =
                 encode(fn, &ep->maps[i][0],
                        f.cdt == EXW_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, f.color,
@@ -201,9 +206,9 @@ static cudaError_t run_all(EngineParams *ep, const EngineSpec *specs, int n, int
             const TileParams &p = ep->st[i].p;
             e = launch_bounds(p.depth, p.mv, p.W, p.H, const_cast<float4 *>(p.tile_bounds),
                               const_cast<float2 *>(p.tile_depth), const_cast<float4 *>(p.region_bounds), p.fh, s);
-            if (e == cudaSuccess) e = launch_plan(p, (exw_dtype)ep->st[i].cdt, s);
+            if (e == cudaSuccess) e = launch_plan(p, (exw_dtype)ep->st[i].cdt, sc.shape, s);
         }
-        if (e == cudaSuccess) e = launch_engine(*ep, fill, tiles < sms ? tiles : sms, s);
+        if (e == cudaSuccess) e = launch_engine(*ep, fill, sc.shape, tiles < sms ? tiles : sms, s);
     }
     return e;
 }
@@ -214,6 +219,8 @@ using namespace exw;
 
 struct exw_tuner {
     std::mutex mu;
+    bool fixed = false;  // exw_tuner_fix: every batch runs this schedule, nothing is timed
+    Schedule fix{1, 1, 0, 1};
     struct Entry {
         Schedule best;
         std::vector<std::pair<Schedule, float>> trials;
@@ -238,14 +245,16 @@ exw_status engine_run(const EngineSpec *specs, int n, int nfrac, unsigned flags,
     const bool fill = (flags & EXW_FLAG_NO_FILL) == 0;
     const char *fault = std::getenv("EXW_FAULT");
     const bool inject = fault != nullptr && std::strcmp(fault, "timeout") == 0;
-    Schedule sc{(flags & EXW_FLAG_NO_TMA) ? 0 : 1, 1};
+    Schedule sc{(flags & EXW_FLAG_NO_TMA) ? 0 : 1, 1, 0, 1};
     static thread_local EngineParams ep;  // 32 KB: kept off the stack
     char *wsb = (char *)ws;
     if (t != nullptr && !inject) {
         const std::string key = batch_key(specs, n, nfrac, flags);
         std::unique_lock<std::mutex> g(t->mu);
         auto it = t->table.find(key);
-        if (it != t->table.end()) {
+        if (t->fixed) {
+            sc = Schedule{sc.tma, t->fix.lag, t->fix.shape, t->fix.pair};
+        } else if (it != t->table.end()) {
             sc = it->second.best;
         } else {
             cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -260,29 +269,31 @@ exw_status engine_run(const EngineSpec *specs, int n, int nfrac, unsigned flags,
                     return EXW_ERR_CUDA;
                 }
                 exw_status st = EXW_OK;
-                for (int tma = (flags & EXW_FLAG_NO_TMA) ? 0 : 1; tma >= 0 && st == EXW_OK; --tma) {
+                for (int shape = 0; shape < kWinShapes && st == EXW_OK; ++shape) {
                     for (int lag = 1; lag <= 2 && st == EXW_OK; ++lag) {
-                        const Schedule c{tma, lag};
-                        float ms = 1e30f;
-                        for (int r = 0; r < 3; ++r) {
-                            cudaEventRecord(e0, s);
-                            if (run_all(&ep, specs, n, nfrac, fill, wsb, bl, c, false, s) != cudaSuccess) {
-                                st = EXW_ERR_CUDA;
-                                break;
+                        for (int pair = 1; pair >= 0 && st == EXW_OK; --pair) {
+                            const Schedule c{sc.tma, lag, shape, pair};
+                            float ms = 1e30f;
+                            for (int r = 0; r < 3; ++r) {
+                                cudaEventRecord(e0, s);
+                                if (run_all(&ep, specs, n, nfrac, fill, wsb, bl, c, false, s) != cudaSuccess) {
+                                    st = EXW_ERR_CUDA;
+                                    break;
+                                }
+                                cudaEventRecord(e1, s);
+                                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                                    st = EXW_ERR_CUDA;
+                                    break;
+                                }
+                                float m = 0.f;
+                                cudaEventElapsedTime(&m, e0, e1);
+                                if (r > 0 && m < ms) ms = m;
                             }
-                            cudaEventRecord(e1, s);
-                            if (cudaEventSynchronize(e1) != cudaSuccess) {
-                                st = EXW_ERR_CUDA;
-                                break;
+                            ent.trials.push_back({c, ms});
+                            if (ms < best) {
+                                best = ms;
+                                ent.best = c;
                             }
-                            float m = 0.f;
-                            cudaEventElapsedTime(&m, e0, e1);
-                            if (r > 0 && m < ms) ms = m;
-                        }
-                        ent.trials.push_back({c, ms});
-                        if (ms < best) {
-                            best = ms;
-                            ent.best = c;
                         }
                     }
                 }
@@ -299,9 +310,28 @@ exw_status engine_run(const EngineSpec *specs, int n, int nfrac, unsigned flags,
 
 }  // namespace exw
 
+namespace exw {
+// "FP32 56x48 / FP16 64x56": the staging window of each colour type for a shape.
+static std::string shape_name(int shape) {
+    char b[64];
+    std::snprintf(b, sizeof b, "FP32 %dx%d / FP16 %dx%d", win_x(shape, EXW_F32), win_y(shape, EXW_F32),
+                  win_x(shape, EXW_F16), win_y(shape, EXW_F16));
+    return b;
+}
+}  // namespace exw
+
 extern "C" {
 
 exw_tuner *exw_tuner_create(void) { return new exw_tuner(); }
+
+exw_status exw_tuner_fix(exw_tuner *t, int shape, int lag, int pair) {
+    if (t == nullptr || shape < 0 || shape >= kWinShapes || lag < 1 || lag > 4 || pair < 0 || pair > 1)
+        return EXW_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(t->mu);
+    t->fixed = true;
+    t->fix = Schedule{1, lag, shape, pair};
+    return EXW_OK;
+}
 
 void exw_tuner_destroy(exw_tuner *t) { delete t; }
 
@@ -311,13 +341,14 @@ size_t exw_tuner_report(const exw_tuner *t, char *buf, size_t len) {
         exw_tuner *tt = const_cast<exw_tuner *>(t);
         std::lock_guard<std::mutex> g(tt->mu);
         for (auto &kv : tt->table) {
-            r += "streams " + kv.first.substr(0, kv.first.find(':')) + ": best tma=" +
-                 std::to_string(kv.second.best.tma) + " lag=" + std::to_string(kv.second.best.lag) + " (";
+            const Schedule &bs = kv.second.best;
+            r += "streams " + kv.first.substr(0, kv.first.find(':')) + ": best window " + shape_name(bs.shape) +
+                 " lag=" + std::to_string(bs.lag) + " pair=" + std::to_string(bs.pair) + " (";
             for (size_t i = 0; i < kv.second.trials.size(); ++i) {
-                char tmp[96];
-                std::snprintf(tmp, sizeof tmp, "%stma %d lag %d: %.3f ms", i ? ", " : "",
-                              kv.second.trials[i].first.tma, kv.second.trials[i].first.lag,
-                              kv.second.trials[i].second);
+                const Schedule &c = kv.second.trials[i].first;
+                char tmp[128];
+                std::snprintf(tmp, sizeof tmp, "%swindow %s lag %d pair %d: %.3f ms", i ? ", " : "",
+                              shape_name(c.shape).c_str(), c.lag, c.pair, kv.second.trials[i].second);
                 r += tmp;
             }
             r += ")\n";

@@ -329,13 +329,10 @@ __global__ void __launch_bounds__(256) splat_multi_kernel(const float *__restric
 template <typename CT, bool FUSED>
 static cudaError_t launch_bwd_tiles(const BwdArgs &a, cudaStream_t s) {
     constexpr size_t kSmem = sizeof(BwdSmem<CT>);
-    static bool configured = false;  // (the attribute is per function; setting it twice is harmless)
-    if (!configured) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(bwd_tile_kernel<CT, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    // set on every launch: the attribute belongs to the current device's context
+    const cudaError_t e =
+        cudaFuncSetAttribute(bwd_tile_kernel<CT, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    if (e != cudaSuccess) return e;
     const dim3 g((unsigned)ceil_div(a.W, kFillTile), (unsigned)ceil_div(a.H, kFillTile), 1);
     bwd_tile_kernel<CT, FUSED><<<g, kBwdThreads, kSmem, s>>>(a);
     return cudaSuccess;

@@ -4,7 +4,7 @@
 
 namespace exw {
 
-template <bool FILL>
+template <bool FILL, int SHAPE>
 __global__ void __launch_bounds__(kEngineThreads, 1) engine_kernel(const __grid_constant__ EngineParams ep) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     EngineSmem &s = *reinterpret_cast<EngineSmem *>(smem_raw);
@@ -17,27 +17,29 @@ __global__ void __launch_bounds__(kEngineThreads, 1) engine_kernel(const __grid_
         s.abort = 0;
     }
     __syncthreads();
-    if (threadIdx.x >= kConsumerThreads) engine_producer(s, ep);
-    else engine_consumer<FILL>(s, ep.status);
+    if (threadIdx.x >= kConsumerThreads) engine_producer<SHAPE>(s, ep);
+    else engine_consumer<FILL, SHAPE>(s, ep.status);
 }
 
-cudaError_t launch_engine(const EngineParams &ep, bool fill, int grid, cudaStream_t s) {
+template <bool FILL, int SHAPE>
+static cudaError_t launch_one(const EngineParams &ep, int grid, cudaStream_t s) {
     constexpr size_t kSmem = sizeof(EngineSmem);
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e =
-            cudaFuncSetAttribute(engine_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(engine_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    // set on every launch: the attribute belongs to the current device's context
+    const cudaError_t e =
+        cudaFuncSetAttribute(engine_kernel<FILL, SHAPE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    if (e != cudaSuccess) return e;
+    engine_kernel<FILL, SHAPE><<<grid, kEngineThreads, kSmem, s>>>(ep);
+    return cudaSuccess;
+}
+
+cudaError_t launch_engine(const EngineParams &ep, bool fill, int shape, int grid, cudaStream_t s) {
     timing_begin("exw_engine", s);
-    if (fill) engine_kernel<true><<<grid, kEngineThreads, kSmem, s>>>(ep);
-    else engine_kernel<false><<<grid, kEngineThreads, kSmem, s>>>(ep);
+    cudaError_t e;
+    if (shape == 0) e = fill ? launch_one<true, 0>(ep, grid, s) : launch_one<false, 0>(ep, grid, s);
+    else e = fill ? launch_one<true, 1>(ep, grid, s) : launch_one<false, 1>(ep, grid, s);
     count_launch();
     timing_end("exw_engine", s);
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace exw

@@ -56,6 +56,7 @@ struct EngineSeg {
 };
 struct EngineParams {
     int n, nseg, total, inject;
+    int pair_smooth;  // two smooth tiles of a stream that follow each other share one slot
     uint64_t ahead;  // streams whose bounds and plans were computed before the launch (bit s = stream s)
     uint32_t *queue, *status;
     EngineStream st[kMaxStreams];
@@ -95,9 +96,11 @@ struct alignas(16) TileSlot {
 
 constexpr int kWindowBytes = 64512;  // both window shapes (56 x 48 FP32, 64 x 56 FP16) hold 64,512 bytes
 static_assert(64 * 16 * kConsumerWarps <= kWindowBytes, "the coarse pass's per-warp scratch fits one buffer");
-static_assert(sizeof(Window<float, kWinXF32, kWinYF32>) == kWindowBytes &&
-                  sizeof(Window<__half, kWinXF16, kWinYF16>) == kWindowBytes,
-              "one buffer size for both colour types");
+static_assert(sizeof(Window<float, WinShape<0>::xf32, WinShape<0>::yf32>) == kWindowBytes &&
+                  sizeof(Window<__half, WinShape<0>::xf16, WinShape<0>::yf16>) == kWindowBytes &&
+                  sizeof(Window<float, WinShape<1>::xf32, WinShape<1>::yf32>) == kWindowBytes &&
+                  sizeof(Window<__half, WinShape<1>::xf16, WinShape<1>::yf16>) == kWindowBytes,
+              "one buffer size for every shape and colour type");
 
 struct EngineSmem {
     alignas(128) unsigned char win[2][kWindowBytes];  // TMA destinations, double-buffered
@@ -216,7 +219,9 @@ __device__ __forceinline__ QueueItem decode(const EngineParams &ep, int item, in
     return q;
 }
 
+template <int SHAPE>
 __device__ inline void engine_producer(EngineSmem &s, const EngineParams &ep) {
+    using WS = WinShape<SHAPE>;
     constexpr int kWords = (int)(sizeof(TilePlan) / 4), kParamWords = (int)(sizeof(TileParams) / 4);
     static_assert(sizeof(TileParams) % 4 == 0 && kParamWords <= 64, "two words per lane");
     const int lane = threadIdx.x & 31;
@@ -323,7 +328,7 @@ __device__ inline void engine_producer(EngineSmem &s, const EngineParams &ep) {
                 if (lane == 0) sl.N = uniform_sources(p, umx, umy, X0 - 1, Y0 - 1);
             }
             // two smooth tiles in a row (the second one's plan already read): one slot, one pass of the pipeline
-            pair = mode == 5 && nhave && nxt.stream == stream && nxt.stage == 2 &&
+            pair = ep.pair_smooth && mode == 5 && nhave && nxt.stream == stream && nxt.stage == 2 &&
                    __shfl_sync(0xFFFFFFFFu, nword, 0) == 5;
             if (pair) {
                 const int X02 = (nxt.local % p.n5x) * kFillTile, Y02 = (nxt.local / p.n5x) * kFillTile;
@@ -358,7 +363,7 @@ __device__ inline void engine_producer(EngineSmem &s, const EngineParams &ep) {
             const CUtensorMap *m = ep.maps[stream];
             unsigned char *wb = s.win[b];
             // a window holds npx pixels: depth (4 B), motion (8 B), colour (3 c B) planes in this order
-            const int npx = st.cdt == EXW_F16 ? kWinXF16 * kWinYF16 : kWinXF32 * kWinYF32;
+            const int npx = st.cdt == EXW_F16 ? WS::xf16 * WS::yf16 : WS::xf32 * WS::yf32;
             const uint32_t cbytes = (uint32_t)npx * 3u * (st.cdt == EXW_F16 ? 2u : 4u);
             if (kind == kSlotTile && mode == 5) {  // smooth: only the colour is read, at the buffer's start
                 fence_proxy_async_smem();
@@ -1269,8 +1274,9 @@ struct HalfGroupBarrier {  // the 4 warps of half group h: named barrier 5 + h
     __device__ __forceinline__ void operator()() const { bar_sync(id, kGroupThreads / 2); }
 };
 
-template <bool FILL>
+template <bool FILL, int SHAPE>
 __device__ void engine_consumer(EngineSmem &s, uint32_t *status) {
+    using WS = WinShape<SHAPE>;
     const int tid = threadIdx.x;  // 0 .. 767
     const int g = tid >> 8, tg = tid & (kGroupThreads - 1);
     const int lane = tid & 31, w = tid >> 5;
@@ -1297,10 +1303,10 @@ __device__ void engine_consumer(EngineSmem &s, uint32_t *status) {
         const TileParams &p = sl.p;
         if (ok && mode == 0) {
             if (sl.cdt == EXW_F16)
-                build_source_words(window<__half, kWinXF16, kWinYF16>(s, b), sl.plan.wx0, sl.plan.wy0, sl.N,
+                build_source_words(window<__half, WS::xf16, WS::yf16>(s, b), sl.plan.wx0, sl.plan.wy0, sl.N,
                                    __uint_as_float(sl.plan.umx), __uint_as_float(sl.plan.umy), tid);
             else
-                build_source_words(window<float, kWinXF32, kWinYF32>(s, b), sl.plan.wx0, sl.plan.wy0, sl.N,
+                build_source_words(window<float, WS::xf32, WS::yf32>(s, b), sl.plan.wx0, sl.plan.wy0, sl.N,
                                    __uint_as_float(sl.plan.umx), __uint_as_float(sl.plan.umy), tid);
         }
         if (ok && mode >= 1 && mode <= 3 && g < p.nfrac)
@@ -1333,8 +1339,8 @@ __device__ void engine_consumer(EngineSmem &s, uint32_t *status) {
         } else if (kind == kSlotPlans) {
             const int tile = sl.index * kPlansPerItem + w;
             if (tile < p.n5x * p.n5y) {
-                if (sl.cdt == EXW_F16) plan_tile<__half, kWinXF16, kWinYF16>(p, tile);
-                else plan_tile<float, kWinXF32, kWinYF32>(p, tile);
+                if (sl.cdt == EXW_F16) plan_tile<__half, WS::xf16, WS::yf16>(p, tile);
+                else plan_tile<float, WS::xf32, WS::yf32>(p, tile);
                 if (lane == 0) {
                     __threadfence();
                     atomicAdd(&p.fh->pdone, 1u);
@@ -1353,11 +1359,11 @@ __device__ void engine_consumer(EngineSmem &s, uint32_t *status) {
             if (sl.cdt == EXW_F16) fixup_slice<__half>(p, (uint32_t)sl.index, kFixupItems, tid, kConsumerThreads);
             else fixup_slice<float>(p, (uint32_t)sl.index, kFixupItems, tid, kConsumerThreads);
         } else {  // target tile
-            if (sl.cdt == EXW_F16) tile_splat<__half, kWinXF16, kWinYF16>(s, sl, b, tid);
-            else tile_splat<float, kWinXF32, kWinYF32>(s, sl, b, tid);
+            if (sl.cdt == EXW_F16) tile_splat<__half, WS::xf16, WS::yf16>(s, sl, b, tid);
+            else tile_splat<float, WS::xf32, WS::yf32>(s, sl, b, tid);
             if (g < p.nfrac) {
-                if (sl.cdt == EXW_F16) tile_group<__half, kWinXF16, kWinYF16, FILL>(s, sl, b, g, (int)(i & 1u));
-                else tile_group<float, kWinXF32, kWinYF32, FILL>(s, sl, b, g, (int)(i & 1u));
+                if (sl.cdt == EXW_F16) tile_group<__half, WS::xf16, WS::yf16, FILL>(s, sl, b, g, (int)(i & 1u));
+                else tile_group<float, WS::xf32, WS::yf32, FILL>(s, sl, b, g, (int)(i & 1u));
                 if (FILL && tg == 0) {
                     pend.add(p.fh);
                     if (mode == 5 && sl.pair) pend.add(p.fh);

@@ -81,12 +81,19 @@ __global__ void __launch_bounds__(kThreads) fixup_kernel(TileParams p) {
 // ------------------------------------------------------------------------------------------------------------
 static dim3 tile_grid(const TileParams &p) { return dim3((unsigned)p.n5x, (unsigned)p.n5y, 1); }
 
-cudaError_t launch_plan(const TileParams &p, exw_dtype cdt, cudaStream_t s) {
+cudaError_t launch_plan(const TileParams &p, exw_dtype cdt, int shape, cudaStream_t s) {
     const int ntiles = p.n5x * p.n5y;
     const unsigned g = (unsigned)((ntiles + kWarps - 1) / kWarps);
     timing_begin("exw_plan", s);
-    if (cdt == EXW_F32) plan_kernel<float, kWinXF32, kWinYF32><<<g, kThreads, 0, s>>>(p);
-    else plan_kernel<__half, kWinXF16, kWinYF16><<<g, kThreads, 0, s>>>(p);
+    using S0 = WinShape<0>;
+    using S1 = WinShape<1>;
+    if (shape == 0) {
+        if (cdt == EXW_F32) plan_kernel<float, S0::xf32, S0::yf32><<<g, kThreads, 0, s>>>(p);
+        else plan_kernel<__half, S0::xf16, S0::yf16><<<g, kThreads, 0, s>>>(p);
+    } else {
+        if (cdt == EXW_F32) plan_kernel<float, S1::xf32, S1::yf32><<<g, kThreads, 0, s>>>(p);
+        else plan_kernel<__half, S1::xf16, S1::yf16><<<g, kThreads, 0, s>>>(p);
+    }
     count_launch();
     timing_end("exw_plan", s);
     return cudaGetLastError();

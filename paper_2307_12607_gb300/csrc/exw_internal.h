@@ -135,9 +135,25 @@ struct alignas(16) TileParams {
     uint32_t *status;           // workspace status word (EXW_OK, or EXW_ERR_TIMEOUT from a bounded wait)
 };
 
-// Shared-memory source windows of the persistent TMA kernel (x extent, y extent); both are 64,512 bytes.
-constexpr int kWinXF32 = 56, kWinYF32 = 48;
-constexpr int kWinXF16 = 64, kWinYF16 = 56;
+// Shared-memory source windows of the persistent TMA kernel (x extent, y extent): two shapes per colour type, all
+// 64,512 bytes (depth, motion and colour planes); the autotuner picks one per batch.  x is a multiple of 16 bytes
+// of every plane (TMA) and at most 64 (a half warp covers a row when the depth plane is rewritten).
+constexpr int kWinShapes = 2;
+template <int SHAPE> struct WinShape;
+template <> struct WinShape<0> {  // the default: wider for FP16
+    static constexpr int xf32 = 56, yf32 = 48, xf16 = 64, yf16 = 56;
+};
+template <> struct WinShape<1> {  // wide FP32, tall FP16
+    static constexpr int xf32 = 64, yf32 = 42, xf16 = 56, yf16 = 64;
+};
+inline int win_x(int shape, exw_dtype cdt) {
+    return shape == 0 ? (cdt == EXW_F16 ? WinShape<0>::xf16 : WinShape<0>::xf32)
+                      : (cdt == EXW_F16 ? WinShape<1>::xf16 : WinShape<1>::xf32);
+}
+inline int win_y(int shape, exw_dtype cdt) {
+    return shape == 0 ? (cdt == EXW_F16 ? WinShape<0>::yf16 : WinShape<0>::yf32)
+                      : (cdt == EXW_F16 ? WinShape<1>::yf16 : WinShape<1>::yf32);
+}
 
 // Launchers (exw_fwd.cu, exw_aux.cu, exw_bwd.cu).  Each returns the launch error.
 cudaError_t launch_clear_keys(uint64_t *keys, size_t n, cudaStream_t s);
@@ -150,7 +166,7 @@ cudaError_t launch_bounds(const float *depth, const float *mv, int W, int H, flo
                           float4 *region_bounds, FrameHeader *fh, cudaStream_t s);
 cudaError_t launch_bounds_finalize(const FrameHeader *fh, float *frame_bounds, cudaStream_t s);
 
-cudaError_t launch_plan(const TileParams &p, exw_dtype cdt, cudaStream_t s);
+cudaError_t launch_plan(const TileParams &p, exw_dtype cdt, int shape, cudaStream_t s);
 
 size_t recursive_workspace_bytes(int W, int H);
 size_t train_workspace_bytes(int W, int H, int nfrac);

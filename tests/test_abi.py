@@ -237,6 +237,11 @@ def test_tuner_lifecycle_on_host(lib):
     t = lib.exw_tuner_create()
     assert t
     try:
+        assert lib.exw_tuner_fix(t, 2, 1, 1) == 1          # only window shapes 0 and 1
+        assert lib.exw_tuner_fix(t, 0, 0, 1) == 1          # queue distance >= 1
+        assert lib.exw_tuner_fix(t, 1, 2, 2) == 1          # pair is 0 or 1
+        assert lib.exw_tuner_fix(None, 0, 1, 1) == 1
+        assert lib.exw_tuner_fix(t, 1, 2, 0) == 0
         buf = ctypes.create_string_buffer(64)
         assert lib.exw_tuner_report(t, buf, 64) == 1 and buf.value == b""       # nothing tuned yet
         assert lib.exw_tuner_report(None, None, 0) == 1

@@ -82,6 +82,25 @@ def test_batched_matches_single_stream(b, fill, tma):
         assert same(o, o1)
 
 
+@pytest.mark.parametrize("shape", [0, 1])
+@pytest.mark.parametrize("lag,pair", [(1, True), (2, False), (3, True)])
+def test_every_schedule_the_tuner_can_choose_matches_oracle(b, shape, lag, pair):
+    # each window shape, queue distance and smooth-tile sharing, forced through exw_tuner_fix: every stream against
+    # the oracle and bit-identical to the single-stream launch (which runs the default schedule)
+    streams = make_streams(seed=6)
+    t = b.exw_tuner_create()
+    try:
+        b.exw_tuner_fix(t, shape, lag, pair)
+        for fill in (True, False):
+            outs = b.exw_extrapolate_batched(streams, nfrac=3, fill=fill, tuner=t)
+            for i, (s, o) in enumerate(zip(streams, outs)):
+                assert_matches_oracle(s, o, 3, fill, f"shape {shape} lag {lag} pair {pair} stream {i}")
+                o1, k1 = b.exw_extrapolate(*s, nfrac=3, fill=fill)
+                assert torch.equal(o[1], k1) and same(o[0], o1)
+    finally:
+        b.exw_tuner_destroy(t)
+
+
 def test_batched_with_tuner_and_fewer_fractions(b):
     streams = make_streams(seed=1)
     t = b.exw_tuner_create()
@@ -95,6 +114,8 @@ def test_batched_with_tuner_and_fewer_fractions(b):
                 assert_matches_oracle(streams[i], outs[i], nfrac, True, f"tuned, nfrac {nfrac}, stream {i}")
         rep = b.exw_tuner_report(t)
         assert rep.count("best") == 2 and "lag" in rep
+        # both window shapes were timed (each trial line names its window)
+        assert "FP32 56x48 / FP16 64x56" in rep and "FP32 64x42 / FP16 56x64" in rep
     finally:
         b.exw_tuner_destroy(t)
 
