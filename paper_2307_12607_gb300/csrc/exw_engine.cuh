@@ -102,13 +102,22 @@ static_assert(sizeof(Window<float, WinShape<0>::xf32, WinShape<0>::yf32>) == kWi
                   sizeof(Window<__half, WinShape<1>::xf16, WinShape<1>::yf16>) == kWindowBytes,
               "one buffer size for every shape and colour type");
 
+// A candidate 8 x 8 source tile of a splat: the fractions whose landing rectangle meets R and, for a clean tile
+// (one exact motion, every pixel can land), its whole-pixel offsets per fraction.
+struct alignas(16) SplatTile {
+    uint16_t bx, by;
+    uint8_t fm, clean;
+    int8_t ox[kMaxFrac], oy[kMaxFrac];
+    int8_t pad[2];
+};
+static_assert(sizeof(SplatTile) == 16, "one load per descriptor");
 struct EngineSmem {
     alignas(128) unsigned char win[2][kWindowBytes];  // TMA destinations, double-buffered
     uint64_t key[kMaxFrac][kRegionN];                // region keys per fraction (modes 1-3)
     float4 l2[kMaxFrac][2][64];                      // pyramid level 2 (8 x 8 nodes) per group, by tile parity
     float4 bpart[kMaxFrac][64];                      // per group: partial bounds of a region
     TileSlot slot[2];                                // the item in each buffer
-    uint32_t cand[kConsumerThreads];                 // candidate 8 x 8 source tiles of the global-memory splat
+    SplatTile cand[kConsumerThreads];                // candidate 8 x 8 source tiles of a splat
     uint32_t ncand;
     int abort;                                       // a bounded wait ran out: every warp leaves
     uint64_t full[2], empty[2];
@@ -586,16 +595,7 @@ __device__ __forceinline__ Rect plan_union(const TilePlan &pl, int nfrac) {
     return U;
 }
 
-// A candidate 8 x 8 source tile of a splat: the fractions whose landing rectangle meets R and, for a clean tile
-// (one exact motion, every pixel can land), its whole-pixel offsets per fraction.
-struct alignas(16) SplatTile {
-    uint16_t bx, by;
-    uint8_t fm, clean;
-    int8_t ox[kMaxFrac], oy[kMaxFrac];
-    int8_t pad[2];
-};
-static_assert(sizeof(SplatTile) == 16, "one load per descriptor");
-constexpr int kMaxSplatTiles = (int)(sizeof(uint32_t) * kConsumerThreads / sizeof(SplatTile));
+constexpr int kMaxSplatTiles = kConsumerThreads;
 
 // Describe the 8 x 8 source tiles overlapping rectangle U (all consumer threads, no barrier).  Returns the count.
 __device__ __forceinline__ int describe_tiles(SplatTile *out, const TileParams &p, const FrameDims &d, Rect U,
@@ -635,7 +635,7 @@ __device__ __forceinline__ int describe_tiles(SplatTile *out, const TileParams &
 template <typename CT, int WX, int WY>
 __device__ __forceinline__ void engine_splat_window(EngineSmem &s, const TileParams &p, const FrameDims &d,
                                                     const WinAcc<CT, WX, WY> &a, Rect U, int RX0, int RY0, int tid) {
-    SplatTile *tiles = reinterpret_cast<SplatTile *>(s.cand);
+    SplatTile *tiles = s.cand;
     const int nt = describe_tiles(tiles, p, d, U, RX0, RY0, tid);
     bar_sync(kBarConsumers, kConsumerThreads);
     // half a source tile per warp and round (its descriptor is one broadcast load), all warps busy
@@ -666,7 +666,9 @@ __device__ __forceinline__ void engine_splat_window(EngineSmem &s, const TilePar
     }
 }
 
-// Splat from global memory: the 8 x 8 source tiles whose bounds reach R, 64 threads per tile (all consumers).
+// Splat from global memory: the 8 x 8 source tiles whose bounds reach R, 64 threads per tile (all consumers).  A
+// clean candidate (one exact motion, every pixel can land) splats with its precomputed offsets and reads only the
+// depth of its pixels.
 __device__ inline void engine_splat_global(EngineSmem &s, const TileParams &p, const FrameDims &d, int RX0, int RY0,
                                            int tid) {
     int bx0, bx1, by0, by1;
@@ -681,18 +683,27 @@ __device__ inline void engine_splat_global(EngineSmem &s, const TileParams &p, c
         if (idx < total) {
             const int by = by0 + idx / nbxr, bx = bx0 + idx % nbxr;
             const float4 b = __ldcg(p.tile_bounds + (size_t)by * p.nbx + bx);
+            const float2 dr = __ldcg(p.tile_depth + (size_t)by * p.nbx + bx);  // issued with the bounds
             if (b.x <= b.y) {
+                SplatTile st{};
                 uint32_t fm = 0;
+                bool small = true;  // every offset fits an int8 (else a clean tile still splats per pixel)
                 for (int kk = 0; kk < p.nfrac; ++kk) {
                     int ox0, ox1, oy0, oy1;
                     tile_offsets(b, p.k0 + kk, p.L, ox0, ox1, oy0, oy1);
                     const int tx0 = 8 * bx + ox0, tx1 = 8 * bx + 7 + ox1;
                     const int ty0 = 8 * by + oy0, ty1 = 8 * by + 7 + oy1;
                     if (tx1 >= RX0 && tx0 < RX0 + kRegion && ty1 >= RY0 && ty0 < RY0 + kRegion) fm |= 1u << kk;
+                    small = small && ox0 >= -128 && ox0 <= 127 && oy0 >= -128 && oy0 <= 127;
+                    st.ox[kk] = (int8_t)max(-128, min(127, ox0));
+                    st.oy[kk] = (int8_t)max(-128, min(127, oy0));
                 }
                 if (fm) {
-                    const uint32_t slot = atomicAdd(&s.ncand, 1u);
-                    s.cand[slot] = (uint32_t)bx | ((uint32_t)by << 12) | (fm << 24);
+                    st.bx = (uint16_t)bx;
+                    st.by = (uint16_t)by;
+                    st.fm = (uint8_t)fm;
+                    st.clean = b.x == b.y && b.z == b.w && dr.x > 0.0f && small ? 1 : 0;
+                    s.cand[atomicAdd(&s.ncand, 1u)] = st;
                 }
             }
         }
@@ -701,14 +712,26 @@ __device__ inline void engine_splat_global(EngineSmem &s, const TileParams &p, c
         for (int c0 = 0; c0 < nc; c0 += kConsumerThreads / 64) {
             const int ci = c0 + (tid >> 6);
             if (ci < nc) {
-                const uint32_t e = s.cand[ci];
-                const int bx = (int)(e & 0xFFFu), by = (int)((e >> 12) & 0xFFFu);
-                const int x = 8 * bx + (tid & 7), y = 8 * by + ((tid >> 3) & 7);
+                const SplatTile st = s.cand[ci];
+                const int x = 8 * st.bx + (tid & 7), y = 8 * st.by + ((tid >> 3) & 7);
                 if (x < p.W && y < p.H) {
                     const size_t i = (size_t)y * p.W + x;
-                    engine_splat_pixel(s.key, d, x, y, __float_as_uint(__ldg(p.depth + i)),
-                                       __float_as_uint(__ldg(p.mv + i)), __float_as_uint(__ldg(p.mv + plane + i)),
-                                       e >> 24, RX0, RY0);
+                    const uint32_t db = __float_as_uint(__ldg(p.depth + i));
+                    if (st.clean) {
+                        const uint64_t kv = pack_key_local(db, x, y);
+#pragma unroll
+                        for (int kk = 0; kk < kMaxFrac; ++kk) {
+                            if (!(st.fm & (1u << kk))) continue;
+                            const int gx = x + st.ox[kk], gy = y + st.oy[kk];
+                            if ((unsigned)gx >= (unsigned)d.W || (unsigned)gy >= (unsigned)d.H) continue;
+                            const int rx = gx - RX0, ry = gy - RY0;
+                            if ((unsigned)rx < (unsigned)kRegion && (unsigned)ry < (unsigned)kRegion)
+                                atomicMin((unsigned long long *)&s.key[kk][ry * kRegion + rx], (unsigned long long)kv);
+                        }
+                    } else {
+                        engine_splat_pixel(s.key, d, x, y, db, __float_as_uint(__ldg(p.mv + i)),
+                                           __float_as_uint(__ldg(p.mv + plane + i)), st.fm, RX0, RY0);
+                    }
                 }
             }
         }
