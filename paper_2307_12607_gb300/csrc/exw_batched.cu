@@ -47,7 +47,7 @@ static EngineLayout engine_layout(const EngineSpec *specs, int n, int nfrac, boo
     b.nslots = n < kMaxStreams ? n : kMaxStreams;
     for (int i = 0; i < b.nslots; ++i) {
         const exw_frame &f = specs[shared_size ? 0 : i].src;
-        b.l[i] = ws_layout(f.W, f.H, 1, nfrac, false);
+        b.l[i] = ws_layout(f.W, f.H, 1, nfrac, false, true);
         b.base[i] = off;
         off += b.l[i].total;
     }
@@ -129,6 +129,7 @@ static bool build_params(EngineParams *ep, const EngineSpec *specs, int first, i
         p.tile_depth = (const float2 *)(sb + l.tile_depth);
         p.region_bounds = (const float4 *)(sb + l.region_bounds);
         p.plans = (TilePlan *)(sb + l.plans);
+        p.pdesc = (SplatTile *)(sb + l.pdesc);
         p.nbx = l.nbx;
         p.nby = l.nby;
         p.fh = headers + i;

@@ -102,15 +102,6 @@ static_assert(sizeof(Window<float, WinShape<0>::xf32, WinShape<0>::yf32>) == kWi
                   sizeof(Window<__half, WinShape<1>::xf16, WinShape<1>::yf16>) == kWindowBytes,
               "one buffer size for every shape and colour type");
 
-// A candidate 8 x 8 source tile of a splat: the fractions whose landing rectangle meets R and, for a clean tile
-// (one exact motion, every pixel can land), its whole-pixel offsets per fraction.
-struct alignas(16) SplatTile {
-    uint16_t bx, by;
-    uint8_t fm, clean;
-    int8_t ox[kMaxFrac], oy[kMaxFrac];
-    int8_t pad[2];
-};
-static_assert(sizeof(SplatTile) == 16, "one load per descriptor");
 struct EngineSmem {
     alignas(128) unsigned char win[2][kWindowBytes];  // TMA destinations, double-buffered
     uint64_t key[kMaxFrac][kRegionN];                // region keys per fraction (modes 1-3)
@@ -118,6 +109,7 @@ struct EngineSmem {
     float4 bpart[kMaxFrac][64];                      // per group: partial bounds of a region
     TileSlot slot[2];                                // the item in each buffer
     SplatTile cand[kConsumerThreads];                // candidate 8 x 8 source tiles of a splat
+    SplatTile pdesc[2][kPlanDesc];                   // the plan's candidates of the tile in each buffer
     uint32_t ncand;
     int abort;                                       // a bounded wait ran out: every warp leaves
     uint64_t full[2], empty[2];
@@ -328,8 +320,15 @@ __device__ inline void engine_producer(EngineSmem &s, const EngineParams &ep) {
             mode = __shfl_sync(0xFFFFFFFFu, word, 0);
             wx0 = __shfl_sync(0xFFFFFFFFu, word, 1);
             wy0 = __shfl_sync(0xFFFFFFFFu, word, 2);
+            const int ndesc = __shfl_sync(0xFFFFFFFFu, word, 3);
             const int X0 = (local % p.n5x) * kFillTile, Y0 = (local / p.n5x) * kFillTile;
             if (!st.tma && mode != 4) mode = 3;  // no window: every tile reads global memory
+            if (mode >= 1 && mode <= 3 && ndesc > 0) {  // the splat's candidates, as the plan found them
+                const uint4 *src = reinterpret_cast<const uint4 *>(p.pdesc + (size_t)local * kPlanDesc);
+                uint4 *dst = reinterpret_cast<uint4 *>(s.pdesc[b]);
+                if (lane < ndesc) dst[lane] = __ldcg(src + lane);
+                if (lane + 32 < ndesc) dst[lane + 32] = __ldcg(src + lane + 32);
+            }
             if (mode == 0 || mode == 5) {
                 const uint32_t umx = (uint32_t)__shfl_sync(0xFFFFFFFFu, word, 16);
                 const uint32_t umy = (uint32_t)__shfl_sync(0xFFFFFFFFu, word, 17);
@@ -634,10 +633,16 @@ __device__ __forceinline__ int describe_tiles(SplatTile *out, const TileParams &
 // 8 x 8 tiles only, a warp per tile (two pixels per lane); a clean tile splats with its precomputed offsets.
 template <typename CT, int WX, int WY>
 __device__ __forceinline__ void engine_splat_window(EngineSmem &s, const TileParams &p, const FrameDims &d,
-                                                    const WinAcc<CT, WX, WY> &a, Rect U, int RX0, int RY0, int tid) {
-    SplatTile *tiles = s.cand;
-    const int nt = describe_tiles(tiles, p, d, U, RX0, RY0, tid);
-    bar_sync(kBarConsumers, kConsumerThreads);
+                                                    const WinAcc<CT, WX, WY> &a, Rect U, int RX0, int RY0, int tid,
+                                                    const SplatTile *pre, int npre) {
+    // the plan's candidates landed with the slot; without them (too many) they are described here
+    const SplatTile *tiles = pre;
+    int nt = npre;
+    if (npre == 0) {
+        nt = describe_tiles(s.cand, p, d, U, RX0, RY0, tid);
+        tiles = s.cand;
+        bar_sync(kBarConsumers, kConsumerThreads);
+    }
     // half a source tile per warp and round (its descriptor is one broadcast load), all warps busy
     for (int q = tid; q < 64 * nt; q += kConsumerThreads) {
         const SplatTile st = tiles[q >> 6];
@@ -669,13 +674,23 @@ __device__ __forceinline__ void engine_splat_window(EngineSmem &s, const TilePar
 // Splat from global memory: the 8 x 8 source tiles whose bounds reach R, 64 threads per tile (all consumers).  A
 // clean candidate (one exact motion, every pixel can land) splats with its precomputed offsets and reads only the
 // depth of its pixels.
+__device__ __forceinline__ void splat_global_candidate(EngineSmem &s, const TileParams &p, const FrameDims &d,
+                                                       const SplatTile &st, int RX0, int RY0, int tid);
+
 __device__ inline void engine_splat_global(EngineSmem &s, const TileParams &p, const FrameDims &d, int RX0, int RY0,
-                                           int tid) {
+                                           int tid, const SplatTile *pre, int npre) {
+    if (npre > 0) {  // the plan's candidates, 64 threads each
+        for (int c0 = 0; c0 < npre; c0 += kConsumerThreads / 64) {
+            const int ci = c0 + (tid >> 6);
+            if (ci < npre) splat_global_candidate(s, p, d, pre[ci], RX0, RY0, tid);
+        }
+        bar_sync(kBarConsumers, kConsumerThreads);
+        return;
+    }
     int bx0, bx1, by0, by1;
     if (!frame_window(p, RX0, RY0, bx0, bx1, by0, by1)) return;
     const int nbxr = bx1 - bx0 + 1;
     const int total = nbxr * (by1 - by0 + 1);
-    const size_t plane = (size_t)p.W * p.H;
     for (int base = 0; base < total; base += kConsumerThreads) {
         if (tid == 0) s.ncand = 0u;
         bar_sync(kBarConsumers, kConsumerThreads);
@@ -711,31 +726,34 @@ __device__ inline void engine_splat_global(EngineSmem &s, const TileParams &p, c
         const int nc = (int)s.ncand;
         for (int c0 = 0; c0 < nc; c0 += kConsumerThreads / 64) {
             const int ci = c0 + (tid >> 6);
-            if (ci < nc) {
-                const SplatTile st = s.cand[ci];
-                const int x = 8 * st.bx + (tid & 7), y = 8 * st.by + ((tid >> 3) & 7);
-                if (x < p.W && y < p.H) {
-                    const size_t i = (size_t)y * p.W + x;
-                    const uint32_t db = __float_as_uint(__ldg(p.depth + i));
-                    if (st.clean) {
-                        const uint64_t kv = pack_key_local(db, x, y);
-#pragma unroll
-                        for (int kk = 0; kk < kMaxFrac; ++kk) {
-                            if (!(st.fm & (1u << kk))) continue;
-                            const int gx = x + st.ox[kk], gy = y + st.oy[kk];
-                            if ((unsigned)gx >= (unsigned)d.W || (unsigned)gy >= (unsigned)d.H) continue;
-                            const int rx = gx - RX0, ry = gy - RY0;
-                            if ((unsigned)rx < (unsigned)kRegion && (unsigned)ry < (unsigned)kRegion)
-                                atomicMin((unsigned long long *)&s.key[kk][ry * kRegion + rx], (unsigned long long)kv);
-                        }
-                    } else {
-                        engine_splat_pixel(s.key, d, x, y, db, __float_as_uint(__ldg(p.mv + i)),
-                                           __float_as_uint(__ldg(p.mv + plane + i)), st.fm, RX0, RY0);
-                    }
-                }
-            }
+            if (ci < nc) splat_global_candidate(s, p, d, s.cand[ci], RX0, RY0, tid);
         }
         bar_sync(kBarConsumers, kConsumerThreads);
+    }
+}
+
+// One pixel (of 64 threads' 8 x 8 tile) of a candidate source tile, from global memory.
+__device__ __forceinline__ void splat_global_candidate(EngineSmem &s, const TileParams &p, const FrameDims &d,
+                                                       const SplatTile &st, int RX0, int RY0, int tid) {
+    const int x = 8 * st.bx + (tid & 7), y = 8 * st.by + ((tid >> 3) & 7);
+    if (x >= p.W || y >= p.H) return;
+    const size_t i = (size_t)y * p.W + x;
+    const uint32_t db = __float_as_uint(__ldg(p.depth + i));
+    if (st.clean) {
+        const uint64_t kv = pack_key_local(db, x, y);
+#pragma unroll
+        for (int kk = 0; kk < kMaxFrac; ++kk) {
+            if (!(st.fm & (1u << kk))) continue;
+            const int gx = x + st.ox[kk], gy = y + st.oy[kk];
+            if ((unsigned)gx >= (unsigned)d.W || (unsigned)gy >= (unsigned)d.H) continue;
+            const int rx = gx - RX0, ry = gy - RY0;
+            if ((unsigned)rx < (unsigned)kRegion && (unsigned)ry < (unsigned)kRegion)
+                atomicMin((unsigned long long *)&s.key[kk][ry * kRegion + rx], (unsigned long long)kv);
+        }
+    } else {
+        const size_t plane = (size_t)p.W * p.H;
+        engine_splat_pixel(s.key, d, x, y, db, __float_as_uint(__ldg(p.mv + i)),
+                           __float_as_uint(__ldg(p.mv + plane + i)), st.fm, RX0, RY0);
     }
 }
 
@@ -1283,12 +1301,13 @@ __device__ __forceinline__ void tile_splat(EngineSmem &s, const TileSlot &sl, in
     const FrameDims d = dims_of(p);
     const int mode = sl.plan.mode;
     const int RX0 = sl.X0 - 1, RY0 = sl.Y0 - 1;
+    const int npre = sl.plan.ndesc;  // the plan's candidates in s.pdesc[b] (0: none stored)
     if (mode == 1) {
         const WinAcc<CT, WX, WY> wa{&window<CT, WX, WY>(s, b), sl.plan.wx0, sl.plan.wy0};
-        engine_splat_window(s, p, d, wa, plan_union(sl.plan, d.nfrac), RX0, RY0, tid);
+        engine_splat_window(s, p, d, wa, plan_union(sl.plan, d.nfrac), RX0, RY0, tid, s.pdesc[b], npre);
         bar_sync(kBarConsumers, kConsumerThreads);
     } else if (mode == 2 || mode == 3) {
-        engine_splat_global(s, p, d, RX0, RY0, tid);
+        engine_splat_global(s, p, d, RX0, RY0, tid, s.pdesc[b], npre);
     }
 }
 

@@ -48,12 +48,24 @@ struct FrameHeader {
 };
 static_assert(sizeof(FrameHeader) == 128, "FrameHeader is 128 bytes");
 
+// A candidate 8 x 8 source tile of a target tile's splat: the fractions whose landing rectangle meets the tile's
+// region and, for a clean tile (one exact motion, every pixel can land, offsets within int8), its whole-pixel
+// offsets per fraction.
+struct alignas(16) SplatTile {
+    uint16_t bx, by;
+    uint8_t fm, clean;
+    int8_t ox[3], oy[3];
+    int8_t pad[2];
+};
+static_assert(sizeof(SplatTile) == 16, "one load per descriptor");
+constexpr int kPlanDesc = 64;  // candidate descriptors the plan stores per target tile (more: none are stored)
+
 // Per target tile, how the fused pass stages its sources (written by the plan kernel).
 struct alignas(16) TilePlan {
     int mode;          // 0 uniform motion, 1 one window, 2 one window per fraction, 3 global memory, 4 nothing
                        // lands, 5 uniform motion over smooth valid sources (every pixel a winner, every tap agrees)
     int wx0, wy0;      // window origin (modes 0 and 1)
-    int pad0;
+    int ndesc;         // candidate source tiles stored in the plan's descriptors (0: more than kPlanDesc)
     int rect[3][4];    // per fraction, landing rectangle x0, x1, y0, y1 (source pixels; empty if x1 < x0)
     uint32_t umx, umy; // the one motion of a uniform tile (float bits)
     int pad1[2];
@@ -62,7 +74,7 @@ static_assert(sizeof(TilePlan) == 80, "TilePlan is 80 bytes");
 
 // Byte offsets of the workspace sections for nframes frames of W x H with nfrac fractions.
 struct WsLayout {
-    size_t headers, tile_bounds, tile_depth, region_bounds, plans, nodes, list, fillval, coarse, keys, total;
+    size_t headers, tile_bounds, tile_depth, region_bounds, plans, pdesc, nodes, list, fillval, coarse, keys, total;
     int nbx, nby;       // motion-bounds tiles
     int n5x, n5y;       // fill tiles (level-5 nodes of the pyramid)
     int ncoarse;        // pyramid nodes above level 5, per fraction
@@ -78,7 +90,7 @@ inline int coarse_nodes(int n5x, int n5y) {
     return total;
 }
 
-inline WsLayout ws_layout(int W, int H, int nframes, int nfrac, bool with_keys) {
+inline WsLayout ws_layout(int W, int H, int nframes, int nfrac, bool with_keys, bool with_desc = false) {
     WsLayout l{};
     l.nbx = ceil_div(W, 8);
     l.nby = ceil_div(H, 8);
@@ -97,6 +109,8 @@ inline WsLayout ws_layout(int W, int H, int nframes, int nfrac, bool with_keys) 
     off += align_up(n5 * 16);
     l.plans = off;
     off += align_up(n5 * sizeof(TilePlan));
+    l.pdesc = off;  // the plans' candidate descriptors (the persistent engine only)
+    if (with_desc) off += align_up(n5 * kPlanDesc * sizeof(SplatTile));
     l.nodes = off;
     off += align_up((size_t)nfrac * n5 * 16);
     l.list = off;
@@ -125,6 +139,7 @@ struct alignas(16) TileParams {
     const float2 *tile_depth;   // per 8 x 8 tile: depth range of its pixels, (-1, -1) if one cannot land
     const float4 *region_bounds;  // per 32 x 32 region (fill tile): motion bounds of its 8 x 8 tiles
     TilePlan *plans;            // [n5] staging plan per target tile (persistent TMA kernel)
+    SplatTile *pdesc;           // [n5][kPlanDesc] candidate source tiles per target tile, or null
     int nbx, nby;
     FrameHeader *fh;
     float4 *nodes;              // [nfrac][n5]

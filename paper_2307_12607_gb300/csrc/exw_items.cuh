@@ -45,11 +45,15 @@ __device__ inline void plan_tile(const TileParams &p, int tile) {  // called by 
     }
     bool uni = true, has = false;
     uint32_t mx = 0u, my = 0u;
-    // One 8 x 8 bounds tile (bx, by): does it reach R, and with which landing rectangles and motion?
-    auto visit = [&](int bx, int by) {
+    // One 8 x 8 bounds tile (bx, by): does it reach R, and with which landing rectangles and motion?  Returns its
+    // splat descriptor (fm = 0 when it does not reach R).
+    auto visit = [&](int bx, int by) -> SplatTile {
+        SplatTile st{};
         const float4 b = __ldcg(p.tile_bounds + (size_t)by * p.nbx + bx);
-        if (!(b.x <= b.y)) return;
-        bool cand = false;
+        const float2 dr = __ldcg(p.tile_depth + (size_t)by * p.nbx + bx);  // issued with the bounds
+        if (!(b.x <= b.y)) return st;
+        uint32_t fm = 0u;
+        bool small = true;
 #pragma unroll
         for (int kk = 0; kk < kMaxFrac; ++kk) {
             int ox0, ox1, oy0, oy1;
@@ -57,19 +61,30 @@ __device__ inline void plan_tile(const TileParams &p, int tile) {  // called by 
             const int lx0 = max(8 * bx, RX0 - ox1), lx1 = min(min(8 * bx + 7, p.W - 1), RX0 + kRegion - 1 - ox0);
             const int ly0 = max(8 * by, RY0 - oy1), ly1 = min(min(8 * by + 7, p.H - 1), RY0 + kRegion - 1 - oy0);
             const bool hit = kk < p.nfrac && lx0 <= lx1 && ly0 <= ly1;
-            cand = cand || hit;
+            fm |= hit ? 1u << kk : 0u;
             r[kk][0] = hit ? min(r[kk][0], lx0) : r[kk][0];
             r[kk][1] = hit ? max(r[kk][1], lx1) : r[kk][1];
             r[kk][2] = hit ? min(r[kk][2], ly0) : r[kk][2];
             r[kk][3] = hit ? max(r[kk][3], ly1) : r[kk][3];
+            small = small && ox0 >= -128 && ox0 <= 127 && oy0 >= -128 && oy0 <= 127;
+            st.ox[kk] = (int8_t)max(-128, min(127, ox0));
+            st.oy[kk] = (int8_t)max(-128, min(127, oy0));
         }
-        if (cand) {
+        if (fm) {
             const uint32_t bxb = __float_as_uint(b.x), byb = __float_as_uint(b.z);
             if (b.x != b.y || b.z != b.w) uni = false;
             else if (!has) { has = true; mx = bxb; my = byb; }
             else if (mx != bxb || my != byb) uni = false;
+            st.bx = (uint16_t)bx;
+            st.by = (uint16_t)by;
+            st.fm = (uint8_t)fm;
+            st.clean = b.x == b.y && b.z == b.w && dr.x > 0.0f && small ? 1 : 0;
         }
+        return st;
     };
+    // the candidates, compacted in visiting order into the plan's descriptors (none when there are too many)
+    SplatTile *desc = p.pdesc != nullptr ? p.pdesc + (size_t)tile * kPlanDesc : nullptr;
+    int ndesc = 0;
     // Two levels: the 32 x 32 regions within the frame-wide motion range whose bounds can reach R (one per lane),
     // then the 16 bounds tiles of each such region (two regions per pass, 16 lanes each).  A region's bounds
     // contain its tiles' bounds and the offsets are monotone in the motion, so no tile that reaches R is skipped.
@@ -106,13 +121,19 @@ __device__ inline void plan_tile(const TileParams &p, int tile) {  // called by 
                 const int src = lane < 16 ? l0 : l1;
                 const int qx = __shfl_sync(0xFFFFFFFFu, rxl, src < 0 ? 0 : src);
                 const int qy = __shfl_sync(0xFFFFFFFFu, ryl, src < 0 ? 0 : src);
+                SplatTile st{};
                 if (src >= 0) {
                     const int bx = 4 * qx + (lane & 3), by = 4 * qy + ((lane >> 2) & 3);
-                    if (bx < p.nbx && by < p.nby) visit(bx, by);
+                    if (bx < p.nbx && by < p.nby) st = visit(bx, by);
                 }
+                const unsigned hm = __ballot_sync(0xFFFFFFFFu, st.fm != 0);
+                const int slot = ndesc + __popc(hm & ((1u << lane) - 1u));
+                if (desc != nullptr && st.fm != 0 && slot < kPlanDesc) desc[slot] = st;
+                ndesc += __popc(hm);
             }
         }
     }
+    __syncwarp();  // every lane's descriptors before lane 0 publishes the plan
 #pragma unroll
     for (int kk = 0; kk < kMaxFrac; ++kk) {
         r[kk][0] = __reduce_min_sync(0xFFFFFFFFu, r[kk][0]);
@@ -189,6 +210,7 @@ __device__ inline void plan_tile(const TileParams &p, int tile) {  // called by 
     pl.mode = -1;
     pl.umx = mx;
     pl.umy = my;
+    pl.ndesc = desc != nullptr && ndesc <= kPlanDesc ? ndesc : 0;
     if (U.empty()) {
         pl.mode = 4;
     } else if (uni && hasm) {
