@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--impl", choices=["exw", "reference"], default="exw")
     ap.add_argument("--frames", type=int, default=NFRAMES)
     ap.add_argument("--e2e-steps", type=int, default=0, help="end-to-end steps (0: as many as --steps)")
-    ap.add_argument("--e2e-chunk", type=int, default=2, help="frames per overlapped copy/compute chunk (e2e)")
+    ap.add_argument("--e2e-chunk", type=int, default=8, help="frames per overlapped copy/compute chunk (e2e)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
@@ -662,8 +662,11 @@ def run_exw(args):
     barrier()
     e2e_steps = args.e2e_steps if args.e2e_steps > 0 else args.steps
     t0 = time.perf_counter()   # wall clock: the host's own work per call counts too
+    enqueue = 0.0
     for _ in range(e2e_steps):
+        ta = time.perf_counter()
         e2e_step()
+        enqueue += time.perf_counter() - ta
     torch.cuda.synchronize()
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, devc)
     barrier()
@@ -686,6 +689,7 @@ def run_exw(args):
                 "cpu_baseline": cpu,
                 "e2e": {"value": whole_job_rate(world, out_px, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3, "steps": e2e_steps,
+                        "chunk_frames": args.e2e_chunk, "host_enqueue_ms_per_step": enqueue / e2e_steps * 1e3,
                         "copy_ceiling": ceiling,
                         "frac_of_copy_ceiling": ceiling["both_directions_ms"] / (e2e_s * 1e3)},
                 "extras": extras}
