@@ -66,22 +66,27 @@ def dist_env():
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of a kernel per SOURCE FRAME it processed, from one ncu
 # capture (a smaller launch; the engine's traffic grows in proportion to the frames of a launch), with the hash of
-# the engine's sources (ENGINE_SOURCES) it was taken on: reported only while they are unchanged, else null.
+# the kernel's sources (KERNEL_SOURCES) it was taken on: reported only while they are unchanged, else null.
 MEASURED_TRAFFIC = {
-    ("exw_engine", "sequence_1080p_fp32"): ((238.34e6 + 279.37e6) / 4, "6234f90c90ef1c89"),
-    ("exw_engine", "warp_4k_fp16"): (105.39e6 + 129.86e6, "6234f90c90ef1c89"),
+    ("exw_engine", "sequence_1080p_fp32"): ((236.007e6 + 279.348e6) / 4, "cafc3368605ea736"),
+    ("exw_engine", "warp_4k_fp16"): (105.188e6 + 129.443e6, "cafc3368605ea736"),
+    ("exw_train", "fwd_bwd_1080p"): (215.143e6 + 27.901e6, "b0b6ea69f6dae11e"),
 }
 
 
-# The sources of the engine kernel and its host-side launch (the kernel whose traffic is recorded above).
-ENGINE_SOURCES = ("exw_engine.cu", "exw_engine.cuh", "exw_items.cuh", "exw_tile.cuh", "exw_device.cuh", "exw_tma.cuh",
-                  "exw_internal.h", "exw_batched.cu")
+# The sources of each kernel and its host-side launch (the kernels whose traffic is recorded above).
+KERNEL_SOURCES = {
+    "exw_engine": ("exw_engine.cu", "exw_engine.cuh", "exw_items.cuh", "exw_tile.cuh", "exw_device.cuh",
+                   "exw_tma.cuh", "exw_internal.h", "exw_batched.cu"),
+    "exw_train": ("exw_bwd.cu", "exw_device.cuh", "exw_internal.h"),
+}
+ENGINE_SOURCES = KERNEL_SOURCES["exw_engine"]
 
 
-def csrc_hash() -> str:
+def csrc_hash(kernel: str = "exw_engine") -> str:
     import hashlib
     h = hashlib.sha256()
-    for name in ENGINE_SOURCES:
+    for name in KERNEL_SOURCES[kernel]:
         f = os.path.join(ROOT, "paper_2307_12607_gb300", "csrc", name)
         h.update(name.encode())
         with open(f, "rb") as fh:
@@ -91,7 +96,7 @@ def csrc_hash() -> str:
 
 def measured_traffic(kernel: str, workload: str):
     t = MEASURED_TRAFFIC.get((kernel, workload))
-    return t[0] if t is not None and t[1] == csrc_hash() else None
+    return t[0] if t is not None and t[1] == csrc_hash(kernel) else None
 
 
 def peaks():
@@ -506,7 +511,9 @@ def _extras_diff(b, devc, ex):
                            "kernel_us": _kernel_means(b, fused),
                            "roofline": {"bound": "hbm", "algorithmic_bytes_per_source_px": alg,
                                         "achieved_gbs": alg * 8 * W * H / (ms_fused / 1e3) / 1e9,
-                                        "frac": alg * 8 * W * H / (ms_fused / 1e3) / 1e9 / peak},
+                                        "frac": alg * 8 * W * H / (ms_fused / 1e3) / 1e9 / peak,
+                                        "traffic_train_kernel_per_frame": measured_traffic("exw_train",
+                                                                                           "fwd_bwd_1080p")},
                            "staged_path": {"value": px / ms_fb / 1e3, "ms_per_step": ms_fb,
                                            "fwd_only": px / ms_f / 1e3, "kernel_us": _kernel_means(b, fwd_bwd)},
                            "ratio_vs_staged": ms_fb / ms_fused,
