@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--case", choices=EXTRAS, default=None,
+    ap.add_argument("--case", choices=CASES, default=None,
                     help="time only this one configuration and print its JSON (for profiling)")
     return ap.parse_args()
 
@@ -308,6 +308,7 @@ def _kernel_means(b, fn):
 
 
 EXTRAS = ("warp_4k_fp16", "extrapolate_4k_fp16_fill", "batched_48_streams", "fwd_bwd_1080p", "quality_and_stats")
+CASES = EXTRAS + ("fwd_bwd_fused_only",)  # the last: the fused training pass alone (for profiling it)
 
 
 def run_extras(b, devc, names=EXTRAS):
@@ -324,6 +325,8 @@ def run_extras(b, devc, names=EXTRAS):
         _extras_batched(b, devc, ex)
     if "fwd_bwd_1080p" in names:
         _extras_diff(b, devc, ex)
+    if "fwd_bwd_fused_only" in names:
+        _extras_diff(b, devc, ex, fused_only=True)
     if "quality_and_stats" in names:
         _extras_quality(b, devc, peak, ex)
     return ex
@@ -452,7 +455,7 @@ def _extras_batched(b, devc, ex):
     b.exw_tuner_destroy(tuner)
 
 
-def _extras_diff(b, devc, ex):
+def _extras_diff(b, devc, ex, fused_only=False):
     import torch
     from paper_2307_12607_gb300 import scenes
     # differentiation: 8 frames 1080p FP32, k = 1..3, L2 loss against the ground truth at t + k/4
@@ -499,6 +502,11 @@ def _extras_diff(b, devc, ex):
 
     def fused():
         b.exw_warp_l2_grad(c_all, d_all, m_all, t_all, 3, grad_color=gcb, grad_mv=gmb, loss=lossb, ws=wsf)
+    if fused_only:
+        ms_fused = _event_ms(fused, 10)
+        ex["fwd_bwd_fused_only"] = {"value": 8 * 3 * W * H / ms_fused / 1e3, "unit": "Mpixel/s",
+                                    "ms_per_step": ms_fused}
+        return
     ms_f = _event_ms(fwd, 3)
     ms_fb = _event_ms(fwd_bwd, 3)
     ms_fused = _event_ms(fused, 10)
