@@ -51,9 +51,10 @@ def test_workspace_sizes(lib):
     from paper_2307_12607_gb300 import binding as b
     n1 = b.exw_workspace_bytes(b.OP_EXTRAPOLATE, 1920, 1080, b.F32, 1, 3)
     n60 = b.exw_workspace_bytes(b.OP_EXTRAPOLATE, 1920, 1080, b.F32, 60, 3)
-    # per frame: a header; per frame in flight (at most 48 per launch): bounds, plans, pyramid nodes -- a few
-    # percent of the frames' own bytes
-    assert 0 < n1 < n60 < 0.03 * 60 * 1920 * 1080 * (12 + 4 + 8)
+    # per frame: a header; per frame in flight (at most 48 per launch): bounds, plans with their candidate source
+    # tiles (1 KB per 32 x 32 target tile), pyramid nodes -- a few percent of the frames' own input bytes
+    assert 0 < n1 < n60 < 0.06 * 60 * 1920 * 1080 * (12 + 4 + 8)
+    assert n60 < 49 * n1  # frames beyond the 48 of a launch add only their 128-byte header
     assert b.exw_workspace_bytes(b.OP_WARP_BACKWARD, 64, 64) >= 64 * 64 * 8
     assert b.exw_workspace_bytes(b.OP_EXTRAPOLATE, 0, 10) == 0
     assert b.exw_workspace_bytes(b.OP_EXTRAPOLATE, 16385, 10) == 0
