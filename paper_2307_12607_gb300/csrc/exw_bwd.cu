@@ -24,15 +24,14 @@ constexpr int kBwdThreads = 256;
 constexpr int kStage = kFillTile + 4;  // S plus a two-pixel ring: the ring's winners and their taps
 constexpr int kStageN = kStage * kStage;
 
-// Shared memory of a CTA: the staged source (read once, used by every fraction), the per-fraction records of
-// phase 1 and the motion accumulators of S.
+// Shared memory of a CTA: the staged source depth and colour (read once, used by every fraction; the motion is
+// read at p only, through L1), the per-fraction records of phase 1 and the motion accumulators of S.
 template <typename CT>
 struct BwdSmem {
     float4 recw[kRegionN];  // w_t / S for taps (p), (p+sx), (p+sy), (p+sx+sy)
     float4 recg[kRegionN];  // g(q) rgb, .w = flags: bit0 active, bits1-2 sx+1, bits3-4 sy+1
     float2 gms[kFillTile * kFillTile];
     float depth[kStageN];   // NaN outside the frame (never lands, never agrees)
-    float mvx[kStageN], mvy[kStageN];
     CT col[3][kStageN];
     double red[kBwdThreads / 32];
     int last;
@@ -54,7 +53,7 @@ struct BwdArgs {
 };
 
 template <typename CT, bool FUSED>
-__global__ void __launch_bounds__(kBwdThreads, 2) bwd_tile_kernel(const BwdArgs a) {
+__global__ void __launch_bounds__(kBwdThreads, 3) bwd_tile_kernel(const BwdArgs a) {
     extern __shared__ __align__(16) unsigned char bwd_smem_raw[];
     BwdSmem<CT> &sm = *reinterpret_cast<BwdSmem<CT> *>(bwd_smem_raw);
     float4 *recw = sm.recw, *recg = sm.recg;
@@ -88,8 +87,6 @@ __global__ void __launch_bounds__(kBwdThreads, 2) bwd_tile_kernel(const BwdArgs 
         const bool in = x >= 0 && x < W && y >= 0 && y < H;
         const size_t i = in ? (size_t)y * W + x : 0;
         sm.depth[c] = in ? __ldg(a.depth + i) : __int_as_float(0x7FC00000);
-        sm.mvx[c] = in ? __ldg(a.mv + i) : 0.0f;
-        sm.mvy[c] = in ? __ldg(a.mv + plane + i) : 0.0f;
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) sm.col[ch][c] = in ? col[ch * plane + i] : to_storage<CT>(0.0f);
     }
@@ -111,7 +108,7 @@ __global__ void __launch_bounds__(kBwdThreads, 2) bwd_tile_kernel(const BwdArgs 
             if (px >= 0 && px < W && py >= 0 && py < H) {
                 const size_t i = (size_t)py * W + px;
                 const uint32_t db = __float_as_uint(sm.depth[e]);
-                const uint32_t ux = __float_as_uint(sm.mvx[e]), uy = __float_as_uint(sm.mvy[e]);
+                const uint32_t ux = __float_as_uint(__ldg(a.mv + i)), uy = __float_as_uint(__ldg(a.mv + plane + i));
                 if (depth_ok(db) && finite_bits(ux) && finite_bits(uy)) {
                     const AxisDec dx = axis_dec(ux, L), dy = axis_dec(uy, L);
                     const bool lands = dx.land && dy.land;
