@@ -24,15 +24,14 @@ constexpr int kBwdThreads = 256;
 constexpr int kStage = kFillTile + 4;  // S plus a two-pixel ring: the ring's winners and their taps
 constexpr int kStageN = kStage * kStage;
 
-// Shared memory of a CTA: the staged source depth and colour (read once, used by every fraction; the motion is
-// read at p only, through L1), the per-fraction records of phase 1 and the motion accumulators of S.
+// Shared memory of a CTA: the staged source depth (read once, used by every fraction for the taps' agreement; the
+// motion and colour are read through L1), the per-fraction records of phase 1 and the motion accumulators of S.
 template <typename CT>
 struct BwdSmem {
     float4 recw[kRegionN];  // w_t / S for taps (p), (p+sx), (p+sy), (p+sx+sy)
     float4 recg[kRegionN];  // g(q) rgb, .w = flags: bit0 active, bits1-2 sx+1, bits3-4 sy+1
     float2 gms[kFillTile * kFillTile];
     float depth[kStageN];   // NaN outside the frame (never lands, never agrees)
-    CT col[3][kStageN];
     double red[kBwdThreads / 32];
     int last;
 };
@@ -53,7 +52,7 @@ struct BwdArgs {
 };
 
 template <typename CT, bool FUSED>
-__global__ void __launch_bounds__(kBwdThreads, 3) bwd_tile_kernel(const BwdArgs a) {
+__global__ void __launch_bounds__(kBwdThreads, 4) bwd_tile_kernel(const BwdArgs a) {
     extern __shared__ __align__(16) unsigned char bwd_smem_raw[];
     BwdSmem<CT> &sm = *reinterpret_cast<BwdSmem<CT> *>(bwd_smem_raw);
     float4 *recw = sm.recw, *recg = sm.recg;
@@ -87,8 +86,6 @@ __global__ void __launch_bounds__(kBwdThreads, 3) bwd_tile_kernel(const BwdArgs 
         const bool in = x >= 0 && x < W && y >= 0 && y < H;
         const size_t i = in ? (size_t)y * W + x : 0;
         sm.depth[c] = in ? __ldg(a.depth + i) : __int_as_float(0x7FC00000);
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) sm.col[ch][c] = in ? col[ch * plane + i] : to_storage<CT>(0.0f);
     }
     __syncthreads();  // phase 1 reads the stage and updates cells another thread loaded
     float lacc = 0.0f;  // this thread's loss terms (at most 5 cells x 3 fractions x 3 channels), then FP64
@@ -150,13 +147,14 @@ __global__ void __launch_bounds__(kBwdThreads, 3) bwd_tile_kernel(const BwdArgs 
                                                  __fmul_rn(w11, inv));
                                 float C[3][4];  // tap colours (0 for taps that do not take part)
                                 if (FUSED || inside) {
+                                    const size_t t10 = i + sx, t01 = sy > 0 ? i + W : i - W, t11 = t01 + sx;
 #pragma unroll
                                     for (int c = 0; c < 3; ++c) {
-                                        const CT *cp = sm.col[c];
-                                        C[c][0] = to_f<CT>(cp[e]);
-                                        C[c][1] = a10 ? to_f<CT>(cp[e10]) : 0.f;
-                                        C[c][2] = a01 ? to_f<CT>(cp[e01]) : 0.f;
-                                        C[c][3] = a11 ? to_f<CT>(cp[e11]) : 0.f;
+                                        const CT *cp = col + c * plane;
+                                        C[c][0] = load_c<CT>(cp + i);
+                                        C[c][1] = a10 ? load_c<CT>(cp + t10) : 0.f;
+                                        C[c][2] = a01 ? load_c<CT>(cp + t01) : 0.f;
+                                        C[c][3] = a11 ? load_c<CT>(cp + t11) : 0.f;
                                     }
                                 }
                                 float g[3];
