@@ -611,9 +611,10 @@ __device__ __forceinline__ int describe_tiles(SplatTile *out, const TileParams &
         if (b.x <= b.y) {
             const bool uni = b.x == b.y && b.z == b.w;
             uint32_t fm = 0;
+            const BoundsDec bd = bounds_dec(b, d.L);
             for (int kk = 0; kk < d.nfrac; ++kk) {
                 int ox0, ox1, oy0, oy1;
-                tile_offsets(b, d.k0 + kk, d.L, ox0, ox1, oy0, oy1);
+                bounds_offsets(bd, d.k0 + kk, ox0, ox1, oy0, oy1);
                 if (8 * bx + 7 + ox1 >= RX0 && 8 * bx + ox0 < RX0 + kRegion && 8 * by + 7 + oy1 >= RY0 &&
                     8 * by + oy0 < RY0 + kRegion)
                     fm |= 1u << kk;
@@ -703,9 +704,10 @@ __device__ inline void engine_splat_global(EngineSmem &s, const TileParams &p, c
                 SplatTile st{};
                 uint32_t fm = 0;
                 bool small = true;  // every offset fits an int8 (else a clean tile still splats per pixel)
+                const BoundsDec bd = bounds_dec(b, p.L);
                 for (int kk = 0; kk < p.nfrac; ++kk) {
                     int ox0, ox1, oy0, oy1;
-                    tile_offsets(b, p.k0 + kk, p.L, ox0, ox1, oy0, oy1);
+                    bounds_offsets(bd, p.k0 + kk, ox0, ox1, oy0, oy1);
                     const int tx0 = 8 * bx + ox0, tx1 = 8 * bx + 7 + ox1;
                     const int ty0 = 8 * by + oy0, ty1 = 8 * by + 7 + oy1;
                     if (tx1 >= RX0 && tx0 < RX0 + kRegion && ty1 >= RY0 && ty0 < RY0 + kRegion) fm |= 1u << kk;

@@ -54,10 +54,11 @@ __device__ inline void plan_tile(const TileParams &p, int tile) {  // called by 
         if (!(b.x <= b.y)) return st;
         uint32_t fm = 0u;
         bool small = true;
+        const BoundsDec bd = bounds_dec(b, p.L);
 #pragma unroll
         for (int kk = 0; kk < kMaxFrac; ++kk) {
             int ox0, ox1, oy0, oy1;
-            tile_offsets(b, p.k0 + kk, p.L, ox0, ox1, oy0, oy1);
+            bounds_offsets(bd, p.k0 + kk, ox0, ox1, oy0, oy1);
             const int lx0 = max(8 * bx, RX0 - ox1), lx1 = min(min(8 * bx + 7, p.W - 1), RX0 + kRegion - 1 - ox0);
             const int ly0 = max(8 * by, RY0 - oy1), ly1 = min(min(8 * by + 7, p.H - 1), RY0 + kRegion - 1 - oy0);
             const bool hit = kk < p.nfrac && lx0 <= lx1 && ly0 <= ly1;
@@ -101,9 +102,10 @@ __device__ inline void plan_tile(const TileParams &p, int tile) {  // called by 
                 rxl = rx0 + idx % nrr;
                 const float4 rb = __ldcg(p.region_bounds + (size_t)ryl * p.n5x + rxl);
                 if (rb.x <= rb.y) {
+                    const BoundsDec rd = bounds_dec(rb, p.L);
                     for (int kk = 0; kk < p.nfrac && !reach; ++kk) {
                         int ox0, ox1, oy0, oy1;
-                        tile_offsets(rb, p.k0 + kk, p.L, ox0, ox1, oy0, oy1);
+                        bounds_offsets(rd, p.k0 + kk, ox0, ox1, oy0, oy1);
                         reach = 32 * rxl + 31 + ox1 >= RX0 && 32 * rxl + ox0 <= RX0 + kRegion - 1 &&
                                 32 * ryl + 31 + oy1 >= RY0 && 32 * ryl + oy0 <= RY0 + kRegion - 1;
                     }

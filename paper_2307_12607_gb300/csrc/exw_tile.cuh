@@ -61,12 +61,20 @@ __device__ __forceinline__ bool frame_window(const TileParams &p, int RX0, int R
     return bx0 <= bx1 && by0 <= by1;
 }
 
-// Offsets of one bounds tile for fraction k: [ox0, ox1] x [oy0, oy1].
-__device__ __forceinline__ void tile_offsets(const float4 &b, int k, int L, int &ox0, int &ox1, int &oy0, int &oy1) {
-    ox0 = axis_off_of(__float_as_uint(b.x), k, L);
-    ox1 = axis_off_of(__float_as_uint(b.y), k, L);
-    oy0 = axis_off_of(__float_as_uint(b.z), k, L);
-    oy1 = axis_off_of(__float_as_uint(b.w), k, L);
+// The four motion bounds of a tile decoded once (axis_dec); each fraction's offsets [ox0, ox1] x [oy0, oy1] then
+// cost four shift-adds (axis_off of the decoded bounds: the offset is monotone in the motion).
+struct BoundsDec {
+    AxisDec x0, x1, y0, y1;
+};
+__device__ __forceinline__ BoundsDec bounds_dec(const float4 &b, int L) {
+    return BoundsDec{axis_dec(__float_as_uint(b.x), L), axis_dec(__float_as_uint(b.y), L),
+                     axis_dec(__float_as_uint(b.z), L), axis_dec(__float_as_uint(b.w), L)};
+}
+__device__ __forceinline__ void bounds_offsets(const BoundsDec &d, int k, int &ox0, int &ox1, int &oy0, int &oy1) {
+    ox0 = axis_off(d.x0, k);
+    ox1 = axis_off(d.x1, k);
+    oy0 = axis_off(d.y0, k);
+    oy1 = axis_off(d.y1, k);
 }
 
 // Splat one source pixel (x, y) for the fractions in fm into the region keys.
@@ -118,9 +126,10 @@ __device__ inline void splat_global(TileSmem &s, const TileParams &p, int RX0, i
             const float4 b = __ldcg(p.tile_bounds + (size_t)by * p.nbx + bx);
             if (b.x <= b.y) {
                 uint32_t fm = 0;
+                const BoundsDec bd = bounds_dec(b, p.L);
                 for (int kk = 0; kk < p.nfrac; ++kk) {
                     int ox0, ox1, oy0, oy1;
-                    tile_offsets(b, p.k0 + kk, p.L, ox0, ox1, oy0, oy1);
+                    bounds_offsets(bd, p.k0 + kk, ox0, ox1, oy0, oy1);
                     const int tx0 = 8 * bx + ox0, tx1 = 8 * bx + 7 + ox1;
                     const int ty0 = 8 * by + oy0, ty1 = 8 * by + 7 + oy1;
                     if (tx1 >= RX0 && tx0 < RX0 + kRegion && ty1 >= RY0 && ty0 < RY0 + kRegion) fm |= 1u << kk;
