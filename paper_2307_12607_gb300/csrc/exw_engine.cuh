@@ -905,23 +905,43 @@ struct PendingCount {
     }
 };
 
-// Fill and store one fraction of the tile for the calling group (contains one group barrier; a warp without holes
-// only arrives at it unless it is warp 0, which builds the upper levels, or the group read splat keys, whose next
-// initialisation the barrier orders after every read).  c[] .w = validity.
+// Lazy level-5 nodes.  A tile-fraction without a hole is left as it is by the fill, and its level-5 node matters
+// only to the coarse pass of a fraction with a tile without any valid pixel -- which most frames never run.  Such a
+// tile publishes a placeholder instead of building its pyramid; when a coarse pass needs the node (it lies under
+// the first valid ancestor of an invalid tile), one warp computes it: a smooth tile from its source colour
+// (smooth_node), any other from its stored outputs (output_node).
+constexpr float kNodeLazy = 2.0f;       // .w of a smooth tile's node that is not computed
+constexpr float kNodeNeeded = 3.0f;     // .w of a lazy smooth node the coarse pass needs
+constexpr float kNodeLazyOut = 4.0f;    // .w of the node of another tile-fraction without a hole, not computed
+constexpr float kNodeNeededOut = 5.0f;  // .w of such a node the coarse pass needs
+
+// Fill and store one fraction of the tile for the calling group.  The group first votes on whether the tile has a
+// hole (a barrier that also orders every read of the splat keys before their next initialisation).  Without one the
+// fill leaves the tile as it is: the group stores, and the tile publishes a lazy node computed from its stored outputs
+// only if a coarse pass needs it (the group's stores are ordered before thread 0's count by a second barrier).  With
+// holes the pyramid is built: a second group barrier, at which a warp without holes only arrives unless it is warp 0,
+// which builds the upper levels.  c[] .w = validity.
 template <typename CT>
 __device__ __forceinline__ void fill_store_block(EngineSmem &s, const TileParams &p, const FrameDims &d, CT *oc,
                                                  uint8_t *om, int g, int kk, int tile, int buf, int TX, int TY,
-                                                 float4 c[4], const uint8_t m[4], bool vec, bool keys) {
+                                                 float4 c[4], const uint8_t m[4], bool vec) {
     const int tg = threadIdx.x & (kGroupThreads - 1);
     const int lane = tg & 31, w = tg >> 5;
+    const bool holes = __any_sync(0xFFFFFFFFu, (m[0] | m[1] | m[2] | m[3]) != 0);  // in the warp's rows
+    const bool all[4] = {true, true, true, true};
+    if (!bar_red_or(2 + g, kGroupThreads, holes)) {
+        store_block<CT>(d, oc, om, TX, TY, c, m, all, vec);
+        if (w == 0) bar_sync(2 + g, kGroupThreads);  // thread 0 counts the tile after every store of the group
+        else asm volatile("bar.arrive %0, %1;" ::"r"(2 + g), "r"(kGroupThreads) : "memory");
+        if (tg == 0) publish_node(p, make_float4(0.f, 0.f, 0.f, kNodeLazyOut), kk, tile);
+        return;
+    }
     const float4 n1 = mean4(c[0], c[1], c[2], c[3]);
     const float4 a1 = shfl4_xor(n1, 1), a16 = shfl4_xor(n1, 16), a17 = shfl4_xor(n1, 17);
     const float4 n2o = mean4(n1, a1, a16, a17);  // meaningful on lanes with even block x and even block y
     float4 *l2 = s.l2[g][buf];
     if ((lane & 17) == 0) l2[w * 8 + (lane >> 1)] = n2o;
-    const bool holes = __any_sync(0xFFFFFFFFu, (m[0] | m[1] | m[2] | m[3]) != 0);  // in the warp's rows
-    const bool all[4] = {true, true, true, true};
-    if (!holes && w != 0 && !keys) {  // needs no upper level; no other warp of the group still reads keys
+    if (!holes && w != 0) {  // needs no upper level
         asm volatile("bar.arrive %0, %1;" ::"r"(2 + g), "r"(kGroupThreads) : "memory");
         store_block<CT>(d, oc, om, TX, TY, c, m, all, vec);
         return;
@@ -983,13 +1003,49 @@ __device__ __forceinline__ float4 smooth_level2(const CT out[4][3]) {
     return right ? mean4(Ap, A, Bp, B) : mean4(A, Ap, B, Bp);
 }
 
-// Lazy level-5 nodes.  A smooth tile has no hole, so the fill never changes it, and its level-5 node matters only to
-// the coarse pass of a fraction with a tile without any valid pixel -- which most frames never run.  The tile
-// publishes kNodeLazy instead of building its pyramid; when a coarse pass needs the node (it lies under the first
-// valid ancestor of an invalid tile), one warp recomputes it: the tile's outputs again from the source colour (the
-// same arithmetic as smooth_column_t, so the same bits), then the same pyramid.
-constexpr float kNodeLazy = 2.0f;    // .w of a valid node that is not computed
-constexpr float kNodeNeeded = 3.0f;  // .w of a lazy node the coarse pass needs
+// The lazy smooth node, recomputed by one warp: the tile's outputs again from the source colour (the same arithmetic
+// as smooth_column_t, so the same bits), then the same pyramid.
+
+template <typename CT> __device__ __forceinline__ float load_out(const CT *q);
+template <> __device__ __forceinline__ float load_out<float>(const float *q) { return __ldcg(q); }
+template <> __device__ __forceinline__ float load_out<__half>(const __half *q) {
+    return __half2float(__ushort_as_half(__ldcg(reinterpret_cast<const unsigned short *>(q))));
+}
+
+// The level-5 node of a tile-fraction without a hole from its stored outputs (one warp): the 2 x 2 blocks, the
+// order and the levels of fill_store_block, warp row w of the group as loop step w (a pixel outside the frame is
+// invalid, as in the gather), so the same bits.
+template <typename CT>
+__device__ float4 output_node(const TileParams &p, int tile, int kk, float4 *l2) {
+    const int lane = threadIdx.x & 31, bx = lane & 15;
+    const int X0 = (tile % p.n5x) * kFillTile, Y0 = (tile / p.n5x) * kFillTile;
+    const size_t plane = (size_t)p.W * p.H;
+    const CT *oc = (const CT *)p.out_color[kk];
+#pragma unroll 1
+    for (int w = 0; w < kFillTile / 4; ++w) {
+        const int TX = X0 + 2 * bx, TY = Y0 + 2 * (2 * w + (lane >> 4));
+        float4 c[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int x = TX + (t & 1), y = TY + (t >> 1);
+            c[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (x < p.W && y < p.H) {
+                const size_t q = (size_t)y * p.W + x;
+                c[t] = make_float4(load_out<CT>(oc + q), load_out<CT>(oc + plane + q), load_out<CT>(oc + 2 * plane + q),
+                                   1.0f);
+            }
+        }
+        const float4 n1 = mean4(c[0], c[1], c[2], c[3]);
+        const float4 a1 = shfl4_xor(n1, 1), a16 = shfl4_xor(n1, 16), a17 = shfl4_xor(n1, 17);
+        const float4 n2o = mean4(n1, a1, a16, a17);
+        if ((lane & 17) == 0) l2[w * 8 + (lane >> 1)] = n2o;
+    }
+    __syncwarp();
+    float4 l3, l4, l5;
+    upper_levels(l2, l3, l4, l5);
+    __syncwarp();
+    return l5;
+}
 
 template <typename CT>
 __device__ float4 smooth_node(const TileParams &p, int tile, int kk, float4 *l2) {
@@ -1067,11 +1123,6 @@ __device__ inline void coarse_levels(const float4 *nodes, float4 *cz, int n5x, i
 }
 
 // Coarse levels of the pyramid and the value of every tile without a valid pixel (all consumer threads).  Lazy
-// level-5 nodes are computed first where a fill value depends on them: under the first valid ancestor of some tile
-// without a valid pixel.  scratch: 64 float4 per consumer warp of shared memory.
-// (Not inlined, like the fix-up slice: the engine's throughput depends on how compact the code of its frequent
-// items stays in the instruction cache.)
-// Coarse levels of the pyramid and the value of every tile without a valid pixel (all consumer threads).  Lazy
 // level-5 nodes are computed first where a fill value depends on them: in the subtree of the first valid ancestor
 // of some tile without a valid pixel.  That ancestor is found without the pyramid: an ancestor d levels above
 // level 5 is valid when a level-5 node of its 2^d x 2^d block is (a lazy node is valid).  scratch: 64 float4 per
@@ -1102,8 +1153,9 @@ static __device__ __noinline__ void engine_coarse_pass(const TileParams &p, floa
                 if (!__any_sync(0xFFFFFFFFu, valid)) continue;
                 for (int c = lane; c < bw * bh; c += 32) {
                     float *w = &nodes[(by0 + c / bw) * p.n5x + bx0 + c % bw].w;
-                    if (__ldcg(w) == kNodeLazy) {
-                        *w = kNodeNeeded;
+                    const float lw = __ldcg(w);
+                    if (lw == kNodeLazy || lw == kNodeLazyOut) {
+                        *w = lw == kNodeLazy ? kNodeNeeded : kNodeNeededOut;
                         any = true;
                     }
                 }
@@ -1116,12 +1168,17 @@ static __device__ __noinline__ void engine_coarse_pass(const TileParams &p, floa
             float4 *l2 = scratch + 64 * wid;
             for (int base = 32 * wid; base < n5; base += 32 * kConsumerWarps) {
                 const int i = base + lane;
-                unsigned m = __ballot_sync(0xFFFFFFFFu, i < n5 && __ldcg(&nodes[i].w) == kNodeNeeded);
+                const float nw = i < n5 ? __ldcg(&nodes[i].w) : 0.0f;
+                unsigned m = __ballot_sync(0xFFFFFFFFu, nw == kNodeNeeded || nw == kNodeNeededOut);
+                const unsigned mo = __ballot_sync(0xFFFFFFFFu, nw == kNodeNeededOut);
                 while (m) {
-                    const int t = base + __ffs(m) - 1;
+                    const int b = __ffs(m) - 1, t = base + b;
                     m &= m - 1u;
-                    const float4 v =
-                        cdt == EXW_F16 ? smooth_node<__half>(p, t, kk, l2) : smooth_node<float>(p, t, kk, l2);
+                    float4 v;
+                    if (mo & (1u << b))
+                        v = cdt == EXW_F16 ? output_node<__half>(p, t, kk, l2) : output_node<float>(p, t, kk, l2);
+                    else
+                        v = cdt == EXW_F16 ? smooth_node<__half>(p, t, kk, l2) : smooth_node<float>(p, t, kk, l2);
                     if (lane == 0) nodes[t] = v;
                 }
             }
@@ -1287,7 +1344,7 @@ __device__ __forceinline__ void tile_group(EngineSmem &s, const TileSlot &sl, in
         }
     }
     if (FILL) {
-        fill_store_block<CT>(s, p, d, oc, om, g, kk, tile, buf, TX, TY, c, m, vec, mode >= 1 && mode <= 3);
+        fill_store_block<CT>(s, p, d, oc, om, g, kk, tile, buf, TX, TY, c, m, vec);
     } else {
         const bool all[4] = {true, true, true, true};
         store_block<CT>(d, oc, om, TX, TY, c, m, all, vec);
