@@ -502,12 +502,14 @@ def exw_l2_loss_grad(out, target, mask, grad_out=None, loss=None, stream=None):
 def frame_stats(ws, frame: int = 0) -> dict:
     """Diagnostics an exw_extrapolate call leaves in its workspace for source frame ``frame``: tiles per staging
     mode (smooth uniform motion / other uniform motion / one window for all fractions / one per fraction / global
-    memory / nothing lands) and, per fraction, tiles without any valid pixel.  Reads the 128-byte frame header at
-    byte 256 + 128 * frame (see csrc/exw_internal.h)."""
+    memory / nothing lands), per fraction, tiles without any valid pixel, and the lazy level-5 nodes the coarse
+    passes computed (smooth tiles from their source, other tiles without a hole from their stored outputs).  Reads
+    the 128-byte frame header at byte 256 + 128 * frame (see csrc/exw_internal.h)."""
     words = ws[256 + 128 * frame: 256 + 128 * (frame + 1)].view(torch.int32).cpu().tolist()
     return {"tiles_smooth": words[15], "tiles_uniform": words[10], "tiles_window_all": words[11],
             "tiles_window_each": words[12], "tiles_global": words[13], "tiles_nothing_lands": words[14],
-            "tiles_without_valid_pixel": words[5:8]}
+            "tiles_without_valid_pixel": words[5:8],
+            "lazy_nodes_computed": {"smooth": words[18], "from_outputs": words[19]}}
 
 
 def exw_device_status(ws, stream=None) -> int:

@@ -1179,7 +1179,10 @@ static __device__ __noinline__ void engine_coarse_pass(const TileParams &p, floa
                         v = cdt == EXW_F16 ? output_node<__half>(p, t, kk, l2) : output_node<float>(p, t, kk, l2);
                     else
                         v = cdt == EXW_F16 ? smooth_node<__half>(p, t, kk, l2) : smooth_node<float>(p, t, kk, l2);
-                    if (lane == 0) nodes[t] = v;
+                    if (lane == 0) {
+                        nodes[t] = v;
+                        atomicAdd(&p.fh->nlazy[(mo >> b) & 1u], 1u);
+                    }
                 }
             }
             __threadfence_block();

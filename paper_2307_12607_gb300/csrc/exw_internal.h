@@ -44,7 +44,8 @@ struct FrameHeader {
     uint32_t nmode[6];     // tiles done per plan mode (TilePlan::mode)
     uint32_t bdone;        // batched path: bounds regions finished
     uint32_t pdone;        // batched path: plan groups finished
-    uint32_t pad[14];
+    uint32_t nlazy[2];     // lazy level-5 nodes a coarse pass computed: smooth tiles, others (from their outputs)
+    uint32_t pad[12];
 };
 static_assert(sizeof(FrameHeader) == 128, "FrameHeader is 128 bytes");
 

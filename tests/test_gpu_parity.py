@@ -263,10 +263,13 @@ def test_smooth_tiles_every_residual_sign(b, pan, dtype):
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float16])
 @pytest.mark.parametrize("hole", [(128, 256, 64, 160), (0, 384, 0, 256), (32, 480, 96, 168)])
-def test_lazy_smooth_nodes_under_large_holes(b, dtype, hole):
-    # smooth tiles (one motion over a smooth surface) do not build their pyramid; when a fraction has tiles without
-    # any valid pixel, the coarse pass recomputes the smooth tiles' level-5 nodes it needs -- up to most of the frame
-    # when the hole covers three quarters of it -- and the fill must equal the staged fill bit for bit
+@pytest.mark.parametrize("motion", ["uniform", "varying"])
+def test_lazy_nodes_under_large_holes(b, dtype, hole, motion):
+    # tiles without a hole do not build their pyramid; when a fraction has tiles without any valid pixel, the coarse
+    # pass computes the level-5 nodes it needs -- up to most of the frame when the hole covers three quarters of it:
+    # a smooth tile's (one motion over a smooth surface) from its source colour, another tile's (a motion that
+    # varies from pixel to pixel: one-window splat tiles) from its stored outputs -- and the fill must equal the
+    # staged fill bit for bit
     W, H = 512, 256
     rng = np.random.default_rng(sum(hole))
     color = rng.uniform(size=(3, H, W)).astype(np.float32).astype(dtype)
@@ -275,13 +278,23 @@ def test_lazy_smooth_nodes_under_large_holes(b, dtype, hole):
     x0, x1, y0, y1 = hole
     depth[y0:y1, x0:x1] = np.nan                      # sources that never land: whole tiles without a valid pixel
     mv = np.empty((2, H, W), np.float32)
-    mv[0], mv[1] = 1.3, -0.7
+    if motion == "uniform":
+        mv[0], mv[1] = 1.3, -0.7
+    else:
+        mv[0], mv[1] = 1.3 + 0.002 * xx, -0.7 + 0.001 * yy
     c, d, m = dev(color), dev(depth), dev(mv)
     ws = b.workspace(b.exw_workspace_bytes(b.OP_EXTRAPOLATE, W, H, b.F16 if dtype == np.float16 else b.F32, 1, 3),
                      c.device)
     out, mask = b.exw_extrapolate(c, d, m, fill=True, ws=ws)
     st = b.frame_stats(ws)
-    assert st["tiles_smooth"] > 0 and min(st["tiles_without_valid_pixel"]) > 0
+    lazy = st["lazy_nodes_computed"]
+    assert min(st["tiles_without_valid_pixel"]) > 0 and lazy["from_outputs"] > 0
+    if motion == "uniform":
+        assert st["tiles_smooth"] > 0 and st["tiles_uniform"] > 0
+        if hole == (0, 384, 0, 256):  # the ancestors of the hole over three quarters of the frame hold smooth tiles
+            assert lazy["smooth"] > 0
+    else:
+        assert st["tiles_window_all"] > 0
     iv = torch.int16 if dtype == np.float16 else torch.int32
     for j in range(3):
         keys = b.exw_splat_motion(d, m, j + 1, 4)
