@@ -844,6 +844,28 @@ __device__ __forceinline__ void upper_levels(const float4 *l2, float4 &l3, float
     l5 = mean4(shfl4_idx(l4, 0), shfl4_idx(l4, 1), shfl4_idx(l4, 2), shfl4_idx(l4, 3));
 }
 
+// upper_levels through shared memory, for the fill of a tile: l2 the 64 level-2 nodes, up 20 float4 of the warp's
+// own scratch (level 3, then level 4).  Every lane returns l5, the level-3 node (w >> 1, bx >> 2) and the level-4
+// node (w >> 2, bx >> 3) above its block; the same nodes and order as upper_levels.
+__device__ __forceinline__ void upper_levels_smem(const float4 *l2, float4 *up, int w, int bx, float4 &v3, float4 &v4,
+                                                  float4 &l5) {
+    const int lane = threadIdx.x & 31;
+    if (lane < 16) {
+        const float4 *c = l2 + (2 * (lane >> 2)) * 8 + 2 * (lane & 3);
+        up[lane] = mean4(c[0], c[1], c[8], c[9]);
+    }
+    __syncwarp();
+    if (lane < 4) {
+        const int b4 = 8 * (lane >> 1) + 2 * (lane & 1);
+        up[16 + lane] = mean4(up[b4], up[b4 + 1], up[b4 + 4], up[b4 + 5]);
+    }
+    __syncwarp();
+    l5 = mean4(up[16], up[17], up[18], up[19]);
+    v3 = up[(w >> 1) * 4 + (bx >> 2)];
+    v4 = up[16 + (w >> 2) * 2 + (bx >> 3)];
+    __syncwarp();  // every read of the scratch before the warp's next use of it
+}
+
 template <typename CT>
 __device__ __forceinline__ void store_block(const FrameDims &p, CT *oc, uint8_t *om, int TX, int TY, const float4 c[4],
                                             const uint8_t m[4], const bool write[4], bool vec) {
@@ -936,37 +958,40 @@ __device__ __forceinline__ void fill_store_block(EngineSmem &s, const TileParams
         if (tg == 0) publish_node(p, make_float4(0.f, 0.f, 0.f, kNodeLazyOut), kk, tile);
         return;
     }
+    // level 1 of the group's 2 x 2 blocks in shared memory (the splat's candidate list is free until the next
+    // slot's vote), thread tg = block (tg & 15, tg >> 4); level 2 from four of them
     const float4 n1 = mean4(c[0], c[1], c[2], c[3]);
-    const float4 a1 = shfl4_xor(n1, 1), a16 = shfl4_xor(n1, 16), a17 = shfl4_xor(n1, 17);
-    const float4 n2o = mean4(n1, a1, a16, a17);  // meaningful on lanes with even block x and even block y
+    float4 *l1 = reinterpret_cast<float4 *>(s.cand) + g * kGroupThreads;
+    l1[tg] = n1;
+    __syncwarp();
     float4 *l2 = s.l2[g][buf];
-    if ((lane & 17) == 0) l2[w * 8 + (lane >> 1)] = n2o;
+    if ((lane & 17) == 0) l2[w * 8 + (lane >> 1)] = mean4(n1, l1[tg + 1], l1[tg + 16], l1[tg + 17]);
     if (!holes && w != 0) {  // needs no upper level
         asm volatile("bar.arrive %0, %1;" ::"r"(2 + g), "r"(kGroupThreads) : "memory");
         store_block<CT>(d, oc, om, TX, TY, c, m, all, vec);
         return;
     }
     bar_sync(2 + g, kGroupThreads);
+    float4 *up = l1 + 32 * w;  // the warp's level-1 slots, read by no one after the barrier: levels 3 and 4
+    const int bx = lane & 15;
     if (!holes) {
         if (w == 0) {
-            float4 l3, l4, l5;
-            upper_levels(l2, l3, l4, l5);
+            float4 v3, v4, l5;
+            upper_levels_smem(l2, up, w, bx, v3, v4, l5);
             if (lane == 0) publish_node(p, l5, kk, tile);
         }
         store_block<CT>(d, oc, om, TX, TY, c, m, all, vec);
         return;
     }
-    const float4 n2 = shfl4_idx(n2o, lane & ~17);
+    const float4 n2 = l2[w * 8 + (bx >> 1)];  // level 2 of this thread's block
     bool deep = false;  // a hole whose level-1 and level-2 ancestors are both invalid
 #pragma unroll
     for (int t = 0; t < 4; ++t) deep = deep || (m[t] != 0 && n1.w == 0.0f && n2.w == 0.0f);
-    float4 l3 = n2, l4 = n2, l5 = n2;
-    if (w == 0 || __any_sync(0xFFFFFFFFu, deep)) upper_levels(l2, l3, l4, l5);
+    // push: first valid ancestor (tile rows 4w..4w+3: level-3 node (w >> 1, bx >> 2), level-4 (w >> 2, bx >> 3));
+    // without a deep hole in the warp levels 3-5 are not read
+    float4 v3 = n2, v4 = n2, l5 = n2;
+    if (w == 0 || __any_sync(0xFFFFFFFFu, deep)) upper_levels_smem(l2, up, w, bx, v3, v4, l5);
     if (w == 0 && lane == 0) publish_node(p, l5, kk, tile);
-    // push: first valid ancestor (tile rows 4w..4w+3: level-3 node (w >> 1, bx >> 2), level-4 (w >> 2, bx >> 3))
-    const int bx = lane & 15;
-    const float4 v3 = shfl4_idx(l3, (w >> 1) * 4 + (bx >> 2));
-    const float4 v4 = shfl4_idx(l4, (w >> 2) * 2 + (bx >> 3));
     const float4 push = n1.w != 0.0f ? n1 : n2.w != 0.0f ? n2 : v3.w != 0.0f ? v3 : v4.w != 0.0f ? v4 : l5;
     bool write[4];
 #pragma unroll
