@@ -238,18 +238,28 @@ __device__ inline void engine_producer(EngineSmem &s, const EngineParams &ep) {
     int seg = 0;
     QueueItem cur = decode(ep, __shfl_sync(0xFFFFFFFFu, qa, 0), seg);
     int word = 0;
-    bool have_word = false;
+    bool have_word = false, have_desc = false;
+    uint4 desc0 = make_uint4(0u, 0u, 0u, 0u), desc1 = desc0;  // the current item's candidates (look-ahead)
     int copied0 = -1, copied1 = -1;  // stream whose parameters slot 0 / slot 1 holds
     for (uint32_t i = 0;; ++i) {
         const int b = (int)(i & 1u);
         const QueueItem nxt = decode(ep, cur.item < ep.total ? __shfl_sync(0xFFFFFFFFu, qb, 0) : ep.total, seg);
         if (lane == 0 && nxt.item < ep.total) qb = (int)atomicAdd(ep.queue, 1u);
         int nword = 0;
-        bool nhave = false;
+        bool nhave = false, nhave_desc = false;
+        uint4 ndesc0 = make_uint4(0u, 0u, 0u, 0u), ndesc1 = ndesc0;
         if (nxt.item < ep.total && nxt.stage == 2 && (planned & (1ull << nxt.stream))) {
-            nword = lane < kWords ? __ldcg(reinterpret_cast<const int *>(ep.st[nxt.stream].p.plans + nxt.local) + lane)
-                                  : 0;
+            const TileParams &np = ep.st[nxt.stream].p;
+            nword = lane < kWords ? __ldcg(reinterpret_cast<const int *>(np.plans + nxt.local) + lane) : 0;
             nhave = true;
+            // and its splat candidates (what the next slot copies into shared memory)
+            const int nm = __shfl_sync(0xFFFFFFFFu, nword, 0), nd = __shfl_sync(0xFFFFFFFFu, nword, 3);
+            if (nm >= 1 && nm <= 3 && nd > 0) {
+                const uint4 *src = reinterpret_cast<const uint4 *>(np.pdesc + (size_t)nxt.local * kPlanDesc);
+                if (lane < nd) ndesc0 = __ldcg(src + lane);
+                if (lane + 32 < nd) ndesc1 = __ldcg(src + lane + 32);
+                nhave_desc = true;
+            }
         }
         const int item = cur.item, stream = cur.stream, stage = cur.stage, local = cur.local;
         const EngineStream &st = ep.st[stream];
@@ -316,18 +326,50 @@ __device__ inline void engine_producer(EngineSmem &s, const EngineParams &ep) {
         bool pair = false;
         if (kind == kSlotTile) {
             if (!have_word) word = lane < kWords ? __ldcg(reinterpret_cast<const int *>(p.plans + local) + lane) : 0;
-            if (lane < kWords) reinterpret_cast<int *>(&sl.plan)[lane] = word;
             mode = __shfl_sync(0xFFFFFFFFu, word, 0);
             wx0 = __shfl_sync(0xFFFFFFFFu, word, 1);
             wy0 = __shfl_sync(0xFFFFFFFFu, word, 2);
             const int ndesc = __shfl_sync(0xFFFFFFFFu, word, 3);
-            const int X0 = (local % p.n5x) * kFillTile, Y0 = (local / p.n5x) * kFillTile;
             if (!st.tma && mode != 4) mode = 3;  // no window: every tile reads global memory
+            // two smooth tiles in a row (the second one's plan already read): one slot, one pass of the pipeline
+            pair = ep.pair_smooth && mode == 5 && nhave && nxt.stream == stream && nxt.stage == 2 &&
+                   __shfl_sync(0xFFFFFFFFu, nword, 0) == 5;
+            if (pair) {
+                wx02 = __shfl_sync(0xFFFFFFFFu, nword, 1);
+                wy02 = __shfl_sync(0xFFFFFFFFu, nword, 2);
+            }
+            // the window copies first: they land while the rest of the slot is written (the slot's arrival, last,
+            // completes the phase together with their bytes)
+            if (lane == 0 && (mode == 0 || mode == 1 || mode == 5)) {
+                const CUtensorMap *m = ep.maps[stream];
+                unsigned char *wb = s.win[b];
+                // a window holds npx pixels: depth (4 B), motion (8 B), colour (3 c B) planes in this order
+                const int npx = st.cdt == EXW_F16 ? WS::xf16 * WS::yf16 : WS::xf32 * WS::yf32;
+                const uint32_t cbytes = (uint32_t)npx * 3u * (st.cdt == EXW_F16 ? 2u : 4u);
+                fence_proxy_async_smem();
+                if (mode == 5) {  // smooth: only the colour is read, at the buffer's start
+                    mbar_expect_tx(&s.full[b], pair ? 2u * cbytes : cbytes);
+                    tma_load_3d(wb, &m[0], wx0, wy0, 0, &s.full[b]);
+                    if (pair) tma_load_3d(wb + cbytes, &m[0], wx02, wy02, 0, &s.full[b]);
+                } else {
+                    mbar_expect_tx(&s.full[b], (uint32_t)kWindowBytes);
+                    tma_load_2d(wb, &m[1], wx0, wy0, &s.full[b]);
+                    tma_load_3d(wb + 4 * npx, &m[2], wx0, wy0, 0, &s.full[b]);
+                    tma_load_3d(wb + 12 * npx, &m[0], wx0, wy0, 0, &s.full[b]);
+                }
+            }
+            if (lane < kWords) reinterpret_cast<int *>(&sl.plan)[lane] = word;
+            const int X0 = (local % p.n5x) * kFillTile, Y0 = (local / p.n5x) * kFillTile;
             if (mode >= 1 && mode <= 3 && ndesc > 0) {  // the splat's candidates, as the plan found them
-                const uint4 *src = reinterpret_cast<const uint4 *>(p.pdesc + (size_t)local * kPlanDesc);
                 uint4 *dst = reinterpret_cast<uint4 *>(s.pdesc[b]);
-                if (lane < ndesc) dst[lane] = __ldcg(src + lane);
-                if (lane + 32 < ndesc) dst[lane + 32] = __ldcg(src + lane + 32);
+                if (have_desc) {  // loaded with the look-ahead
+                    if (lane < ndesc) dst[lane] = desc0;
+                    if (lane + 32 < ndesc) dst[lane + 32] = desc1;
+                } else {
+                    const uint4 *src = reinterpret_cast<const uint4 *>(p.pdesc + (size_t)local * kPlanDesc);
+                    if (lane < ndesc) dst[lane] = __ldcg(src + lane);
+                    if (lane + 32 < ndesc) dst[lane + 32] = __ldcg(src + lane + 32);
+                }
             }
             if (mode == 0 || mode == 5) {
                 const uint32_t umx = (uint32_t)__shfl_sync(0xFFFFFFFFu, word, 16);
@@ -335,15 +377,10 @@ __device__ inline void engine_producer(EngineSmem &s, const EngineParams &ep) {
                 if (lane < 8 * p.nfrac) uniform_frac(sl.u[lane >> 3], p, umx, umy, lane >> 3, lane & 7);
                 if (lane == 0) sl.N = uniform_sources(p, umx, umy, X0 - 1, Y0 - 1);
             }
-            // two smooth tiles in a row (the second one's plan already read): one slot, one pass of the pipeline
-            pair = ep.pair_smooth && mode == 5 && nhave && nxt.stream == stream && nxt.stage == 2 &&
-                   __shfl_sync(0xFFFFFFFFu, nword, 0) == 5;
             if (pair) {
                 const int X02 = (nxt.local % p.n5x) * kFillTile, Y02 = (nxt.local / p.n5x) * kFillTile;
                 const uint32_t umx = (uint32_t)__shfl_sync(0xFFFFFFFFu, nword, 16);
                 const uint32_t umy = (uint32_t)__shfl_sync(0xFFFFFFFFu, nword, 17);
-                wx02 = __shfl_sync(0xFFFFFFFFu, nword, 1);
-                wy02 = __shfl_sync(0xFFFFFFFFu, nword, 2);
                 if (lane < 8 * p.nfrac)
                     uniform_frac(sl.u2[lane >> 3], p, umx, umy, lane >> 3, lane & 7);
                 if (lane == 0) {
@@ -368,34 +405,20 @@ __device__ inline void engine_producer(EngineSmem &s, const EngineParams &ep) {
             sl.index = local;
             sl.cdt = st.cdt;
             if (kind == kSlotTile) atomicAdd(&p.fh->nmode[mode], pair ? 2u : 1u);
-            const CUtensorMap *m = ep.maps[stream];
-            unsigned char *wb = s.win[b];
-            // a window holds npx pixels: depth (4 B), motion (8 B), colour (3 c B) planes in this order
-            const int npx = st.cdt == EXW_F16 ? WS::xf16 * WS::yf16 : WS::xf32 * WS::yf32;
-            const uint32_t cbytes = (uint32_t)npx * 3u * (st.cdt == EXW_F16 ? 2u : 4u);
-            if (kind == kSlotTile && mode == 5) {  // smooth: only the colour is read, at the buffer's start
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&s.full[b], pair ? 2u * cbytes : cbytes);
-                tma_load_3d(wb, &m[0], wx0, wy0, 0, &s.full[b]);
-                if (pair) tma_load_3d(wb + cbytes, &m[0], wx02, wy02, 0, &s.full[b]);
-            } else if (kind == kSlotTile && (mode == 0 || mode == 1)) {
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&s.full[b], (uint32_t)kWindowBytes);
-                tma_load_2d(wb, &m[1], wx0, wy0, &s.full[b]);
-                tma_load_3d(wb + 4 * npx, &m[2], wx0, wy0, 0, &s.full[b]);
-                tma_load_3d(wb + 12 * npx, &m[0], wx0, wy0, 0, &s.full[b]);
-            } else {
-                mbar_arrive(&s.full[b]);
-            }
+            mbar_arrive(&s.full[b]);
         }
         if (pair) {  // the second tile is taken: the item after it comes next
             cur = decode(ep, __shfl_sync(0xFFFFFFFFu, qb, 0), seg);
             if (lane == 0 && cur.item < ep.total) qb = (int)atomicAdd(ep.queue, 1u);
             have_word = false;
+            have_desc = false;
         } else {
             cur = nxt;
             word = nword;
             have_word = nhave;
+            have_desc = nhave_desc;
+            desc0 = ndesc0;
+            desc1 = ndesc1;
         }
     }
 }
