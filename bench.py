@@ -68,8 +68,8 @@ def dist_env():
 # capture (a smaller launch; the engine's traffic grows in proportion to the frames of a launch), with the hash of
 # the kernel's sources (KERNEL_SOURCES) it was taken on: reported only while they are unchanged, else null.
 MEASURED_TRAFFIC = {
-    ("exw_engine", "sequence_1080p_fp32"): ((236.007e6 + 279.348e6) / 4, "cafc3368605ea736"),
-    ("exw_engine", "warp_4k_fp16"): (105.188e6 + 129.443e6, "cafc3368605ea736"),
+    ("exw_engine", "sequence_1080p_fp32"): ((236.035e6 + 279.950e6) / 4, "f230cb54b87b7095"),
+    ("exw_engine", "warp_4k_fp16"): (105.064e6 + 129.609e6, "f230cb54b87b7095"),
     ("exw_train", "fwd_bwd_1080p"): (215.143e6 + 27.901e6, "b0b6ea69f6dae11e"),
 }
 
