@@ -1463,7 +1463,12 @@ __device__ void engine_consumer(EngineSmem &s, uint32_t *status) {
         }
         if (ok && mode >= 1 && mode <= 3 && g < p.nfrac)
             for (int r = tg; r < kRegionN; r += kGroupThreads) s.key[g][r] = kKeyEmpty;
-        if (bar_red_or(kBarConsumers, kConsumerThreads, !ok)) {
+        // The consumer-wide vote: every thread agrees that the slot arrived, and every group has finished the slots
+        // before it.  A smooth tile's slot shares nothing between the groups (no keys, candidates, pyramid or bounds
+        // scratch, no barrier), so its groups go on without it; a thread whose wait ran out meets the others at the
+        // next slot's vote, which every other kind of slot (the end included) takes.
+        const bool solo = kind == kSlotTile && mode == 5;
+        if (!solo && bar_red_or(kBarConsumers, kConsumerThreads, !ok)) {
             if (tid == 0) {  // (the slot may never have been written: its parameters are not used here)
                 atomicCAS(status, 0u, (uint32_t)EXW_ERR_TIMEOUT);
                 *(volatile int *)&s.abort = 1;
