@@ -31,7 +31,8 @@ constexpr int kGroupThreads = 256;                          // one fraction: 16 
 constexpr int kConsumerThreads = kMaxFrac * kGroupThreads;  // 768
 constexpr int kConsumerWarps = kConsumerThreads / 32;       // 24
 constexpr int kEngineThreads = kConsumerThreads + 32;       // + the producer warp
-constexpr int kBarConsumers = 1;                            // named barriers: 1 all consumers, 2 + g group g
+constexpr int kBarConsumers = 1;                            // named barriers: 1 all consumers, 2 + g group g,
+constexpr int kBarBounds = 11;                              // 5 + h half group h (bounds), 11 + g group g (bounds)
 constexpr int kMaxStreams = 48;                             // streams per launch (kernel-parameter space)
 constexpr int kRegionsPerItem = 2 * kMaxFrac;               // a bounds item: one region per half group (4 warps)
 constexpr int kPlansPerItem = kConsumerWarps;               // a plan item: one tile per consumer warp
@@ -1464,10 +1465,13 @@ __device__ void engine_consumer(EngineSmem &s, uint32_t *status) {
         if (ok && mode >= 1 && mode <= 3 && g < p.nfrac)
             for (int r = tg; r < kRegionN; r += kGroupThreads) s.key[g][r] = kKeyEmpty;
         // The consumer-wide vote: every thread agrees that the slot arrived, and every group has finished the slots
-        // before it.  A smooth tile's slot shares nothing between the groups (no keys, candidates, pyramid or bounds
-        // scratch, no barrier), so its groups go on without it; a thread whose wait ran out meets the others at the
-        // next slot's vote, which every other kind of slot (the end included) takes.
-        const bool solo = kind == kSlotTile && mode == 5;
+        // before it.  Slots that share nothing between the groups and use no barrier that an earlier slot's warps may
+        // still be due at (the fill's group barriers) -- smooth tiles (each group its own fraction, no barrier),
+        // bounds items (each half group its own region, partials and barriers), plan items (a warp per tile),
+        // fix-up slices after the first (plain stores) -- go on without it; a thread whose wait ran out meets the
+        // others at the next slot's vote, which every other kind of slot (the end included) takes.
+        const bool solo = (kind == kSlotTile && mode == 5) || kind == kSlotBounds || kind == kSlotPlans ||
+                          (kind == kSlotFixup && sl.index != 0);
         if (!solo && bar_red_or(kBarConsumers, kConsumerThreads, !ok)) {
             if (tid == 0) {  // (the slot may never have been written: its parameters are not used here)
                 atomicCAS(status, 0u, (uint32_t)EXW_ERR_TIMEOUT);
@@ -1492,7 +1496,9 @@ __device__ void engine_consumer(EngineSmem &s, uint32_t *status) {
                     if (th == 0) atomicAdd(&p.fh->bdone, 1u);
                 }
             }
-            bar_sync(2 + g, kGroupThreads);  // the group's bounds partials are free again
+            // the group's bounds partials are free again (its own barrier: a bounds slot takes no vote, and a warp may
+            // still be due at barrier 2 + g of an earlier tile, where warps without holes only arrive)
+            bar_sync(kBarBounds + g, kGroupThreads);
         } else if (kind == kSlotPlans) {
             const int tile = sl.index * kPlansPerItem + w;
             if (tile < p.n5x * p.n5y) {
