@@ -32,13 +32,19 @@ constexpr int kConsumerThreads = kMaxFrac * kGroupThreads;  // 768
 constexpr int kConsumerWarps = kConsumerThreads / 32;       // 24
 constexpr int kEngineThreads = kConsumerThreads + 32;       // + the producer warp
 constexpr int kBarConsumers = 1;                            // named barriers: 1 all consumers, 2 + g group g,
-constexpr int kBarBounds = 11;                              // 5 + h half group h (bounds), 11 + g group g (bounds)
+constexpr int kBarBounds = 11;  // 5 + h half group h (bounds), 11 + g group g (bounds)
 constexpr int kMaxStreams = 48;                             // streams per launch (kernel-parameter space)
 constexpr int kRegionsPerItem = 2 * kMaxFrac;               // a bounds item: one region per half group (4 warps)
 constexpr int kPlansPerItem = kConsumerWarps;               // a plan item: one tile per consumer warp
 constexpr uint32_t kFixupItems = 8u;                        // fix-up items per stream (with the fill)
-constexpr uint32_t kStageWaitLimit = 1u << 22;              // iterations (>= 64 ns each) before a wait gives up
-constexpr uint32_t kInjectedWaitLimit = 20000u;             // the injected fault gives up after a few ms
+// Every wait of the engine is bounded in time.  The producer gives up on a stage or on a buffer's release after
+// kProducerWaitNs, and then hands no further slot over (it raises the abort flag); a consumer gives up on a slot
+// only after kConsumerWaitNs, four times longer, and waits for a slot only once the producer has handed over the
+// previous one.  So a consumer never gives up on a slot the producer still hands over: all consumers take the same
+// slots, which lets the slots without a consumer-wide vote use group barriers.
+constexpr uint64_t kProducerWaitNs = 1000000000ull;
+constexpr uint64_t kConsumerWaitNs = 4000000000ull;
+constexpr uint64_t kInjectedWaitNs = 5000000ull;  // the injected fault gives up after 5 ms
 
 // Slot kinds.
 constexpr int kSlotEnd = 0, kSlotBounds = 1, kSlotPlans = 2, kSlotTile = 3, kSlotFixup = 4;
@@ -145,16 +151,17 @@ __device__ __forceinline__ bool bar_red_or(int id, int n, bool v) {
 __device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mbar)) : "memory");
 }
-// Bounded wait on an mbarrier phase that also gives up when another warp raised the abort flag.
-__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *mbar, uint32_t parity, const volatile int *abort) {
-    for (uint32_t i = 1; i <= kWaitLimit; ++i) {
+// Wait on an mbarrier phase for at most limit_ns; gives up early when another warp raised the abort flag.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *mbar, uint32_t parity, const volatile int *abort,
+                                                   uint64_t limit_ns) {
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t i = 1;; ++i) {
         if (mbar_try_wait(mbar, parity)) return true;
         if ((i & 15u) == 0u) {
-            if (*abort) return false;
+            if (*abort || globaltimer_ns() - t0 > limit_ns) return false;
             __nanosleep(64);
         }
     }
-    return false;
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -195,14 +202,14 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
 
 // Lane 0 waits until *counter >= target; false when the limit ran out, the workspace status reports an error or
 // the CTA aborts.
-__device__ __forceinline__ bool stage_wait(const uint32_t *counter, uint32_t target, uint32_t limit,
+__device__ __forceinline__ bool stage_wait(const uint32_t *counter, uint32_t target, uint64_t limit_ns,
                                            const uint32_t *status, const volatile int *abort) {
-    for (uint32_t i = 0; i < limit; ++i) {
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t i = 0;; ++i) {
         if (ld_acquire(counter) >= target) return true;
-        if (*(const volatile uint32_t *)status != 0u || *abort) return false;
+        if (*(const volatile uint32_t *)status != 0u || *abort || globaltimer_ns() - t0 > limit_ns) return false;
         __nanosleep(i < 64 ? 32 : 256);
     }
-    return false;
 }
 
 struct QueueItem {
@@ -281,7 +288,7 @@ __device__ inline void engine_producer(EngineSmem &s, const EngineParams &ep) {
                                         : stage == 2 ? (uint32_t)st.ntiles + (injected ? 1u : 0u)
                                         : first_fix  ? (uint32_t)st.ntiles * (uint32_t)p.nfrac : 1u;
                 if (lane == 0)
-                    ok = stage_wait(counter, target, injected ? kInjectedWaitLimit : kStageWaitLimit, ep.status,
+                    ok = stage_wait(counter, target, injected ? kInjectedWaitNs : kProducerWaitNs, ep.status,
                                     &s.abort);
                 ok = __shfl_sync(0xFFFFFFFFu, (int)ok, 0) != 0;
                 if (ok && !first_fix) {
@@ -292,7 +299,7 @@ __device__ inline void engine_producer(EngineSmem &s, const EngineParams &ep) {
             }
         }
         if (ok && i >= 2) {  // the consumers' release of this buffer's previous use
-            if (lane == 0) ok = mbar_wait_or_abort(&s.empty[b], ((i >> 1) - 1u) & 1u, &s.abort);
+            if (lane == 0) ok = mbar_wait_or_abort(&s.empty[b], ((i >> 1) - 1u) & 1u, &s.abort, kProducerWaitNs);
             ok = __shfl_sync(0xFFFFFFFFu, (int)ok, 0) != 0;
         }
         if (!ok) {
@@ -1439,17 +1446,7 @@ __device__ void engine_consumer(EngineSmem &s, uint32_t *status) {
         // the next item is not ready: count what this group published before blocking (the producer may be
         // waiting for exactly that count)
         if (FILL && tg == 0 && pend.n != 0u && !mbar_test_wait(&s.full[b], (i >> 1) & 1u)) pend.flush();
-        bool ok = false;
-        for (uint32_t it = 1; it <= kWaitLimit; ++it) {
-            if (mbar_try_wait(&s.full[b], (i >> 1) & 1u)) {
-                ok = true;
-                break;
-            }
-            if ((it & 15u) == 0u) {
-                if (*(volatile int *)&s.abort) break;
-                __nanosleep(64);
-            }
-        }
+        const bool ok = mbar_wait_or_abort(&s.full[b], (i >> 1) & 1u, &s.abort, kConsumerWaitNs);
         const TileSlot &sl = s.slot[b];
         const int kind = ok ? sl.kind : kSlotEnd;
         const int mode = kind == kSlotTile ? sl.plan.mode : -1;
