@@ -68,9 +68,9 @@ def dist_env():
 # capture (a smaller launch; the engine's traffic grows in proportion to the frames of a launch), with the hash of
 # the kernel's sources (KERNEL_SOURCES) it was taken on: reported only while they are unchanged, else null.
 MEASURED_TRAFFIC = {
-    ("exw_engine", "sequence_1080p_fp32"): ((236.035e6 + 279.950e6) / 4, "f230cb54b87b7095"),
-    ("exw_engine", "warp_4k_fp16"): (105.064e6 + 129.609e6, "f230cb54b87b7095"),
-    ("exw_train", "fwd_bwd_1080p"): (215.143e6 + 27.901e6, "b0b6ea69f6dae11e"),
+    ("exw_engine", "sequence_1080p_fp32"): ((236.082e6 + 279.961e6) / 4, "330b04cab1b3b6c0"),
+    ("exw_engine", "warp_4k_fp16"): (105.105e6 + 129.334e6, "330b04cab1b3b6c0"),
+    ("exw_train", "fwd_bwd_1080p"): (215.118e6 + 28.133e6, "5a89d921cf4509d2"),
 }
 
 
