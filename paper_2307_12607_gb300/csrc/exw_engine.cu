@@ -16,9 +16,11 @@ __global__ void __launch_bounds__(kEngineThreads, 1) engine_kernel(const __grid_
         fence_mbar_init();
         s.abort = 0;
     }
+    // both key sets start empty; a group empties its fraction's keys again after each gather from them
+    for (int r = threadIdx.x; r < 2 * kMaxFrac * kRegionN; r += blockDim.x) (&s.key[0][0][0])[r] = kKeyEmpty;
     __syncthreads();
     if (threadIdx.x >= kConsumerThreads) engine_producer<SHAPE>(s, ep);
-    else engine_consumer<FILL, SHAPE>(s, ep.status);
+    else engine_consumer<FILL, SHAPE>(s, ep);
 }
 
 template <bool FILL, int SHAPE>

@@ -89,8 +89,7 @@ __device__ __forceinline__ FrameDims dims_of(const TileParams &p) { return Frame
 
 // What the producer hands the consumers with each buffer.
 struct alignas(16) TileSlot {
-    TileParams p;             // the item's stream
-    int kind, stream, index, cdt;
+    int kind, stream, index, cdt;  // the stream's parameters are read from the launch's (ep.st[stream].p)
     TilePlan plan;            // tile: its plan (mode 3 for every tile of a stream without TMA windows)
     int X0, Y0;
     Rect N;                   // modes 0, 5: the source rectangle the fractions read
@@ -98,11 +97,15 @@ struct alignas(16) TileSlot {
     // mode 5: a second smooth tile of the same stream, the next in the queue, shares the slot (its colour window
     // follows the first one's in the buffer)
     int pair, index2, X02, Y02, wx02, wy02;
-    UniformFrac u2[kMaxFrac];
+    union {
+        SplatTile pdesc[kPlanDesc];  // modes 1-3: the plan's candidates of the tile
+        UniformFrac u2[kMaxFrac];    // mode 5, paired: the second tile's constants
+    };
 };
 
 constexpr int kWindowBytes = 64512;  // both window shapes (56 x 48 FP32, 64 x 56 FP16) hold 64,512 bytes
 static_assert(64 * 16 * kConsumerWarps <= kWindowBytes, "the coarse pass's per-warp scratch fits one buffer");
+static_assert(sizeof(SplatTile) == sizeof(float4), "the candidate list doubles as one float4 per consumer thread");
 static_assert(sizeof(Window<float, WinShape<0>::xf32, WinShape<0>::yf32>) == kWindowBytes &&
                   sizeof(Window<__half, WinShape<0>::xf16, WinShape<0>::yf16>) == kWindowBytes &&
                   sizeof(Window<float, WinShape<1>::xf32, WinShape<1>::yf32>) == kWindowBytes &&
@@ -111,16 +114,21 @@ static_assert(sizeof(Window<float, WinShape<0>::xf32, WinShape<0>::yf32>) == kWi
 
 struct EngineSmem {
     alignas(128) unsigned char win[2][kWindowBytes];  // TMA destinations, double-buffered
-    uint64_t key[kMaxFrac][kRegionN];                // region keys per fraction (modes 1-3)
-    float4 l2[kMaxFrac][2][64];                      // pyramid level 2 (8 x 8 nodes) per group, by tile parity
-    float4 bpart[kMaxFrac][64];                      // per group: partial bounds of a region
+    uint64_t key[2][kMaxFrac][kRegionN];             // region keys per fraction (modes 1-3), a set per splat slot parity
     TileSlot slot[2];                                // the item in each buffer
-    SplatTile cand[kConsumerThreads];                // candidate 8 x 8 source tiles of a splat
-    SplatTile pdesc[2][kPlanDesc];                   // the plan's candidates of the tile in each buffer
+    // A splat's candidate list; between splats per group 256 float4 of scratch (group g from float4 256 g): the fill's
+    // pyramid (32 per warp: level 1 of its blocks, then level 2 in the first 8 and levels 3-4 in the next 20) and a
+    // bounds item's partials (the first 64)
+    SplatTile cand[kConsumerThreads];
     uint32_t ncand;
+    uint32_t snext[2];                               // the next splat chunk of the tile in each buffer
     int abort;                                       // a bounded wait ran out: every warp leaves
     uint64_t full[2], empty[2];
 };
+
+// The shared memory stays within the 196 KB carve-out (with the 1 KB the system keeps per CTA): the next larger one
+// leaves 28 KB of L1 instead of 60, which measured 6% slower at 1080p.
+static_assert(sizeof(EngineSmem) <= 196 * 1024 - 1024, "the engine's shared memory fits the 196 KB carve-out");
 
 template <typename CT, int WX, int WY>
 __device__ __forceinline__ Window<CT, WX, WY> &window(EngineSmem &s, int b) {
@@ -231,8 +239,7 @@ __device__ __forceinline__ QueueItem decode(const EngineParams &ep, int item, in
 template <int SHAPE>
 __device__ inline void engine_producer(EngineSmem &s, const EngineParams &ep) {
     using WS = WinShape<SHAPE>;
-    constexpr int kWords = (int)(sizeof(TilePlan) / 4), kParamWords = (int)(sizeof(TileParams) / 4);
-    static_assert(sizeof(TileParams) % 4 == 0 && kParamWords <= 64, "two words per lane");
+    constexpr int kWords = (int)(sizeof(TilePlan) / 4);
     const int lane = threadIdx.x & 31;
     // streams whose previous stage is known complete (the injected fault makes stream 0's tiles wait)
     uint64_t planned = ep.ahead & (ep.inject ? ~1ull : ~0ull), bounded = ep.ahead, coarsed = 0ull;
@@ -248,7 +255,6 @@ __device__ inline void engine_producer(EngineSmem &s, const EngineParams &ep) {
     int word = 0;
     bool have_word = false, have_desc = false;
     uint4 desc0 = make_uint4(0u, 0u, 0u, 0u), desc1 = desc0;  // the current item's candidates (look-ahead)
-    int copied0 = -1, copied1 = -1;  // stream whose parameters slot 0 / slot 1 holds
     for (uint32_t i = 0;; ++i) {
         const int b = (int)(i & 1u);
         const QueueItem nxt = decode(ep, cur.item < ep.total ? __shfl_sync(0xFFFFFFFFu, qb, 0) : ep.total, seg);
@@ -321,14 +327,6 @@ __device__ inline void engine_producer(EngineSmem &s, const EngineParams &ep) {
             }
             return;
         }
-        if ((b ? copied1 : copied0) != stream) {  // the slot's parameters are another stream's
-            const int *pw = reinterpret_cast<const int *>(&p);
-            int *sw = reinterpret_cast<int *>(&sl.p);
-            sw[lane] = pw[lane];
-            if (lane + 32 < kParamWords) sw[lane + 32] = pw[lane + 32];
-            if (b) copied1 = stream;
-            else copied0 = stream;
-        }
         const int kind = stage == 0 ? kSlotBounds : stage == 1 ? kSlotPlans : stage == 2 ? kSlotTile : kSlotFixup;
         int mode = -1, wx0 = 0, wy0 = 0, wx02 = 0, wy02 = 0;
         bool pair = false;
@@ -369,7 +367,7 @@ __device__ inline void engine_producer(EngineSmem &s, const EngineParams &ep) {
             if (lane < kWords) reinterpret_cast<int *>(&sl.plan)[lane] = word;
             const int X0 = (local % p.n5x) * kFillTile, Y0 = (local / p.n5x) * kFillTile;
             if (mode >= 1 && mode <= 3 && ndesc > 0) {  // the splat's candidates, as the plan found them
-                uint4 *dst = reinterpret_cast<uint4 *>(s.pdesc[b]);
+                uint4 *dst = reinterpret_cast<uint4 *>(sl.pdesc);
                 if (have_desc) {  // loaded with the look-ahead
                     if (lane < ndesc) dst[lane] = desc0;
                     if (lane + 32 < ndesc) dst[lane + 32] = desc1;
@@ -412,6 +410,7 @@ __device__ inline void engine_producer(EngineSmem &s, const EngineParams &ep) {
             sl.stream = stream;
             sl.index = local;
             sl.cdt = st.cdt;
+            s.snext[b] = 0u;  // the splat's chunk claims start over
             if (kind == kSlotTile) atomicAdd(&p.fh->nmode[mode], pair ? 2u : 1u);
             mbar_arrive(&s.full[b]);
         }
@@ -663,60 +662,82 @@ __device__ __forceinline__ int describe_tiles(SplatTile *out, const TileParams &
 
 // Splat the pixels of rectangle U from the staged window for all fractions (all consumer threads): candidate
 // 8 x 8 tiles only, a warp per tile (two pixels per lane); a clean tile splats with its precomputed offsets.
+// Pixel q & 63 of candidate tile st (q >> 6 of the list), from the staged window, for every fraction it reaches.
 template <typename CT, int WX, int WY>
-__device__ __forceinline__ void engine_splat_window(EngineSmem &s, const TileParams &p, const FrameDims &d,
-                                                    const WinAcc<CT, WX, WY> &a, Rect U, int RX0, int RY0, int tid,
-                                                    const SplatTile *pre, int npre) {
-    // the plan's candidates landed with the slot; without them (too many) they are described here
-    const SplatTile *tiles = pre;
-    int nt = npre;
-    if (npre == 0) {
-        nt = describe_tiles(s.cand, p, d, U, RX0, RY0, tid);
-        tiles = s.cand;
-        bar_sync(kBarConsumers, kConsumerThreads);
-    }
-    // half a source tile per warp and round (its descriptor is one broadcast load), all warps busy
-    for (int q = tid; q < 64 * nt; q += kConsumerThreads) {
-        const SplatTile st = tiles[q >> 6];
-        if (!st.fm) continue;
-        {
-            const int x = 8 * st.bx + (q & 7), y = 8 * st.by + ((q >> 3) & 7);
-            if (x < U.x0 || x > U.x1 || y < U.y0 || y > U.y1) continue;
-            const int i = a.at(x, y);
-            const uint32_t db = __float_as_uint(a.w->depth[i]);
-            if (st.clean) {
-                const uint64_t kv = pack_key_local(db, x, y);
+__device__ __forceinline__ void splat_window_pixel(uint64_t (*key)[kRegionN], const FrameDims &d,
+                                                   const WinAcc<CT, WX, WY> &a, Rect U, const SplatTile &st, int q,
+                                                   int RX0, int RY0) {
+    if (!st.fm) return;
+    const int x = 8 * st.bx + (q & 7), y = 8 * st.by + ((q >> 3) & 7);
+    if (x < U.x0 || x > U.x1 || y < U.y0 || y > U.y1) return;
+    const int i = a.at(x, y);
+    const uint32_t db = __float_as_uint(a.w->depth[i]);
+    if (st.clean) {
+        const uint64_t kv = pack_key_local(db, x, y);
 #pragma unroll
-                for (int kk = 0; kk < kMaxFrac; ++kk) {
-                    if (!(st.fm & (1u << kk))) continue;
-                    const int gx = x + st.ox[kk], gy = y + st.oy[kk];
-                    if ((unsigned)gx >= (unsigned)d.W || (unsigned)gy >= (unsigned)d.H) continue;
-                    const int rx = gx - RX0, ry = gy - RY0;
-                    if ((unsigned)rx < (unsigned)kRegion && (unsigned)ry < (unsigned)kRegion)
-                        atomicMin((unsigned long long *)&s.key[kk][ry * kRegion + rx], (unsigned long long)kv);
-                }
-            } else {
-                engine_splat_pixel(s.key, d, x, y, db, __float_as_uint(a.w->mv[0][i]),
-                                   __float_as_uint(a.w->mv[1][i]), st.fm, RX0, RY0);
-            }
+        for (int kk = 0; kk < kMaxFrac; ++kk) {
+            if (!(st.fm & (1u << kk))) continue;
+            const int gx = x + st.ox[kk], gy = y + st.oy[kk];
+            if ((unsigned)gx >= (unsigned)d.W || (unsigned)gy >= (unsigned)d.H) continue;
+            const int rx = gx - RX0, ry = gy - RY0;
+            if ((unsigned)rx < (unsigned)kRegion && (unsigned)ry < (unsigned)kRegion)
+                atomicMin((unsigned long long *)&key[kk][ry * kRegion + rx], (unsigned long long)kv);
         }
+    } else {
+        engine_splat_pixel(key, d, x, y, db, __float_as_uint(a.w->mv[0][i]), __float_as_uint(a.w->mv[1][i]), st.fm,
+                           RX0, RY0);
+    }
+}
+
+// A warp's next chunk of 32 candidate pixels (lane 0 claims, every lane gets it).
+__device__ __forceinline__ int claim_chunk(uint32_t *next) {
+    int c = 0;
+    if ((threadIdx.x & 31) == 0) c = (int)atomicAdd(next, 1u);
+    return __shfl_sync(0xFFFFFFFFu, c, 0);
+}
+
+template <typename CT, int WX, int WY>
+__device__ __forceinline__ void engine_splat_window(EngineSmem &s, uint64_t (*key)[kRegionN], const TileParams &p,
+                                                    const FrameDims &d, const WinAcc<CT, WX, WY> &a, Rect U, int RX0,
+                                                    int RY0, int tid, const SplatTile *pre, int npre, uint32_t *next) {
+    if (npre == 0) {  // too many candidates for the plan: described here, half a tile per warp and round
+        const int nt = describe_tiles(s.cand, p, d, U, RX0, RY0, tid);
+        bar_sync(kBarConsumers, kConsumerThreads);
+        for (int q = tid; q < 64 * nt; q += kConsumerThreads) splat_window_pixel(key, d, a, U, s.cand[q >> 6], q, RX0, RY0);
+        return;
+    }
+    // the plan's candidates, in chunks of half a tile that the warps claim: the warps that start the slot early
+    // take more of them
+    const int nchunk = 2 * npre, lane = tid & 31;
+    int c = claim_chunk(next);
+    while (c < nchunk) {
+        int nx = 0;
+        if (lane == 0) nx = (int)atomicAdd(next, 1u);  // the next claim, in flight while this chunk splats
+        const int q = 32 * c + lane;
+        splat_window_pixel(key, d, a, U, pre[q >> 6], q, RX0, RY0);
+        c = __shfl_sync(0xFFFFFFFFu, nx, 0);
     }
 }
 
 // Splat from global memory: the 8 x 8 source tiles whose bounds reach R, 64 threads per tile (all consumers).  A
 // clean candidate (one exact motion, every pixel can land) splats with its precomputed offsets and reads only the
 // depth of its pixels.
-__device__ __forceinline__ void splat_global_candidate(EngineSmem &s, const TileParams &p, const FrameDims &d,
-                                                       const SplatTile &st, int RX0, int RY0, int tid);
+__device__ __forceinline__ void splat_global_candidate(uint64_t (*key)[kRegionN], const TileParams &p,
+                                                       const FrameDims &d, const SplatTile &st, int RX0, int RY0,
+                                                       int tid);
 
-__device__ inline void engine_splat_global(EngineSmem &s, const TileParams &p, const FrameDims &d, int RX0, int RY0,
-                                           int tid, const SplatTile *pre, int npre) {
-    if (npre > 0) {  // the plan's candidates, 64 threads each
-        for (int c0 = 0; c0 < npre; c0 += kConsumerThreads / 64) {
-            const int ci = c0 + (tid >> 6);
-            if (ci < npre) splat_global_candidate(s, p, d, pre[ci], RX0, RY0, tid);
+__device__ inline void engine_splat_global(EngineSmem &s, uint64_t (*key)[kRegionN], const TileParams &p,
+                                           const FrameDims &d, int RX0, int RY0, int tid, const SplatTile *pre,
+                                           int npre, uint32_t *next) {
+    if (npre > 0) {  // the plan's candidates, in chunks of half a tile that the warps claim
+        const int nchunk = 2 * npre, lane = tid & 31;
+        int c = claim_chunk(next);
+        while (c < nchunk) {
+            int nx = 0;
+            if (lane == 0) nx = (int)atomicAdd(next, 1u);
+            splat_global_candidate(key, p, d, pre[c >> 1], RX0, RY0, 32 * (c & 1) + lane);
+            c = __shfl_sync(0xFFFFFFFFu, nx, 0);
         }
-        bar_sync(kBarConsumers, kConsumerThreads);
         return;
     }
     int bx0, bx1, by0, by1;
@@ -759,15 +780,16 @@ __device__ inline void engine_splat_global(EngineSmem &s, const TileParams &p, c
         const int nc = (int)s.ncand;
         for (int c0 = 0; c0 < nc; c0 += kConsumerThreads / 64) {
             const int ci = c0 + (tid >> 6);
-            if (ci < nc) splat_global_candidate(s, p, d, s.cand[ci], RX0, RY0, tid);
+            if (ci < nc) splat_global_candidate(key, p, d, s.cand[ci], RX0, RY0, tid);
         }
         bar_sync(kBarConsumers, kConsumerThreads);
     }
 }
 
 // One pixel (of 64 threads' 8 x 8 tile) of a candidate source tile, from global memory.
-__device__ __forceinline__ void splat_global_candidate(EngineSmem &s, const TileParams &p, const FrameDims &d,
-                                                       const SplatTile &st, int RX0, int RY0, int tid) {
+__device__ __forceinline__ void splat_global_candidate(uint64_t (*key)[kRegionN], const TileParams &p,
+                                                       const FrameDims &d, const SplatTile &st, int RX0, int RY0,
+                                                       int tid) {
     const int x = 8 * st.bx + (tid & 7), y = 8 * st.by + ((tid >> 3) & 7);
     if (x >= p.W || y >= p.H) return;
     const size_t i = (size_t)y * p.W + x;
@@ -781,11 +803,11 @@ __device__ __forceinline__ void splat_global_candidate(EngineSmem &s, const Tile
             if ((unsigned)gx >= (unsigned)d.W || (unsigned)gy >= (unsigned)d.H) continue;
             const int rx = gx - RX0, ry = gy - RY0;
             if ((unsigned)rx < (unsigned)kRegion && (unsigned)ry < (unsigned)kRegion)
-                atomicMin((unsigned long long *)&s.key[kk][ry * kRegion + rx], (unsigned long long)kv);
+                atomicMin((unsigned long long *)&key[kk][ry * kRegion + rx], (unsigned long long)kv);
         }
     } else {
         const size_t plane = (size_t)p.W * p.H;
-        engine_splat_pixel(s.key, d, x, y, db, __float_as_uint(__ldg(p.mv + i)),
+        engine_splat_pixel(key, d, x, y, db, __float_as_uint(__ldg(p.mv + i)),
                            __float_as_uint(__ldg(p.mv + plane + i)), st.fm, RX0, RY0);
     }
 }
@@ -875,15 +897,16 @@ __device__ __forceinline__ void upper_levels(const float4 *l2, float4 &l3, float
     l5 = mean4(shfl4_idx(l4, 0), shfl4_idx(l4, 1), shfl4_idx(l4, 2), shfl4_idx(l4, 3));
 }
 
-// upper_levels through shared memory, for the fill of a tile: l2 the 64 level-2 nodes, up 20 float4 of the warp's
-// own scratch (level 3, then level 4).  Every lane returns l5, the level-3 node (w >> 1, bx >> 2) and the level-4
-// node (w >> 2, bx >> 3) above its block; the same nodes and order as upper_levels.
+// upper_levels through shared memory, for the fill of a tile: level-2 node (i, j) at l2[32 i + j] (row i in warp
+// i's scratch), up 20 float4 of the warp's own scratch (level 3, then level 4).  Every lane returns l5, the level-3
+// node (w >> 1, bx >> 2) and the level-4 node (w >> 2, bx >> 3) above its block; the same nodes and order as
+// upper_levels.
 __device__ __forceinline__ void upper_levels_smem(const float4 *l2, float4 *up, int w, int bx, float4 &v3, float4 &v4,
                                                   float4 &l5) {
     const int lane = threadIdx.x & 31;
     if (lane < 16) {
-        const float4 *c = l2 + (2 * (lane >> 2)) * 8 + 2 * (lane & 3);
-        up[lane] = mean4(c[0], c[1], c[8], c[9]);
+        const float4 *c = l2 + (2 * (lane >> 2)) * 32 + 2 * (lane & 3);
+        up[lane] = mean4(c[0], c[1], c[32], c[33]);
     }
     __syncwarp();
     if (lane < 4) {
@@ -976,8 +999,8 @@ constexpr float kNodeNeededOut = 5.0f;  // .w of such a node the coarse pass nee
 // which builds the upper levels.  c[] .w = validity.
 template <typename CT>
 __device__ __forceinline__ void fill_store_block(EngineSmem &s, const TileParams &p, const FrameDims &d, CT *oc,
-                                                 uint8_t *om, int g, int kk, int tile, int buf, int TX, int TY,
-                                                 float4 c[4], const uint8_t m[4], bool vec) {
+                                                 uint8_t *om, int g, int kk, int tile, int TX, int TY, float4 c[4],
+                                                 const uint8_t m[4], bool vec) {
     const int tg = threadIdx.x & (kGroupThreads - 1);
     const int lane = tg & 31, w = tg >> 5;
     const bool holes = __any_sync(0xFFFFFFFFu, (m[0] | m[1] | m[2] | m[3]) != 0);  // in the warp's rows
@@ -989,21 +1012,26 @@ __device__ __forceinline__ void fill_store_block(EngineSmem &s, const TileParams
         if (tg == 0) publish_node(p, make_float4(0.f, 0.f, 0.f, kNodeLazyOut), kk, tile);
         return;
     }
-    // level 1 of the group's 2 x 2 blocks in shared memory (the splat's candidate list is free until the next
-    // slot's vote), thread tg = block (tg & 15, tg >> 4); level 2 from four of them
+    // level 1 of the group's 2 x 2 blocks in the group's scratch (thread tg = block (tg & 15, tg >> 4)); a warp's
+    // level-2 nodes (its row w of them) from four of its level-1 nodes, then in the first 8 of its slots.  No later
+    // slot touches the scratch before every warp of the group is done with it (each slot that does starts behind a
+    // barrier of the whole group or of all consumers).
     const float4 n1 = mean4(c[0], c[1], c[2], c[3]);
     float4 *l1 = reinterpret_cast<float4 *>(s.cand) + g * kGroupThreads;
     l1[tg] = n1;
     __syncwarp();
-    float4 *l2 = s.l2[g][buf];
-    if ((lane & 17) == 0) l2[w * 8 + (lane >> 1)] = mean4(n1, l1[tg + 1], l1[tg + 16], l1[tg + 17]);
+    float4 n2o = n1;
+    if ((lane & 17) == 0) n2o = mean4(n1, l1[tg + 1], l1[tg + 16], l1[tg + 17]);
+    __syncwarp();  // every read of the warp's level-1 slots before they hold its level-2 nodes
+    float4 *l2 = l1;  // level-2 node (i, j) at l2[32 i + j]
+    if ((lane & 17) == 0) l2[32 * w + (lane >> 1)] = n2o;
     if (!holes && w != 0) {  // needs no upper level
         asm volatile("bar.arrive %0, %1;" ::"r"(2 + g), "r"(kGroupThreads) : "memory");
         store_block<CT>(d, oc, om, TX, TY, c, m, all, vec);
         return;
     }
     bar_sync(2 + g, kGroupThreads);
-    float4 *up = l1 + 32 * w;  // the warp's level-1 slots, read by no one after the barrier: levels 3 and 4
+    float4 *up = l1 + 32 * w + 8;  // the warp's slots after its level-2 nodes, read by no one else: levels 3 and 4
     const int bx = lane & 15;
     if (!holes) {
         if (w == 0) {
@@ -1014,7 +1042,7 @@ __device__ __forceinline__ void fill_store_block(EngineSmem &s, const TileParams
         store_block<CT>(d, oc, om, TX, TY, c, m, all, vec);
         return;
     }
-    const float4 n2 = l2[w * 8 + (bx >> 1)];  // level 2 of this thread's block
+    const float4 n2 = l2[32 * w + (bx >> 1)];  // level 2 of this thread's block
     bool deep = false;  // a hole whose level-1 and level-2 ancestors are both invalid
 #pragma unroll
     for (int t = 0; t < 4; ++t) deep = deep || (m[t] != 0 && n1.w == 0.0f && n2.w == 0.0f);
@@ -1353,8 +1381,8 @@ __device__ __forceinline__ void store_column(const FrameDims &p, CT *oc, uint8_t
 // ------------------------------------------------------------------------------------------------------------
 // One target tile for the calling group (fraction k0 + g); the splat (modes 1-3) is done.
 template <typename CT, int WX, int WY, bool FILL>
-__device__ __forceinline__ void tile_group(EngineSmem &s, const TileSlot &sl, int b, int g, int buf) {
-    const TileParams &p = sl.p;
+__device__ __forceinline__ void tile_group(EngineSmem &s, const TileSlot &sl, const TileParams &p, int b, int g,
+                                           uint64_t (*key)[kRegionN]) {
     const FrameDims d = dims_of(p);
     const int tg = threadIdx.x & (kGroupThreads - 1);
     const int bx = tg & 15, by = tg >> 4;
@@ -1391,10 +1419,10 @@ __device__ __forceinline__ void tile_group(EngineSmem &s, const TileSlot &sl, in
         uniform_block_any<CT, WX, WY>(win, wx0, wy0, d, u, TX, TY, c, m);
     } else if (mode == 1) {
         const WinAcc<CT, WX, WY> wa{&win, wx0, wy0};
-        gather_block<CT>(s.key[kk], wa, d, k, TX, TY, bx, by, c, m);
+        gather_block<CT>(key[kk], wa, d, k, TX, TY, bx, by, c, m);
     } else if (mode == 2 || mode == 3) {
         const GlobalAcc<CT> ga{(const CT *)p.color, p.depth, p.mv, d.W, (size_t)d.W * d.H};
-        gather_block<CT>(s.key[kk], ga, d, k, TX, TY, bx, by, c, m);
+        gather_block<CT>(key[kk], ga, d, k, TX, TY, bx, by, c, m);
     } else {  // 4: nothing lands
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
@@ -1403,30 +1431,37 @@ __device__ __forceinline__ void tile_group(EngineSmem &s, const TileSlot &sl, in
         }
     }
     if (FILL) {
-        fill_store_block<CT>(s, p, d, oc, om, g, kk, tile, buf, TX, TY, c, m, vec);
+        fill_store_block<CT>(s, p, d, oc, om, g, kk, tile, TX, TY, c, m, vec);
     } else {
         const bool all[4] = {true, true, true, true};
         store_block<CT>(d, oc, om, TX, TY, c, m, all, vec);
         if (mode >= 1 && mode <= 3)
-            bar_sync(2 + g, kGroupThreads);  // every key read of the group is done before the next init
+            bar_sync(2 + g, kGroupThreads);  // every key read of the group is done before they are emptied
     }
+    // the group's keys empty again for the next splat into this set (its reads ended at the barrier above or at
+    // the fill's first barrier)
+    if (mode >= 1 && mode <= 3)
+        for (int r = tg; r < kRegionN; r += kGroupThreads) key[kk][r] = kKeyEmpty;
 }
 
-// The splat of a tile (modes 1-3), all consumer threads; keys were initialised before the slot's vote.
+// The splat of a tile (modes 1-3) into key set `key`, all consumer threads; the set is empty (every group emptied its
+// fraction's keys after its last gather from them).  Ends with a consumer-wide barrier, which also orders every
+// use of the other key set in earlier slots before the next splat into it.
 template <typename CT, int WX, int WY>
-__device__ __forceinline__ void tile_splat(EngineSmem &s, const TileSlot &sl, int b, int tid) {
-    const TileParams &p = sl.p;
+__device__ __forceinline__ void tile_splat(EngineSmem &s, const TileSlot &sl, const TileParams &p, int b, int tid,
+                                           uint64_t (*key)[kRegionN]) {
     const FrameDims d = dims_of(p);
     const int mode = sl.plan.mode;
     const int RX0 = sl.X0 - 1, RY0 = sl.Y0 - 1;
-    const int npre = sl.plan.ndesc;  // the plan's candidates in s.pdesc[b] (0: none stored)
+    const int npre = sl.plan.ndesc;  // the plan's candidates in sl.pdesc (0: none stored)
     if (mode == 1) {
         const WinAcc<CT, WX, WY> wa{&window<CT, WX, WY>(s, b), sl.plan.wx0, sl.plan.wy0};
-        engine_splat_window(s, p, d, wa, plan_union(sl.plan, d.nfrac), RX0, RY0, tid, s.pdesc[b], npre);
-        bar_sync(kBarConsumers, kConsumerThreads);
-    } else if (mode == 2 || mode == 3) {
-        engine_splat_global(s, p, d, RX0, RY0, tid, s.pdesc[b], npre);
+        engine_splat_window(s, key, p, d, wa, plan_union(sl.plan, d.nfrac), RX0, RY0, tid, sl.pdesc, npre,
+                            &s.snext[b]);
+    } else {
+        engine_splat_global(s, key, p, d, RX0, RY0, tid, sl.pdesc, npre, &s.snext[b]);
     }
+    bar_sync(kBarConsumers, kConsumerThreads);
 }
 
 struct HalfGroupBarrier {  // the 4 warps of half group h: named barrier 5 + h
@@ -1435,12 +1470,14 @@ struct HalfGroupBarrier {  // the 4 warps of half group h: named barrier 5 + h
 };
 
 template <bool FILL, int SHAPE>
-__device__ void engine_consumer(EngineSmem &s, uint32_t *status) {
+__device__ void engine_consumer(EngineSmem &s, const EngineParams &ep) {
+    uint32_t *status = ep.status;
     using WS = WinShape<SHAPE>;
     const int tid = threadIdx.x;  // 0 .. 767
     const int g = tid >> 8, tg = tid & (kGroupThreads - 1);
     const int lane = tid & 31, w = tid >> 5;
     PendingCount pend;  // thread 0 of each group
+    uint32_t nsplat = 0;  // splat slots taken: slot n's keys are set n & 1
     for (uint32_t i = 0;; ++i) {
         const int b = (int)(i & 1u);
         // the next item is not ready: count what this group published before blocking (the producer may be
@@ -1450,7 +1487,8 @@ __device__ void engine_consumer(EngineSmem &s, uint32_t *status) {
         const TileSlot &sl = s.slot[b];
         const int kind = ok ? sl.kind : kSlotEnd;
         const int mode = kind == kSlotTile ? sl.plan.mode : -1;
-        const TileParams &p = sl.p;
+        // the stream's parameters (the end slot, and a slot that never arrived, name no stream)
+        const TileParams &p = ep.st[kind == kSlotEnd ? 0 : sl.stream].p;
         if (ok && mode == 0) {
             if (sl.cdt == EXW_F16)
                 build_source_words(window<__half, WS::xf16, WS::yf16>(s, b), sl.plan.wx0, sl.plan.wy0, sl.N,
@@ -1459,16 +1497,19 @@ __device__ void engine_consumer(EngineSmem &s, uint32_t *status) {
                 build_source_words(window<float, WS::xf32, WS::yf32>(s, b), sl.plan.wx0, sl.plan.wy0, sl.N,
                                    __uint_as_float(sl.plan.umx), __uint_as_float(sl.plan.umy), tid);
         }
-        if (ok && mode >= 1 && mode <= 3 && g < p.nfrac)
-            for (int r = tg; r < kRegionN; r += kGroupThreads) s.key[g][r] = kKeyEmpty;
         // The consumer-wide vote: every thread agrees that the slot arrived, and every group has finished the slots
         // before it.  Slots that share nothing between the groups and use no barrier that an earlier slot's warps may
         // still be due at (the fill's group barriers) -- smooth tiles (each group its own fraction, no barrier),
         // bounds items (each half group its own region, partials and barriers), plan items (a warp per tile),
         // fix-up slices after the first (plain stores) -- go on without it; a thread whose wait ran out meets the
         // others at the next slot's vote, which every other kind of slot (the end included) takes.
-        const bool solo = (kind == kSlotTile && mode == 5) || kind == kSlotBounds || kind == kSlotPlans ||
-                          (kind == kSlotFixup && sl.index != 0);
+        // A splat tile whose candidates the plan stored takes none either: its keys are the set the slot before
+        // did not use, emptied by every group after its last gather from them -- which the consumer-wide barrier
+        // closing the previous splat ordered before this one's splat -- and its first barrier is that closing
+        // barrier, which every warp reaches only after its earlier slots.
+        const bool splat = kind == kSlotTile && mode >= 1 && mode <= 3;
+        const bool solo = (kind == kSlotTile && mode == 5) || (splat && sl.plan.ndesc > 0) || kind == kSlotBounds ||
+                          kind == kSlotPlans || (kind == kSlotFixup && sl.index != 0);
         if (!solo && bar_red_or(kBarConsumers, kConsumerThreads, !ok)) {
             if (tid == 0) {  // (the slot may never have been written: its parameters are not used here)
                 atomicCAS(status, 0u, (uint32_t)EXW_ERR_TIMEOUT);
@@ -1482,11 +1523,13 @@ __device__ void engine_consumer(EngineSmem &s, uint32_t *status) {
             const int h = tid >> 7, th = tid & 127;  // half group: 4 warps, 8 rows each, 24 loads in flight
             const int region = sl.index * kRegionsPerItem + h;
             const int nrx = (p.W + 31) / 32;
+            // the partials live in the group's scratch: every warp of the group is done with its last fill
+            bar_sync(kBarBounds + g, kGroupThreads);
+            float4 *part = reinterpret_cast<float4 *>(s.cand) + g * kGroupThreads + 32 * (h & 1);
             if (region < nrx * ((p.H + 31) / 32)) {
                 bounds_region<4>(p.depth, p.mv, p.W, p.H, const_cast<float4 *>(p.tile_bounds),
                                  const_cast<float2 *>(p.tile_depth), const_cast<float4 *>(p.region_bounds), p.fh,
-                                 region % nrx, region / nrx, &s.bpart[g][32 * (h & 1)], true, th,
-                                 HalfGroupBarrier{5 + h});
+                                 region % nrx, region / nrx, part, true, th, HalfGroupBarrier{5 + h});
                 if (th < 32) {  // warp 0 of the half group wrote the bounds
                     __threadfence();
                     __syncwarp();
@@ -1519,11 +1562,15 @@ __device__ void engine_consumer(EngineSmem &s, uint32_t *status) {
             if (sl.cdt == EXW_F16) fixup_slice<__half>(p, (uint32_t)sl.index, kFixupItems, tid, kConsumerThreads);
             else fixup_slice<float>(p, (uint32_t)sl.index, kFixupItems, tid, kConsumerThreads);
         } else {  // target tile
-            if (sl.cdt == EXW_F16) tile_splat<__half, WS::xf16, WS::yf16>(s, sl, b, tid);
-            else tile_splat<float, WS::xf32, WS::yf32>(s, sl, b, tid);
+            uint64_t(*key)[kRegionN] = s.key[nsplat & 1u];
+            if (splat) {
+                if (sl.cdt == EXW_F16) tile_splat<__half, WS::xf16, WS::yf16>(s, sl, p, b, tid, key);
+                else tile_splat<float, WS::xf32, WS::yf32>(s, sl, p, b, tid, key);
+                ++nsplat;
+            }
             if (g < p.nfrac) {
-                if (sl.cdt == EXW_F16) tile_group<__half, WS::xf16, WS::yf16, FILL>(s, sl, b, g, (int)(i & 1u));
-                else tile_group<float, WS::xf32, WS::yf32, FILL>(s, sl, b, g, (int)(i & 1u));
+                if (sl.cdt == EXW_F16) tile_group<__half, WS::xf16, WS::yf16, FILL>(s, sl, p, b, g, key);
+                else tile_group<float, WS::xf32, WS::yf32, FILL>(s, sl, p, b, g, key);
                 if (FILL && tg == 0) {
                     pend.add(p.fh);
                     if (mode == 5 && sl.pair) pend.add(p.fh);
