@@ -6,14 +6,16 @@
 // -- so an item's dependencies (the previous stage of its own stream) come earlier in the queue.
 //
 //   producer warp:   takes items in queue order, waits (bounded) until the item's stage may start, and hands the
-//                    item to the consumers in one of two shared-memory slots.  For a target tile it reads the
-//                    tile's plan, computes the per-fraction constants of uniform tiles and stages the tile's source
-//                    window (depth, motion, colour) into the slot's buffer with TMA loads (cp.async.bulk.tensor,
-//                    mbarrier completion), one item ahead of the consumers.
-//   3 x 8 consumer warps: a bounds item gives each group one 32 x 32 source region, a plan item each warp one
-//                    target tile, a fix-up item all of them a slice; for a target tile, group g computes fraction
-//                    k0 + g -- each thread a 2 x 2 pixel block -- then fills and stores it.  Every consumer warp
-//                    releases the slot through a second mbarrier.
+//                    item to the consumers in one of two shared-memory slots.  For a target tile it stages the
+//                    tile's source window (depth, motion, colour) into the slot's buffer with TMA loads
+//                    (cp.async.bulk.tensor, mbarrier completion) and, while they land, writes the tile's plan, its
+//                    splat candidates and the per-fraction constants of uniform tiles, one item ahead of the
+//                    consumers.
+//   3 x 8 consumer warps: a bounds item gives each half group one 32 x 32 source region, a plan item each warp one
+//                    target tile, a fix-up item all of them a slice; for a target tile all of them splat (modes
+//                    1-3), then group g computes fraction k0 + g -- each thread a 2 x 2 pixel block -- fills and
+//                    stores it.  Every consumer warp releases the slot through a second mbarrier.  Only the slots
+//                    whose groups share state start with a consumer-wide vote (engine_consumer).
 //
 // Tiles whose candidate sources all carry one motion (plan modes 0 and 5) are pure translations: the winner of
 // target q is the source q - o_k when that pixel is valid and carries the tile's motion, so no splat is needed.
