@@ -36,7 +36,8 @@ constexpr int kEngineThreads = kConsumerThreads + 32;       // + the producer wa
 constexpr int kBarConsumers = 1;                            // named barriers: 1 all consumers, 2 + g group g,
 constexpr int kBarBounds = 11;  // 5 + h half group h (bounds), 11 + g group g (bounds)
 constexpr int kMaxStreams = 48;                             // streams per launch (kernel-parameter space)
-constexpr int kRegionsPerItem = 2 * kMaxFrac;               // a bounds item: one region per half group (4 warps)
+constexpr int kRegionsPerHalf = 2;  // a bounds item: two regions per half group (4 warps), one after the other
+constexpr int kRegionsPerItem = 2 * kMaxFrac * kRegionsPerHalf;
 constexpr int kPlansPerItem = kConsumerWarps;               // a plan item: one tile per consumer warp
 constexpr uint32_t kFixupItems = 8u;                        // fix-up items per stream (with the fill)
 // Every wait of the engine is bounded in time.  The producer gives up on a stage or on a buffer's release after
@@ -1523,20 +1524,26 @@ __device__ void engine_consumer(EngineSmem &s, const EngineParams &ep) {
         if (kind == kSlotEnd) return;
         if (kind == kSlotBounds) {
             const int h = tid >> 7, th = tid & 127;  // half group: 4 warps, 8 rows each, 24 loads in flight
-            const int region = sl.index * kRegionsPerItem + h;
-            const int nrx = (p.W + 31) / 32;
-            // the partials live in the group's scratch: every warp of the group is done with its last fill
+            const int nrx = (p.W + 31) / 32, nreg = nrx * ((p.H + 31) / 32);
+            // the partials live in the group's scratch (a part per region, so the second region's partials never
+            // overwrite the first one's while its last warp still reads them): every warp of the group is done with
+            // its last fill
             bar_sync(kBarBounds + g, kGroupThreads);
-            float4 *part = reinterpret_cast<float4 *>(s.cand) + g * kGroupThreads + 32 * (h & 1);
-            if (region < nrx * ((p.H + 31) / 32)) {
+            uint32_t done = 0u;
+#pragma unroll 1
+            for (int j = 0; j < kRegionsPerHalf; ++j) {
+                const int region = sl.index * kRegionsPerItem + h * kRegionsPerHalf + j;
+                float4 *part = reinterpret_cast<float4 *>(s.cand) + g * kGroupThreads + 64 * (h & 1) + 32 * j;
+                if (region >= nreg) break;
                 bounds_region<4>(p.depth, p.mv, p.W, p.H, const_cast<float4 *>(p.tile_bounds),
                                  const_cast<float2 *>(p.tile_depth), const_cast<float4 *>(p.region_bounds), p.fh,
                                  region % nrx, region / nrx, part, true, th, HalfGroupBarrier{5 + h});
-                if (th < 32) {  // warp 0 of the half group wrote the bounds
-                    __threadfence();
-                    __syncwarp();
-                    if (th == 0) atomicAdd(&p.fh->bdone, 1u);
-                }
+                ++done;
+            }
+            if (done != 0u && th < 32) {  // warp 0 of the half group wrote the bounds: one fence, one count
+                __threadfence();
+                __syncwarp();
+                if (th == 0) atomicAdd(&p.fh->bdone, done);
             }
             // the group's bounds partials are free again (its own barrier: a bounds slot takes no vote, and a warp may
             // still be due at barrier 2 + g of an earlier tile, where warps without holes only arrive)
