@@ -36,7 +36,7 @@ constexpr int kEngineThreads = kConsumerThreads + 32;       // + the producer wa
 constexpr int kBarConsumers = 1;                            // named barriers: 1 all consumers, 2 + g group g,
 constexpr int kBarBounds = 11;  // 5 + h half group h (bounds), 11 + g group g (bounds)
 constexpr int kMaxStreams = 48;                             // streams per launch (kernel-parameter space)
-constexpr int kRegionsPerHalf = 2;  // a bounds item: two regions per half group (4 warps), one after the other
+constexpr int kRegionsPerHalf = 4;  // a bounds item: four regions per half group (4 warps), one after the other
 constexpr int kRegionsPerItem = 2 * kMaxFrac * kRegionsPerHalf;
 constexpr int kPlansPerItem = kConsumerWarps;               // a plan item: one tile per consumer warp
 constexpr uint32_t kFixupItems = 8u;                        // fix-up items per stream (with the fill)
@@ -109,6 +109,7 @@ struct alignas(16) TileSlot {
 constexpr int kWindowBytes = 64512;  // both window shapes (56 x 48 FP32, 64 x 56 FP16) hold 64,512 bytes
 static_assert(64 * 16 * kConsumerWarps <= kWindowBytes, "the coarse pass's per-warp scratch fits one buffer");
 static_assert(sizeof(SplatTile) == sizeof(float4), "the candidate list doubles as one float4 per consumer thread");
+static_assert(2 * kRegionsPerHalf * 32 <= kGroupThreads, "a bounds item's partials (32 float4 a region) fit a group's scratch");
 static_assert(sizeof(Window<float, WinShape<0>::xf32, WinShape<0>::yf32>) == kWindowBytes &&
                   sizeof(Window<__half, WinShape<0>::xf16, WinShape<0>::yf16>) == kWindowBytes &&
                   sizeof(Window<float, WinShape<1>::xf32, WinShape<1>::yf32>) == kWindowBytes &&
@@ -1525,15 +1526,14 @@ __device__ void engine_consumer(EngineSmem &s, const EngineParams &ep) {
         if (kind == kSlotBounds) {
             const int h = tid >> 7, th = tid & 127;  // half group: 4 warps, 8 rows each, 24 loads in flight
             const int nrx = (p.W + 31) / 32, nreg = nrx * ((p.H + 31) / 32);
-            // the partials live in the group's scratch (a part per region, so the second region's partials never
-            // overwrite the first one's while its last warp still reads them): every warp of the group is done with
-            // its last fill
+            // the partials live in the group's scratch (a part per region, so a region's partials never overwrite the
+            // previous one's while its last warp still reads them): every warp of the group is done with its last fill
             bar_sync(kBarBounds + g, kGroupThreads);
             uint32_t done = 0u;
 #pragma unroll 1
             for (int j = 0; j < kRegionsPerHalf; ++j) {
                 const int region = sl.index * kRegionsPerItem + h * kRegionsPerHalf + j;
-                float4 *part = reinterpret_cast<float4 *>(s.cand) + g * kGroupThreads + 64 * (h & 1) + 32 * j;
+                float4 *part = reinterpret_cast<float4 *>(s.cand) + g * kGroupThreads + 32 * (kRegionsPerHalf * (h & 1) + j);
                 if (region >= nreg) break;
                 bounds_region<4>(p.depth, p.mv, p.W, p.H, const_cast<float4 *>(p.tile_bounds),
                                  const_cast<float2 *>(p.tile_depth), const_cast<float4 *>(p.region_bounds), p.fh,
