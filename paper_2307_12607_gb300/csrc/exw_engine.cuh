@@ -38,7 +38,8 @@ constexpr int kBarBounds = 11;  // 5 + h half group h (bounds), 11 + g group g (
 constexpr int kMaxStreams = 48;                             // streams per launch (kernel-parameter space)
 constexpr int kRegionsPerHalf = 4;  // a bounds item: four regions per half group (4 warps), one after the other
 constexpr int kRegionsPerItem = 2 * kMaxFrac * kRegionsPerHalf;
-constexpr int kPlansPerItem = kConsumerWarps;               // a plan item: one tile per consumer warp
+constexpr int kPlansPerWarp = 2;                            // a plan item: two tiles per consumer warp
+constexpr int kPlansPerItem = kConsumerWarps * kPlansPerWarp;
 constexpr uint32_t kFixupItems = 8u;                        // fix-up items per stream (with the fill)
 // Every wait of the engine is bounded in time.  The producer gives up on a stage or on a buffer's release after
 // kProducerWaitNs, and then hands no further slot over (it raises the abort flag); a consumer gives up on a slot
@@ -1549,14 +1550,18 @@ __device__ void engine_consumer(EngineSmem &s, const EngineParams &ep) {
             // still be due at barrier 2 + g of an earlier tile, where warps without holes only arrive)
             bar_sync(kBarBounds + g, kGroupThreads);
         } else if (kind == kSlotPlans) {
-            const int tile = sl.index * kPlansPerItem + w;
-            if (tile < p.n5x * p.n5y) {
+            uint32_t done = 0u;
+#pragma unroll 1
+            for (int j = 0; j < kPlansPerWarp; ++j) {
+                const int tile = sl.index * kPlansPerItem + j * kConsumerWarps + w;
+                if (tile >= p.n5x * p.n5y) break;
                 if (sl.cdt == EXW_F16) plan_tile<__half, WS::xf16, WS::yf16>(p, tile);
                 else plan_tile<float, WS::xf32, WS::yf32>(p, tile);
-                if (lane == 0) {
-                    __threadfence();
-                    atomicAdd(&p.fh->pdone, 1u);
-                }
+                ++done;
+            }
+            if (done != 0u && lane == 0) {  // one fence and one count for the warp's plans
+                __threadfence();
+                atomicAdd(&p.fh->pdone, done);
             }
         } else if (kind == kSlotFixup) {
             if (sl.index == 0) {  // every node of the stream is counted: build the coarse levels, then release
