@@ -309,6 +309,26 @@ __device__ inline void engine_producer(EngineSmem &s, const EngineParams &ep) {
                 }
             }
         }
+        // A fix-up item of a stream where every tile of every fraction has a valid pixel has nothing to do: it takes
+        // no slot (the stream's tile count, complete here, covers every count of tiles without one); for the first
+        // item the producer releases the stream's other fix-ups itself.
+        if (ok && item < ep.total && stage == 3) {
+            bool none = true;
+            if (lane == 0)
+                for (int kk = 0; kk < p.nfrac; ++kk) none = none && __ldcg(&p.fh->ninvalid[kk]) == 0u;
+            if (__shfl_sync(0xFFFFFFFFu, (int)none, 0) != 0) {
+                if (lane == 0 && local == 0)
+                    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&p.fh->cready), "r"(1u) : "memory");
+                cur = nxt;
+                word = nword;
+                have_word = nhave;
+                have_desc = nhave_desc;
+                desc0 = ndesc0;
+                desc1 = ndesc1;
+                --i;  // no slot was handed over: the next item takes this one
+                continue;
+            }
+        }
         if (ok && i >= 2) {  // the consumers' release of this buffer's previous use
             if (lane == 0) ok = mbar_wait_or_abort(&s.empty[b], ((i >> 1) - 1u) & 1u, &s.abort, kProducerWaitNs);
             ok = __shfl_sync(0xFFFFFFFFu, (int)ok, 0) != 0;
