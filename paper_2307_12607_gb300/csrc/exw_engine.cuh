@@ -96,7 +96,6 @@ struct alignas(16) TileSlot {
     int kind, stream, index, cdt;  // the stream's parameters are read from the launch's (ep.st[stream].p)
     TilePlan plan;            // tile: its plan (mode 3 for every tile of a stream without TMA windows)
     int X0, Y0;
-    Rect N;                   // modes 0, 5: the source rectangle the fractions read
     UniformFrac u[kMaxFrac];  // modes 0, 5
     // mode 5: a second smooth tile of the same stream, the next in the queue, shares the slot (its colour window
     // follows the first one's in the buffer)
@@ -180,7 +179,6 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *mbar, uint32_t pari
 // ------------------------------------------------------------------------------------------------------------
 // Producer
 // ------------------------------------------------------------------------------------------------------------
-__device__ __forceinline__ Rect uniform_sources(const TileParams &p, uint32_t umx, uint32_t umy, int RX0, int RY0);
 
 // Constants of fraction kk of a uniform tile, by the lanes 8 kk .. 8 kk + 7 of the producer warp (lane 8 kk + j
 // writes inv[j]).
@@ -406,7 +404,6 @@ __device__ inline void engine_producer(EngineSmem &s, const EngineParams &ep) {
                 const uint32_t umx = (uint32_t)__shfl_sync(0xFFFFFFFFu, word, 16);
                 const uint32_t umy = (uint32_t)__shfl_sync(0xFFFFFFFFu, word, 17);
                 if (lane < 8 * p.nfrac) uniform_frac(sl.u[lane >> 3], p, umx, umy, lane >> 3, lane & 7);
-                if (lane == 0) sl.N = uniform_sources(p, umx, umy, X0 - 1, Y0 - 1);
             }
             if (pair) {
                 const int X02 = (nxt.local % p.n5x) * kFillTile, Y02 = (nxt.local / p.n5x) * kFillTile;
@@ -459,62 +456,42 @@ __device__ inline void engine_producer(EngineSmem &s, const EngineParams &ep) {
 // Uniform tiles
 // ------------------------------------------------------------------------------------------------------------
 
-// Source rectangle N a uniform tile reads (the union over fractions of R - o_k grown by one, inside the frame).
-__device__ __forceinline__ Rect uniform_sources(const TileParams &p, uint32_t umx, uint32_t umy, int RX0, int RY0) {
-    Rect N{1 << 30, -(1 << 30), 1 << 30, -(1 << 30)};
-    for (int kk = 0; kk < p.nfrac; ++kk) {
-        const int ox = axis_off_of(umx, p.k0 + kk, p.L), oy = axis_off_of(umy, p.k0 + kk, p.L);
-        N.x0 = min(N.x0, RX0 - ox - 1);
-        N.x1 = max(N.x1, RX0 + kRegion - ox);
-        N.y0 = min(N.y0, RY0 - oy - 1);
-        N.y1 = max(N.y1, RY0 + kRegion - oy);
-    }
-    N.x0 = max(N.x0, 0);
-    N.y0 = max(N.y0, 0);
-    N.x1 = min(N.x1, p.W - 1);
-    N.y1 = min(N.y1, p.H - 1);
-    return N;
-}
-
-// Rewrite the window's depth plane (over N) into source words: depth bits of a valid pixel with motion (mx, my),
-// the bits with the sign set for a valid pixel with another motion, all ones for a pixel without valid depth.
-// Four pixels per step (16-byte shared-memory accesses); all consumer threads.
+// The source words of one fraction of a uniform tile (all threads of its group): for the kWordSide x kWordSide source
+// pixels from (bx0, by0) -- the fraction's sources of the tile's region R, R - o_k grown by one -- the depth bits of a
+// valid pixel with motion (mx, my), the bits with the sign set for a valid pixel with another motion, all ones for a
+// pixel without valid depth or outside the frame.  Read from the staged window into the group's words.
+constexpr int kWordSide = kRegion + 2;
+static_assert((kWordSide * kWordSide + 1) / 2 <= kRegionN, "a fraction's source words fit its part of a key set");
 template <typename CT, int WX, int WY>
-__device__ __forceinline__ void build_source_words(Window<CT, WX, WY> &w, int wx0, int wy0, Rect N, float mx, float my,
-                                                   int tid) {
-    const int qx0 = max((N.x0 - wx0) >> 2, 0), qx1 = min((N.x1 - wx0) >> 2, WX / 4 - 1);
-    const int ry0 = max(N.y0 - wy0, 0), ry1 = min(N.y1 - wy0, WY - 1);
-    static_assert(WX / 4 <= 16, "one half warp covers a window row");
-    const int q = qx0 + (tid & 15);  // a half warp per row, a quad per lane (WX / 4 <= 16)
-    if (q > qx1) return;
-    for (int row = ry0 + (tid >> 4); row <= ry1; row += kConsumerThreads / 16) {
-        const int idx = row * WX + 4 * q;
-        uint4 d = *reinterpret_cast<const uint4 *>(&w.depth[idx]);
-        const float4 vx = *reinterpret_cast<const float4 *>(&w.mv[0][idx]);
-        const float4 vy = *reinterpret_cast<const float4 *>(&w.mv[1][idx]);
-        auto word = [&](uint32_t db, float ux, float uy) -> uint32_t {
-            if (!depth_ok(db)) return 0xFFFFFFFFu;
-            return (ux == mx && uy == my) ? db : (db | 0x80000000u);
-        };
-        d.x = word(d.x, vx.x, vy.x);
-        d.y = word(d.y, vx.y, vy.y);
-        d.z = word(d.z, vx.z, vy.z);
-        d.w = word(d.w, vx.w, vy.w);
-        *reinterpret_cast<uint4 *>(&w.depth[idx]) = d;
+__device__ __forceinline__ void group_source_words(const Window<CT, WX, WY> &w, int wx0, int wy0, const FrameDims &d,
+                                                   uint32_t *words, int bx0, int by0, float mx, float my, int tg) {
+    for (int c = tg; c < kWordSide * kWordSide; c += kGroupThreads) {
+        const int y = by0 + c / kWordSide, x = bx0 + c % kWordSide;
+        uint32_t v = 0xFFFFFFFFu;
+        // (every such pixel inside the frame lies in the window, which holds the sources of all fractions)
+        if ((unsigned)x < (unsigned)d.W && (unsigned)y < (unsigned)d.H && (unsigned)(x - wx0) < (unsigned)WX &&
+            (unsigned)(y - wy0) < (unsigned)WY) {
+            const int i = (y - wy0) * WX + (x - wx0);
+            const uint32_t db = __float_as_uint(w.depth[i]);
+            if (depth_ok(db)) v = (w.mv[0][i] == mx && w.mv[1][i] == my) ? db : (db | 0x80000000u);
+        }
+        words[c] = v;
     }
 }
 
 // One 2 x 2 block of a uniform tile for one fraction.  The block's cells are addressed in a frame mirrored so that
 // the taps lie at +1 in x and y: mirrored column j <-> source column SX + c(j), c(j) = MX ? 2 - j : j - 1 (rows
 // likewise), pixels at j, i in {1, 2}; the mirror flags are runtime values (one code copy for the four cases).  Frame checks for tiles near the border (one code path for every tile:
-// the kernel is sensitive to its instruction footprint); every shared-memory index stays inside the window.
-// Results c[], m[] are in true pixel order (dy * 2 + dx).
+// the kernel is sensitive to its instruction footprint); every shared-memory index stays inside the window and the
+// fraction's source words (words, kWordSide x kWordSide from (bx0, by0)).  Results c[], m[] are in true pixel order
+// (dy * 2 + dx).
 template <typename CT, int WX, int WY>
 __device__ __forceinline__ void uniform_block(const Window<CT, WX, WY> &w, int wx0, int wy0, const FrameDims &p,
-                                              const UniformFrac &u, int TX, int TY, float4 c[4], uint8_t m[4]) {
+                                              const UniformFrac &u, int TX, int TY, const uint32_t *words, int bx0,
+                                              int by0, float4 c[4], uint8_t m[4]) {
     const bool MX = (u.flags & kMirX) != 0, MY = (u.flags & kMirY) != 0;
     const int SX = TX - u.ox, SY = TY - u.oy;
-    int cidx[4], ridx[4];
+    int cidx[4], ridx[4], wcol[4], wrow[4];
     bool fc[4], fr[4], sc[4], sr[4], tc[4], tr[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -524,14 +501,15 @@ __device__ __forceinline__ void uniform_block(const Window<CT, WX, WY> &w, int w
         tc[j] = (unsigned)tx < (unsigned)p.W;
         fc[j] = sc[j] && tc[j];
         cidx[j] = min(max(sx, wx0), wx0 + WX - 1) - wx0;  // a no-op inside the frame: keeps any index in the window
+        wcol[j] = min(max(sx - bx0, 0), kWordSide - 1);
         const int sy = SY + drow, ty = TY + drow;
         sr[j] = (unsigned)sy < (unsigned)p.H;
         tr[j] = (unsigned)ty < (unsigned)p.H;
         fr[j] = sr[j] && tr[j];
         ridx[j] = (min(max(sy, wy0), wy0 + WY - 1) - wy0) * WX;
+        wrow[j] = min(max(sy - by0, 0), kWordSide - 1) * kWordSide;
     }
-    const uint32_t *wd = reinterpret_cast<const uint32_t *>(w.depth);
-    auto V = [&](int i, int j) -> uint32_t { return wd[ridx[i] + cidx[j]]; };
+    auto V = [&](int i, int j) -> uint32_t { return words[wrow[i] + wcol[j]]; };
     // validated word of a target cell: the source word if it is a winner, else all ones
     auto D = [&](uint32_t v, int i, int j) -> uint32_t {
         const uint32_t x = v | (uint32_t)((int32_t)v >> 31);
@@ -610,8 +588,9 @@ __device__ __forceinline__ void uniform_block(const Window<CT, WX, WY> &w, int w
 
 template <typename CT, int WX, int WY>
 __device__ __forceinline__ void uniform_block_any(const Window<CT, WX, WY> &w, int wx0, int wy0, const FrameDims &p,
-                                                  const UniformFrac &u, int TX, int TY, float4 c[4], uint8_t m[4]) {
-    uniform_block<CT, WX, WY>(w, wx0, wy0, p, u, TX, TY, c, m);
+                                                  const UniformFrac &u, int TX, int TY, const uint32_t *words, int bx0,
+                                                  int by0, float4 c[4], uint8_t m[4]) {
+    uniform_block<CT, WX, WY>(w, wx0, wy0, p, u, TX, TY, words, bx0, by0, c, m);
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -1407,7 +1386,7 @@ __device__ __forceinline__ void store_column(const FrameDims &p, CT *oc, uint8_t
 // One target tile for the calling group (fraction k0 + g); the splat (modes 1-3) is done.
 template <typename CT, int WX, int WY, bool FILL>
 __device__ __forceinline__ void tile_group(EngineSmem &s, const TileSlot &sl, const TileParams &p, int b, int g,
-                                           uint64_t (*key)[kRegionN]) {
+                                           uint64_t (*key)[kRegionN], uint64_t (*idle)[kRegionN]) {
     const FrameDims d = dims_of(p);
     const int tg = threadIdx.x & (kGroupThreads - 1);
     const int bx = tg & 15, by = tg >> 4;
@@ -1439,9 +1418,19 @@ __device__ __forceinline__ void tile_group(EngineSmem &s, const TileSlot &sl, co
     }
     float4 c[4];
     uint8_t m[4];
+    // uniform tile: the fraction's source words in the group's part of the key set no splat uses before the next
+    // one (empty again when the group is done)
+    uint32_t *words = reinterpret_cast<uint32_t *>(idle[kk]);
     if (mode == 0) {
         const UniformFrac &u = sl.u[kk];
-        uniform_block_any<CT, WX, WY>(win, wx0, wy0, d, u, TX, TY, c, m);
+        const int bx0 = X0 - 2 - u.ox, by0 = Y0 - 2 - u.oy;  // (R - o_k grown by one)
+        // the slot's first barrier, which every warp of the group reaches only after its earlier slots: their
+        // emptying of these cells (by other threads than the ones that write the words) is done
+        bar_sync(kBarBounds + g, kGroupThreads);
+        group_source_words(win, wx0, wy0, d, words, bx0, by0, __uint_as_float(sl.plan.umx),
+                           __uint_as_float(sl.plan.umy), tg);
+        bar_sync(kBarBounds + g, kGroupThreads);  // every word before any read of them
+        uniform_block_any<CT, WX, WY>(win, wx0, wy0, d, u, TX, TY, words, bx0, by0, c, m);
     } else if (mode == 1) {
         const WinAcc<CT, WX, WY> wa{&win, wx0, wy0};
         gather_block<CT>(key[kk], wa, d, k, TX, TY, bx, by, c, m);
@@ -1460,13 +1449,15 @@ __device__ __forceinline__ void tile_group(EngineSmem &s, const TileSlot &sl, co
     } else {
         const bool all[4] = {true, true, true, true};
         store_block<CT>(d, oc, om, TX, TY, c, m, all, vec);
-        if (mode >= 1 && mode <= 3)
-            bar_sync(2 + g, kGroupThreads);  // every key read of the group is done before they are emptied
+        if (mode <= 3)
+            bar_sync(2 + g, kGroupThreads);  // every key or word read of the group is done before they are emptied
     }
     // the group's keys empty again for the next splat into this set (its reads ended at the barrier above or at
-    // the fill's first barrier)
+    // the fill's first barrier); a uniform tile's words likewise
     if (mode >= 1 && mode <= 3)
         for (int r = tg; r < kRegionN; r += kGroupThreads) key[kk][r] = kKeyEmpty;
+    if (mode == 0)
+        for (int r = tg; r < (kWordSide * kWordSide + 1) / 2; r += kGroupThreads) idle[kk][r] = kKeyEmpty;
 }
 
 // The splat of a tile (modes 1-3) into key set `key`, all consumer threads; the set is empty (every group emptied its
@@ -1514,14 +1505,6 @@ __device__ void engine_consumer(EngineSmem &s, const EngineParams &ep) {
         const int mode = kind == kSlotTile ? sl.plan.mode : -1;
         // the stream's parameters (the end slot, and a slot that never arrived, name no stream)
         const TileParams &p = ep.st[kind == kSlotEnd ? 0 : sl.stream].p;
-        if (ok && mode == 0) {
-            if (sl.cdt == EXW_F16)
-                build_source_words(window<__half, WS::xf16, WS::yf16>(s, b), sl.plan.wx0, sl.plan.wy0, sl.N,
-                                   __uint_as_float(sl.plan.umx), __uint_as_float(sl.plan.umy), tid);
-            else
-                build_source_words(window<float, WS::xf32, WS::yf32>(s, b), sl.plan.wx0, sl.plan.wy0, sl.N,
-                                   __uint_as_float(sl.plan.umx), __uint_as_float(sl.plan.umy), tid);
-        }
         // The consumer-wide vote: every thread agrees that the slot arrived, and every group has finished the slots
         // before it.  Slots that share nothing between the groups and use no barrier that an earlier slot's warps may
         // still be due at (the fill's group barriers) -- smooth tiles (each group its own fraction, no barrier),
@@ -1533,8 +1516,10 @@ __device__ void engine_consumer(EngineSmem &s, const EngineParams &ep) {
         // closing the previous splat ordered before this one's splat -- and its first barrier is that closing
         // barrier, which every warp reaches only after its earlier slots.
         const bool splat = kind == kSlotTile && mode >= 1 && mode <= 3;
-        const bool solo = (kind == kSlotTile && mode == 5) || (splat && sl.plan.ndesc > 0) || kind == kSlotBounds ||
-                          kind == kSlotPlans || (kind == kSlotFixup && sl.index != 0);
+        // So does a uniform tile: each group builds its fraction's source words in its part of the key set no
+        // splat uses before the next one, behind a group barrier.
+        const bool solo = (kind == kSlotTile && (mode == 5 || mode == 0)) || (splat && sl.plan.ndesc > 0) ||
+                          kind == kSlotBounds || kind == kSlotPlans || (kind == kSlotFixup && sl.index != 0);
         if (!solo && bar_red_or(kBarConsumers, kConsumerThreads, !ok)) {
             if (tid == 0) {  // (the slot may never have been written: its parameters are not used here)
                 atomicCAS(status, 0u, (uint32_t)EXW_ERR_TIMEOUT);
@@ -1603,14 +1588,14 @@ __device__ void engine_consumer(EngineSmem &s, const EngineParams &ep) {
                 ++nsplat;
             }
             if (g < p.nfrac) {
-                if (sl.cdt == EXW_F16) tile_group<__half, WS::xf16, WS::yf16, FILL>(s, sl, p, b, g, key);
-                else tile_group<float, WS::xf32, WS::yf32, FILL>(s, sl, p, b, g, key);
+                uint64_t(*idle)[kRegionN] = s.key[(nsplat + 1u) & 1u];  // after this slot's splat, if any
+                if (sl.cdt == EXW_F16) tile_group<__half, WS::xf16, WS::yf16, FILL>(s, sl, p, b, g, key, idle);
+                else tile_group<float, WS::xf32, WS::yf32, FILL>(s, sl, p, b, g, key, idle);
                 if (FILL && tg == 0) {
                     pend.add(p.fh);
                     if (mode == 5 && sl.pair) pend.add(p.fh);
                 }
             }
-            if (mode == 0) fence_proxy_async_smem();  // generic writes to the window before the next TMA into it
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&s.empty[b]);
