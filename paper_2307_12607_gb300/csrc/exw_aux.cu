@@ -36,6 +36,8 @@ __global__ void __launch_bounds__(256, 8) bounds_kernel(const float *__restrict_
                                                         int W, int H, float4 *tile_bounds, float2 *tile_depth,
                                                         float4 *region_bounds, FrameHeader *fh) {
     __shared__ float4 part[64];
+    grid_dependency_wait();  // the frame header is zeroed by the kernel before
+    grid_dependents_launch();
     bounds_region<8>(depth, mv, W, H, tile_bounds, tile_depth, region_bounds, fh, blockIdx.x, blockIdx.y, part, true,
                      (int)threadIdx.x, CtaBarrier{});
 }
@@ -148,10 +150,11 @@ cudaError_t launch_bounds(const float *depth, const float *mv, int W, int H, flo
                           float4 *region_bounds, FrameHeader *fh, cudaStream_t s) {
     const dim3 g((unsigned)ceil_div(W, 32), (unsigned)ceil_div(H, 32), 1);
     timing_begin("exw_bounds", s);
-    bounds_kernel<<<g, 256, 0, s>>>(depth, mv, W, H, tile_bounds, tile_depth, region_bounds, fh);
+    const cudaError_t e = launch_dependent(bounds_kernel, g, dim3(256), 0, s, depth, mv, W, H, tile_bounds, tile_depth,
+                                           region_bounds, fh);
     count_launch();
     timing_end("exw_bounds", s);
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_bounds_finalize(const FrameHeader *fh, float *frame_bounds, cudaStream_t s) {

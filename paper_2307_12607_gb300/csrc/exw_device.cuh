@@ -17,6 +17,12 @@ constexpr int kRegionN = kRegion * kRegion;
 constexpr int kBoundsBlock = 8;        // side of the motion-bounds tiles
 constexpr int kMaxFrac = 3;
 
+// Grids launched by launch_dependent: wait until the grids before this one on the stream have completed and their
+// writes are visible (at once for a grid launched without programmatic serialisation), and let the next grid be
+// scheduled (it waits in turn before touching memory).
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dependents_launch() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 // ------------------------------------------------------------------------------------------------------------
 // Validity of source pixels
 // ------------------------------------------------------------------------------------------------------------

@@ -18,6 +18,7 @@ __global__ void __launch_bounds__(kEngineThreads, 1) engine_kernel(const __grid_
     }
     // both key sets start empty; a group empties its fraction's keys again after each gather from them
     for (int r = threadIdx.x; r < 2 * kMaxFrac * kRegionN; r += blockDim.x) (&s.key[0][0][0])[r] = kKeyEmpty;
+    grid_dependency_wait();  // the bounds and plan kernels of the first stream, or the previous launch
     __syncthreads();
     if (threadIdx.x >= kConsumerThreads) engine_producer<SHAPE>(s, ep);
     else engine_consumer<FILL, SHAPE>(s, ep);
@@ -30,8 +31,7 @@ static cudaError_t launch_one(const EngineParams &ep, int grid, cudaStream_t s) 
     const cudaError_t e =
         cudaFuncSetAttribute(engine_kernel<FILL, SHAPE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
     if (e != cudaSuccess) return e;
-    engine_kernel<FILL, SHAPE><<<grid, kEngineThreads, kSmem, s>>>(ep);
-    return cudaSuccess;
+    return launch_dependent(engine_kernel<FILL, SHAPE>, dim3(grid), dim3(kEngineThreads), kSmem, s, ep);
 }
 
 cudaError_t launch_engine(const EngineParams &ep, bool fill, int shape, int grid, cudaStream_t s) {

@@ -7,6 +7,8 @@ namespace exw {
 // Plans: one warp per target tile (the first stream of an engine launch is planned ahead of the launch).
 template <typename CT, int WX, int WY>
 __global__ void __launch_bounds__(kThreads) plan_kernel(TileParams p) {
+    grid_dependency_wait();  // the bounds kernel before
+    grid_dependents_launch();
     const int tile = blockIdx.x * kWarps + (threadIdx.x >> 5);
     if (tile < p.n5x * p.n5y) plan_tile<CT, WX, WY>(p, tile);
 }
@@ -87,16 +89,14 @@ cudaError_t launch_plan(const TileParams &p, exw_dtype cdt, int shape, cudaStrea
     timing_begin("exw_plan", s);
     using S0 = WinShape<0>;
     using S1 = WinShape<1>;
-    if (shape == 0) {
-        if (cdt == EXW_F32) plan_kernel<float, S0::xf32, S0::yf32><<<g, kThreads, 0, s>>>(p);
-        else plan_kernel<__half, S0::xf16, S0::yf16><<<g, kThreads, 0, s>>>(p);
-    } else {
-        if (cdt == EXW_F32) plan_kernel<float, S1::xf32, S1::yf32><<<g, kThreads, 0, s>>>(p);
-        else plan_kernel<__half, S1::xf16, S1::yf16><<<g, kThreads, 0, s>>>(p);
-    }
+    void (*k)(TileParams) = shape == 0 ? (cdt == EXW_F32 ? plan_kernel<float, S0::xf32, S0::yf32>
+                                                          : plan_kernel<__half, S0::xf16, S0::yf16>)
+                                       : (cdt == EXW_F32 ? plan_kernel<float, S1::xf32, S1::yf32>
+                                                          : plan_kernel<__half, S1::xf16, S1::yf16>);
+    const cudaError_t e = launch_dependent(k, dim3(g), dim3(kThreads), 0, s, p);
     count_launch();
     timing_end("exw_plan", s);
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_warp_tiles(const TileParams &p, exw_dtype cdt, cudaStream_t s) {

@@ -214,6 +214,24 @@ size_t engine_workspace_bytes(const EngineSpec *specs, int n, int nfrac, bool sh
 exw_status engine_run(const EngineSpec *specs, int n, int nfrac, unsigned flags, void *ws, size_t ws_bytes,
                       struct exw_tuner *tuner, bool shared_size, cudaStream_t s);
 
+// Launch with programmatic stream serialisation: the grid may be scheduled while the kernel before it on the stream
+// is still draining, so it must execute grid_dependency_wait() (exw_device.cuh) before it touches any memory.
+template <typename... Params, typename... Args>
+inline cudaError_t launch_dependent(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                    Args &&...args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+}
+
 // Timing hooks (exw_api.cu): bracket a launch with events when timing is enabled.
 void timing_begin(const char *name, cudaStream_t s);
 void timing_end(const char *name, cudaStream_t s);
