@@ -296,6 +296,10 @@ __device__ inline float4 bounds_region(const float *__restrict__ depth, const fl
     const size_t plane = (size_t)W * H;
     float mnx = __int_as_float(0x7F800000), mxx = -mnx, mny = mnx, mxy = -mnx;
     const int x = X0 + lane;
+    // the frame-wide maxima as they stand, read with the data (any earlier value is a valid lower bound: a stale one
+    // only costs an atomic that does not raise anything)
+    uint32_t seen = 0xFFFFFFFFu;
+    if (frame_atomics && tid < 4) seen = reinterpret_cast<volatile uint32_t *>(fh->acc)[tid];
     float fx[rpw], fy[rpw];
     uint32_t db[rpw];
 #pragma unroll
@@ -370,12 +374,10 @@ __device__ inline float4 bounds_region(const float *__restrict__ depth, const fl
         }
         if (t == 0) region_bounds[(size_t)ry * ((W + 31) / 32) + rx] = b;
         if (frame_atomics && t < 4 && b.x <= b.y) {
-            // Frame-wide maxima: an atomic only when this region's value exceeds what is already there (a stale
-            // read just costs one unneeded atomic).
+            // Frame-wide maxima: an atomic only when this region's value exceeds what was there when the region began
             const float v = t == 0 ? -b.x : t == 1 ? b.y : t == 2 ? -b.z : b.w;
             const uint32_t code = float_order(v);
-            volatile uint32_t *acc = fh->acc;
-            if (code > acc[t]) atomicMax(&fh->acc[t], code);
+            if (code > seen) atomicMax(&fh->acc[t], code);
         }
         return b;
     }
