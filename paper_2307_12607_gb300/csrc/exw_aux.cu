@@ -31,14 +31,15 @@ __global__ void __launch_bounds__(256) splat_global_kernel(const float *__restri
     atomicMin(keys + (size_t)gy * W + gx, (unsigned long long)pack_key_global(db, (uint32_t)i));
 }
 
-// Stage (a0): one 32 x 32 source region per CTA of 8 warps (4 rows each), up to 8 CTAs per SM.
-__global__ void __launch_bounds__(256, 8) bounds_kernel(const float *__restrict__ depth, const float *__restrict__ mv,
+// Stage (a0): one 32 x 32 source region per CTA of 4 warps (8 rows each, 24 loads in flight per thread), up to 12
+// CTAs per SM.
+__global__ void __launch_bounds__(128, 12) bounds_kernel(const float *__restrict__ depth, const float *__restrict__ mv,
                                                         int W, int H, float4 *tile_bounds, float2 *tile_depth,
                                                         float4 *region_bounds, FrameHeader *fh) {
-    __shared__ float4 part[64];
+    __shared__ float4 part[32];
     grid_dependency_wait();  // the frame header is zeroed by the kernel before
     grid_dependents_launch();
-    bounds_region<8>(depth, mv, W, H, tile_bounds, tile_depth, region_bounds, fh, blockIdx.x, blockIdx.y, part, true,
+    bounds_region<4>(depth, mv, W, H, tile_bounds, tile_depth, region_bounds, fh, blockIdx.x, blockIdx.y, part, true,
                      (int)threadIdx.x, CtaBarrier{});
 }
 
@@ -150,7 +151,7 @@ cudaError_t launch_bounds(const float *depth, const float *mv, int W, int H, flo
                           float4 *region_bounds, FrameHeader *fh, cudaStream_t s) {
     const dim3 g((unsigned)ceil_div(W, 32), (unsigned)ceil_div(H, 32), 1);
     timing_begin("exw_bounds", s);
-    const cudaError_t e = launch_dependent(bounds_kernel, g, dim3(256), 0, s, depth, mv, W, H, tile_bounds, tile_depth,
+    const cudaError_t e = launch_dependent(bounds_kernel, g, dim3(128), 0, s, depth, mv, W, H, tile_bounds, tile_depth,
                                            region_bounds, fh);
     count_launch();
     timing_end("exw_bounds", s);
