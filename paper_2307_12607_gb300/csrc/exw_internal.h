@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <type_traits>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -215,10 +216,16 @@ exw_status engine_run(const EngineSpec *specs, int n, int nfrac, unsigned flags,
                       struct exw_tuner *tuner, bool shared_size, cudaStream_t s);
 
 // Launch with programmatic stream serialisation: the grid may be scheduled while the kernel before it on the stream
-// is still draining, so it must execute grid_dependency_wait() (exw_device.cuh) before it touches any memory.
+// is still draining, so it must execute grid_dependency_wait() (exw_device.cuh) before it touches any memory.  The
+// arguments are passed by address, not copied (the engine's parameter block is 32 KB), so each must have exactly
+// its parameter's type.
 template <typename... Params, typename... Args>
 inline cudaError_t launch_dependent(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                                    Args &&...args) {
+                                    const Args &...args) {
+    static_assert(sizeof...(Params) == sizeof...(Args), "one argument per kernel parameter");
+    static_assert((std::is_same<typename std::decay<Params>::type, Args>::value && ...),
+                  "each argument has its parameter's exact type");
+    void *pargs[] = {const_cast<void *>(static_cast<const void *>(&args))...};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
@@ -229,7 +236,7 @@ inline cudaError_t launch_dependent(void (*kernel)(Params...), dim3 grid, dim3 b
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+    return cudaLaunchKernelExC(&cfg, reinterpret_cast<const void *>(kernel), pargs);
 }
 
 // Timing hooks (exw_api.cu): bracket a launch with events when timing is enabled.
