@@ -68,9 +68,9 @@ def dist_env():
 # capture (a smaller launch; the engine's traffic grows in proportion to the frames of a launch), with the hash of
 # the kernel's sources (KERNEL_SOURCES) it was taken on: reported only while they are unchanged, else null.
 MEASURED_TRAFFIC = {
-    ("exw_engine", "sequence_1080p_fp32"): ((236.592e6 + 282.124e6) / 4, "42ef17d543ba7802"),
-    ("exw_engine", "warp_4k_fp16"): (105.038e6 + 130.132e6, "42ef17d543ba7802"),
-    ("exw_train", "fwd_bwd_1080p"): (215.191e6 + 28.042e6, "79c814e29d44dfec"),
+    ("exw_engine", "sequence_1080p_fp32"): ((236.626e6 + 282.247e6) / 4, "1ffed5361dabe3d2"),
+    ("exw_engine", "warp_4k_fp16"): (105.047e6 + 130.172e6, "1ffed5361dabe3d2"),
+    ("exw_train", "fwd_bwd_1080p"): (215.129e6 + 28.325e6, "b1abf7c2171af943"),
 }
 
 
