@@ -313,8 +313,9 @@ EXW_API size_t exw_tuner_report(const exw_tuner *t, char *buf, size_t len);
 EXW_API size_t exw_batched_workspace_bytes(const exw_stream_desc *d, int n, int nfrac);
 
 /* Stages (a0)+(a)+(b)+(c) -- P_1..P_nfrac at t + k/4 (Sec. IV-B), as exw_extrapolate -- for n independent streams of
- * possibly different sizes (each with its own colour type) in ONE persistent kernel launch: CTAs pull (stream, stage,
- * tile) work items from a queue in the workspace; a stage waits for the one before it in the same stream with a bounded
+ * possibly different sizes (each with its own colour type) in one persistent kernel launch per 48 streams (the first
+ * stream's bounds and plans run as two kernels ahead of it): CTAs pull (stream, stage, tile) work items from a queue in
+ * the workspace; a stage waits for the one before it in the same stream with a bounded
  * spin (EXW_ERR_TIMEOUT via exw_device_status if it runs out).  Capturable in a CUDA graph. d [n] is a HOST array. t
  * (nullable) is the autotuner: on the first call for a given set of sizes (outside any stream capture) it times
  * every schedule -- the shape of the shared-memory staging windows (FP32 56 x 48 or 64 x 42, FP16 64 x 56 or
